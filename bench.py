@@ -1,0 +1,437 @@
+#!/usr/bin/env python
+"""Benchmark of the oscillator Ising machine hot path on GB300.
+
+One bench step = one full simulation of the workload: every Euler-Maruyama step
+of every replica of every graph, with the periodic readout and cut scoring
+(the whole hot path), from the initial Philox draw to the final scores.
+Default workload: the batched max-cut case, a 50x40 toroidal +-1 grid and an
+Erdos-Renyi G(2000, 0.01) graph, 1024 replicas each, 5000 steps.
+
+Prints one JSON line (rank 0).  `value` is edge-updates/s (directed CSR nonzeros
+x replicas x steps per second) over all ranks; ranks run independent replicas
+(weak scaling, no collective in the data path).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from workloads import make_workload  # noqa: E402
+
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+L2_FLUSH_BYTES = 256 << 20
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        p["source"] = "measured"
+        return p
+    except Exception:
+        p = dict(PEAKS_FALLBACK)
+        p["source"] = "fallback"
+        return p
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-i", str(self.gpu), "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def schedules(w):
+    K = np.stack(w.K).astype(np.float32)
+    Ks = np.stack(w.Ks).astype(np.float32)
+    Kn = np.stack(w.Kn).astype(np.float32)
+    return K, Ks, Kn
+
+
+def stretched(w, factor):
+    """The workload's schedules stretched over factor x steps (same shape in time)."""
+    T = w.steps * factor
+    idx = np.minimum(np.arange(T) // factor, w.steps - 1)
+    K, Ks, Kn = schedules(w)
+    return np.ascontiguousarray(K[:, idx]), np.ascontiguousarray(Ks[:, idx]), np.ascontiguousarray(Kn[:, idx]), T
+
+
+def cpu_oracle_sample(w, seconds_hint=15.0):
+    """Time the FP64 oracle on this host's cores on a bounded sample of the workload."""
+    import oracle
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    oracle.build()
+    K, Ks, Kn = schedules(w)
+    # calibrate with a short run, then size the sample to about seconds_hint
+    R_s = max(1, cores)
+    T_cal = 50
+    t0 = time.perf_counter()
+    for gi, g in enumerate(w.graphs):
+        oracle.run(g, w.q, K[gi, :T_cal].astype(np.float64), Ks[gi, :T_cal].astype(np.float64),
+                   Kn[gi, :T_cal].astype(np.float64), float(np.float32(w.dt)), T_cal, R_s, 1,
+                   graph=gi, nthreads=cores)
+    cal = time.perf_counter() - t0
+    T_s = int(min(w.steps, max(T_cal, T_cal * seconds_hint / max(cal, 1e-6))))
+    t0 = time.perf_counter()
+    for gi, g in enumerate(w.graphs):
+        oracle.run(g, w.q, K[gi, :T_s].astype(np.float64), Ks[gi, :T_s].astype(np.float64),
+                   Kn[gi, :T_s].astype(np.float64), float(np.float32(w.dt)), T_s, R_s, 1,
+                   graph=gi, nthreads=cores)
+    el = time.perf_counter() - t0
+    edge_updates = sum(g.nnz for g in w.graphs) * R_s * T_s
+    return {"value": edge_updates / el, "unit": "edge-updates/s", "cores": cores, "kind": "oracle",
+            "sample": f"all {len(w.graphs)} graphs, {R_s} replicas, first {T_s} of {w.steps} steps "
+                      f"(FP64 C oracle, OpenMP over replicas), {el:.1f} s"}
+
+
+def run_reference(args):
+    """The reference arm: the FP64 CPU oracle, timed on this host's cores."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    w = make_workload(args.workload)
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    oracle.build()
+    K, Ks, Kn = schedules(w)
+    R_s = max(1, cores)
+    # size one reference step to about 8 s of host time
+    T_cal = 20
+    t0 = time.perf_counter()
+    for gi, g in enumerate(w.graphs):
+        oracle.run(g, w.q, K[gi, :T_cal].astype(np.float64), Ks[gi, :T_cal].astype(np.float64),
+                   Kn[gi, :T_cal].astype(np.float64), float(np.float32(w.dt)), T_cal, R_s, 1,
+                   graph=gi, nthreads=cores)
+    cal = time.perf_counter() - t0
+    T_s = int(min(w.steps, max(T_cal, T_cal * 8.0 / max(cal, 1e-6))))
+
+    def step(seed):
+        for gi, g in enumerate(w.graphs):
+            oracle.run(g, w.q, K[gi, :T_s].astype(np.float64), Ks[gi, :T_s].astype(np.float64),
+                       Kn[gi, :T_s].astype(np.float64), float(np.float32(w.dt)), T_s, R_s, seed,
+                       graph=gi, nthreads=cores)
+
+    for k in range(args.warmup):
+        step(100 + k)
+    times = []
+    for k in range(args.steps):
+        t0 = time.perf_counter()
+        step(1 + k)
+        times.append(time.perf_counter() - t0)
+    per = float(np.mean(times))
+    edge_updates = sum(g.nnz for g in w.graphs) * R_s * T_s
+    value = edge_updates / per
+    sample = (f"all {len(w.graphs)} graphs, {R_s} replicas, first {T_s} of {w.steps} steps "
+              f"per reference step (FP64 C oracle, OpenMP over replicas)")
+    line = {
+        "impl": "reference", "metric": "edge-updates/s", "value": value, "unit": "edge-updates/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": w.name, "replicas_sampled": R_s,
+                                        "euler_steps_sampled": T_s},
+        "cpu_baseline": {"value": value, "unit": "edge-updates/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "edge-updates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def first_hit(trace_best, target):
+    """Index of the first readout whose best score reaches target (None if never)."""
+    hit = np.nonzero(trace_best >= target)[0]
+    return int(hit[0]) if hit.size else None
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="torus_er2000")
+    ap.add_argument("--form", default="auto")
+    ap.add_argument("--precision", default="auto")
+    ap.add_argument("--readout-every", type=int, default=50)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-quality", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    from paper_2505_22631_gb300 import Problem, Run, build, capi
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+    capi.load()
+
+    w = make_workload(args.workload)
+    K, Ks, Kn = schedules(w)
+    dK, dKs, dKn = (torch.from_numpy(a).cuda() for a in (K, Ks, Kn))
+    problems = [Problem.from_graph(g, w.q) for g in w.graphs]
+    prob = Problem.batch(problems) if len(problems) > 1 else problems[0]
+    stream = torch.cuda.current_stream()
+    seed_base = 1000 * (rank + 1)
+    run = Run(prob, dK, dKs, dKn, w.dt, w.steps, w.replicas, seed_base, form=args.form,
+              precision=args.precision, readout_every=args.readout_every, stream=stream)
+    info = run.info()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    for k in range(args.warmup):
+        run.rerun(dK, dKs, dKn, w.dt, w.steps, seed_base + 1 + k)
+    run.sync()
+
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    t_wall = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(float(k))                 # L2 flush between timed steps, outside the events
+        starts[k].record(stream)
+        run.rerun(dK, dKs, dKn, w.dt, w.steps, seed_base + 100 + k)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    wall = time.perf_counter() - t_wall
+    clocks = sampler.stop()
+    ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms_step = float(np.mean(ms))
+    if world > 1:
+        t = torch.tensor([ms_step], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_step = float(t.item())
+    edge_updates = w.edge_updates() * world
+    value = edge_updates / (ms_step / 1e3)
+
+    # roofline of the dominant kernel (one launch per step in the resident form)
+    peaks = load_peaks()
+    node_replica_steps = w.nodes * w.replicas * w.steps
+    csr_bytes = sum(4 * g.nnz + 8 * (g.n + 1) for g in w.graphs) * w.steps
+    bytes_per_unit = 24 if info["precision"] in (1,) else 16
+    alg_bytes = node_replica_steps * bytes_per_unit + csr_bytes
+    achieved = alg_bytes / (ms_step / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "kernel": "resident_kernel" if info["form"] == 2 else "step_stream_kernel",
+                "peak_source": peaks["source"],
+                "algorithmic_bytes_per_launch": alg_bytes}
+
+    # end to end through the C ABI with host buffers: upload graphs and schedules,
+    # simulate, read spins and scores back, free everything
+    from paper_2505_22631_gb300 import capi as C
+    host_graphs = [(g.n, np.ascontiguousarray(g.row_ptr), np.ascontiguousarray(g.col),
+                    np.ascontiguousarray(g.w)) for g in w.graphs]
+    pin = {k: torch.from_numpy(a).pin_memory() for k, a in (("K", K), ("Ks", Ks), ("Kn", Kn))}
+    spins_h = torch.empty(w.nodes * w.replicas, dtype=torch.int8).pin_memory()
+    score_h = torch.empty(len(w.graphs) * w.replicas, dtype=torch.float64).pin_memory()
+    best_h = torch.empty(len(w.graphs), dtype=torch.int32).pin_memory()
+    h2d = sum(8 * (n + 1) + 4 * c.shape[0] + 4 * ww.shape[0] for n, _, c, ww in host_graphs) \
+        + 3 * K.size * 4
+    d2h = spins_h.numel() + score_h.numel() * 8 + best_h.numel() * 4
+
+    def e2e_step(seed):
+        hs = [C.oim_create_problem(n, w.q, c.shape[0], rp, c, ww, 2) for n, rp, c, ww in host_graphs]
+        hb = C.oim_create_batch(hs) if len(hs) > 1 else hs[0]
+        o = C.oim_default_opts()
+        o.form = run.opts.form
+        o.precision = run.opts.precision
+        o.readout_every = args.readout_every
+        o.stream = int(stream.cuda_stream)
+        hr = C.oim_run(hb, pin["K"], pin["Ks"], pin["Kn"], w.dt, w.steps, w.replicas, seed, o)
+        C.oim_readout(hr, spins_h, score_h, best_h, None, None)
+        C.oim_destroy_run(hr)
+        if len(hs) > 1:
+            C.oim_destroy_problem(hb)
+        for h in hs:
+            C.oim_destroy_problem(h)
+
+    e2e_step(7)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(args.e2e_steps):
+        e2e_step(8 + k)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / max(args.e2e_steps, 1)
+    e2e = {"value": w.edge_updates() * world / e2e_s, "unit": "edge-updates/s",
+           "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+           "ms_per_step": e2e_s * 1e3}
+
+    line = {
+        "metric": "edge-updates/s", "value": value, "unit": "edge-updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if info["precision"] == 1 else "f32 (16-bit cos/sin cache)",
+        "data": "synthetic",
+        "config": {"workload": w.name, "graphs": [g.name for g in w.graphs],
+                   "nodes": [g.n for g in w.graphs], "nnz": [g.nnz for g in w.graphs],
+                   "replicas": w.replicas, "euler_steps": w.steps,
+                   "readout_every": args.readout_every,
+                   "form": {0: "auto", 1: "stream", 2: "resident", 3: "gemm"}[info["form"]],
+                   "precision": {1: "fp32", 2: "bf16", 3: "fp16"}.get(info["precision"]),
+                   "l2": "256 MB buffer written between timed steps (outside the events)",
+                   "parallelism": f"replicas x{world} (weak)"},
+        "roofline": roofline,
+        "clocks": clocks,
+        "e2e": e2e,
+        "gpu_launches": args.steps * (1 if info["form"] == 2 else
+                                      w.steps + 1 + (w.steps // args.readout_every if args.readout_every else 0)),
+        "wall_s_timed_region": wall,
+        "step_ms_all": ms,
+    }
+
+    if rank == 0 and not args.no_quality:
+        line["quality"] = quality(w, prob, problems, args, stream, ms_step)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_oracle_sample(w)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    run.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def quality(w, prob, problems, args, stream, ms_step_chosen):
+    """Time to 99% of the best known cut: chosen form vs the plain FP32 CSR form."""
+    import torch
+    from paper_2505_22631_gb300 import Run
+    re = args.readout_every
+    q2 = w.q == 2
+    # best known: best score of a 4x longer run of the chosen form
+    K4, Ks4, Kn4, T4 = stretched(w, 4)
+    long = Run(prob, K4, Ks4, Kn4, w.dt, T4, w.replicas, 4242, form=args.form,
+               precision=args.precision, readout_every=re * 4, stream=stream)
+    tr = long.readout(spins=False)["trace"]
+    long.close()
+    best_known = tr.max(axis=(1, 2)) if q2 else tr.min(axis=(1, 2))
+    K, Ks, Kn = schedules(w)
+    chosen = Run(prob, K, Ks, Kn, w.dt, w.steps, w.replicas, 777, form=args.form,
+                 precision=args.precision, readout_every=re, stream=stream).readout(spins=False)
+    per_step_chosen = ms_step_chosen / 1e3 / w.steps
+    res = {"best_known": best_known.tolist(), "graphs": []}
+    t_chosen = 0.0
+    t_plain = 0.0
+    for gi, g in enumerate(w.graphs):
+        # the plain form: one graph per launch, one launch per step, FP32 CSR
+        plain = Run(problems[gi], K[gi], Ks[gi], Kn[gi], w.dt, w.steps, w.replicas, 777,
+                    form="stream", precision="fp32", readout_every=re, use_graph=False,
+                    stream=stream)
+        plain.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plain.rerun(K[gi], Ks[gi], Kn[gi], w.dt, w.steps, 777)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        per_step_plain = e0.elapsed_time(e1) / 1e3 / w.steps
+        po = plain.readout(spins=False)
+        plain.close()
+        target = 0.99 * best_known[gi] if q2 else best_known[gi] / 0.99
+        rows = {}
+        for name, out, per in (("chosen", chosen, per_step_chosen), ("plain_fp32_csr", po, per_step_plain)):
+            tb = out["trace"][gi].max(axis=1) if q2 else -out["trace"][gi].min(axis=1)
+            hit = first_hit(tb, target if q2 else -target)
+            rows[name] = {"time_to_99pct_s": None if hit is None else (hit + 1) * re * per,
+                          "steps_to_99pct": None if hit is None else (hit + 1) * re,
+                          "final_best": float(out["score"][gi].max() if q2 else out["score"][gi].min()),
+                          "final_mean": float(out["score"][gi].mean()),
+                          "s_per_euler_step": per}
+        res["graphs"].append({"graph": g.name, **rows})
+        for name in ("chosen", "plain_fp32_csr"):
+            t = rows[name]["time_to_99pct_s"]
+            if t is None:
+                t = float("inf")
+            if name == "chosen":
+                t_chosen = max(t_chosen, t)
+            else:
+                t_plain += t
+    res["time_to_99pct_best_cut_s"] = {"chosen": t_chosen, "plain_fp32_csr": t_plain}
+    return res
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,214 @@
+/*
+ * oim.h -- C ABI of liboim, a GB300 (sm_103a) simulator of the oscillator
+ * Ising/Potts machine of "GPU-Accelerated Simulated Oscillator Ising/Potts
+ * Machine Solving Combinatorial Optimization Problems" (arXiv 2505.22631).
+ *
+ * The library time-steps many independent replicas of the noisy Kuramoto phase
+ * dynamics with sub-harmonic injection locking (Eq. 5, Algorithm 1) on one GPU,
+ * reads the phases out to spins / colours (the phase threshold kernel of
+ * Sec. III-B) and scores them as cuts (Ising, Eq. 1) or colouring conflicts
+ * (Potts, Eq. 2).
+ *
+ * Conventions shared by every call:
+ *  - Return value: OIM_OK (0) or a negative OIM_E* code; oim_last_error() then
+ *    returns a message for the calling thread.  Outputs are written only on OIM_OK.
+ *  - Pointers marked "host or device" may point to host memory (pageable or
+ *    pinned) or to device memory of the current device; the library inspects
+ *    them with cudaPointerGetAttributes.
+ *  - Handles are owned by the library; the caller frees them with the matching
+ *    oim_destroy_*.  Input arrays are copied; the caller keeps ownership.
+ *  - Work is queued on the stream given in oim_run_opts (NULL = legacy default
+ *    stream) and runs asynchronously; oim_readout, oim_get_phases and
+ *    oim_run_sync wait for it.
+ *  - Calls on one handle must not overlap from several host threads.
+ *
+ * Model (the readings of the paper this library implements):
+ *   d theta_i = [ K_t * sum_j w_ij sin(2 pi (theta_i - theta_j))
+ *                 - Ks_t * sin(2 pi q theta_i) ] dt + Kn_t * sqrt(dt) * xi_i,t
+ *   theta_i <- theta_i - floor(theta_i)                      (phases in [0,1))
+ * with xi ~ N(0,1) drawn from Philox4x32-10 (Salmon et al., SC'11) at counter
+ * (node i, step t, replica>>2, (graph<<1)|1), key = seed, lane = replica&3,
+ * Box-Muller on lane pairs (0,1),(2,3); initial phases are the uniforms
+ * ((x>>9)+0.5)*2^-23 of the same generator at (i, 0, replica>>2, (graph<<1)|0).
+ * Readout: spin = floor(q*theta + 1/2) mod q, taken in FP32.
+ */
+#ifndef OIM_H
+#define OIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define OIM_OK            0
+#define OIM_EINVAL       -1   /* bad argument: size, range, malformed CSR, ...   */
+#define OIM_ENOMEM       -2   /* device or host allocation failed                */
+#define OIM_ECUDA        -3   /* a CUDA runtime call or kernel launch failed     */
+#define OIM_ETIMEOUT     -4   /* a device-side wait gave up (error word set)     */
+#define OIM_EUNSUPPORTED -5   /* valid request this build or GPU cannot serve   */
+#define OIM_ESTATE       -6   /* handle in the wrong state for this call         */
+
+/* ---- integration forms ---------------------------------------------------- */
+#define OIM_FORM_AUTO      0  /* chosen per graph by the autotuner               */
+#define OIM_FORM_STREAM    1  /* plain FP32 CSR: one launch per step, state in HBM */
+#define OIM_FORM_RESIDENT  2  /* one launch for all steps; each block keeps whole  */
+                              /* replicas of one graph in shared memory           */
+#define OIM_FORM_GEMM      3  /* dense coupling on the tensor cores (BF16 W x     */
+                              /* [cos|sin], FP32 accumulate), one launch per step */
+
+/* ---- storage precision of the (cos, sin) cache the coupling reads --------- */
+#define OIM_PREC_AUTO 0
+#define OIM_PREC_FP32 1
+#define OIM_PREC_BF16 2
+#define OIM_PREC_FP16 3
+
+/* ---- problem flags -------------------------------------------------------- */
+#define OIM_FLAG_SKIP_SYMMETRY_CHECK 1u  /* trust the caller that w_ij == w_ji   */
+#define OIM_FLAG_DEFER_UPLOAD        2u  /* keep the graph on the host until its   */
+                                         /* first run (e.g. a member of a batch)   */
+
+typedef struct oim_problem_s* oim_problem_t;
+typedef struct oim_run_s* oim_run_t;
+
+typedef struct oim_run_opts {
+    int32_t form;               /* OIM_FORM_*                                      */
+    int32_t precision;          /* OIM_PREC_*                                      */
+    int64_t readout_every;      /* score all replicas every this many steps (0: at */
+                                /* the end only); a trace entry per readout        */
+    void*   stream;             /* cudaStream_t to queue the work on               */
+    int32_t use_graph;          /* stream form: replay steps from a CUDA graph     */
+    int32_t replicas_per_block; /* resident form: 0 = chosen by the library        */
+    int32_t threads_per_block;  /* 0 = chosen by the library                       */
+    int32_t checkpoint_every;   /* keep phases every this many steps for           */
+                                /* oim_backward (0: no checkpoints)                */
+    int32_t reserved[8];
+} oim_run_opts;
+
+/* Fill *opts with the defaults: AUTO form and precision, readout at the end,
+ * default stream, CUDA graph on, no checkpoints. */
+void oim_default_opts(oim_run_opts* opts);
+
+/* Library version string and the compute capability it was built for. */
+const char* oim_version(void);
+
+/* Message describing the last failed call on this host thread ("" if none). */
+const char* oim_last_error(void);
+
+/*
+ * oim_create_problem -- upload one graph (Sec. II-C: max-cut maps each edge to
+ * a coupling J_ij; colouring maps each edge to a coupling between differently
+ * coloured nodes; here J_ij := w_ij, Eq. 5-6).
+ *   n        number of oscillators (nodes), 1 <= n < 2^30
+ *   q        number of stable phases: 2 = Ising max-cut, >= 3 = Potts colouring
+ *            (the paper's N in Eq. 4-5), 2 <= q <= 16
+ *   nnz      number of directed entries in the CSR (each undirected edge twice)
+ *   row_ptr  int64[n+1], host or device; row_ptr[0] = 0, nondecreasing,
+ *            row_ptr[n] = nnz
+ *   col_idx  int32[nnz], host or device; strictly increasing within a row,
+ *            0 <= col < n, no diagonal entry
+ *   weights  float[nnz], host or device, finite; NULL means every weight is +1.
+ *            The matrix must be symmetric (checked unless
+ *            OIM_FLAG_SKIP_SYMMETRY_CHECK).
+ *   out      receives the new handle.
+ * Errors: OIM_EINVAL for any violation above, OIM_ENOMEM, OIM_ECUDA.
+ */
+int oim_create_problem(int32_t n, int32_t q, int64_t nnz, const int64_t* row_ptr,
+                       const int32_t* col_idx, const float* weights, uint32_t flags,
+                       oim_problem_t* out);
+
+/*
+ * oim_create_batch -- join `count` problems (same q) into one batch problem
+ * whose graphs are simulated together in one launch (graph index g = position in
+ * `problems`, which also selects the random stream of that graph).  The inputs
+ * stay valid and owned by the caller.  Errors: OIM_EINVAL (count < 1, NULL
+ * handle, mixed q, a batch inside a batch), OIM_ENOMEM, OIM_ECUDA.
+ */
+int oim_create_batch(int32_t count, const oim_problem_t* problems, oim_problem_t* out);
+
+/* Number of graphs, total nodes and total directed entries of a problem. */
+int oim_problem_info(oim_problem_t p, int32_t* graphs, int64_t* nodes, int64_t* nnz, int32_t* q);
+
+void oim_destroy_problem(oim_problem_t p);
+
+/*
+ * oim_run -- simulate `replicas` independent trajectories of every graph of p
+ * for `steps` forward-Euler / Euler-Maruyama steps (Algorithm 1, Eq. 5).
+ *   K, Ks, Kn  float[graphs * steps], host or device: per-step coupling
+ *              strength, injection strength and noise amplitude of each graph
+ *              (row g = graph g).  Algorithm 1 builds Ks as a triangular wave;
+ *              any schedule is accepted.
+ *   dt         step size h > 0
+ *   steps      >= 0 and < 2^32
+ *   replicas   1 <= replicas <= 2^20
+ *   seed       key of the Philox stream
+ *   opts       NULL for defaults
+ *   out        receives the run handle, which owns the device state.
+ * The phases start from the INIT stream.  Work is queued asynchronously.
+ * Errors: OIM_EINVAL, OIM_ENOMEM, OIM_ECUDA, OIM_EUNSUPPORTED (form not
+ * available for this problem, e.g. the resident form for a graph too large for
+ * shared memory).
+ */
+int oim_run(oim_problem_t p, const float* K, const float* Ks, const float* Kn, float dt,
+            int64_t steps, int32_t replicas, uint64_t seed, const oim_run_opts* opts,
+            oim_run_t* out);
+
+/*
+ * oim_rerun -- simulate again with the buffers, form and options of r, from the
+ * INIT stream of the new seed.  Same arguments and errors as oim_run; steps may
+ * differ.  Lets a caller time or repeat runs without device allocations.
+ */
+int oim_rerun(oim_run_t r, const float* K, const float* Ks, const float* Kn, float dt,
+              int64_t steps, uint64_t seed);
+
+/* Wait for the run's queued work; maps a device-side error word to an error code. */
+int oim_run_sync(oim_run_t r);
+
+/*
+ * oim_readout -- phase threshold (Sec. III-B: nearest stable phase k/q,
+ * spin = floor(q*theta + 1/2) mod q in FP32) of the final phases, and scores.
+ * Every output may be NULL; each non-NULL one is host or device memory.
+ *   spins         int8[graphs][replicas][n_g] (graphs concatenated)
+ *   score         double[graphs][replicas]: q == 2 the cut weight
+ *                 sum_{i<j} w_ij [s_i != s_j]; q >= 3 the conflict weight
+ *                 sum_{i<j} w_ij [s_i == s_j] (exact for integer weights)
+ *   best_replica  int32[graphs]: replica with the largest cut (smallest
+ *                 conflict weight), lowest index on ties
+ *   trace         double[graphs][n_readouts][replicas]: the score of every
+ *                 replica at every readout (n_readouts = steps / readout_every)
+ *   energy        double[graphs][replicas]: Eq. 6 energy
+ *                 sum_{i<j} w_ij cos(2 pi (theta_i - theta_j)) of the final phases
+ * Synchronises the run's stream.  Errors: OIM_ESTATE, OIM_ECUDA, OIM_ETIMEOUT.
+ */
+int oim_readout(oim_run_t r, int8_t* spins, double* score, int32_t* best_replica,
+                double* trace, double* energy);
+
+/* Number of readouts recorded by the last run (steps / readout_every). */
+int oim_run_info(oim_run_t r, int64_t* steps, int32_t* replicas, int64_t* n_readouts,
+                 int32_t* form, int32_t* precision);
+
+/*
+ * oim_get_phases -- copy the final phases, float[graphs][replicas][n_g] in
+ * [0,1), to host or device memory.  Synchronises.  Errors: OIM_ESTATE, OIM_ECUDA.
+ */
+int oim_get_phases(oim_run_t r, float* theta);
+
+/*
+ * oim_debug_derivative -- the drift of Eq. 5 for given phases of one graph,
+ * f_i = K sum_j w_ij sin(2 pi (theta_i - theta_j)) - Ks sin(2 pi q theta_i),
+ * evaluated with the kernels' trig-cache identity in FP32.
+ *   theta  float[replicas][n] (host or device), f_out float[replicas][n].
+ * Synchronous.  Errors: OIM_EINVAL (batch problem), OIM_ECUDA.
+ */
+int oim_debug_derivative(oim_problem_t p, const float* theta, int32_t replicas, float K, float Ks,
+                         float* f_out);
+
+void oim_destroy_run(oim_run_t r);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OIM_H */

@@ -79,8 +79,8 @@ def _load():
             "orc_scores": (None, [_i32, _i32, _vp, _vp, _vp, _i32, _vp, _vp]),
             "orc_energy": (None, [_i32, _vp, _vp, _vp, _i32, _vp, _vp]),
             "orc_lyapunov": (_dbl, [_i32, _i32, _vp, _vp, _vp, _vp, _dbl, _dbl]),
-            "orc_run": (_i32, [_i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _dbl, _i64, _i32, _u64,
-                               _u32, _i32, _vp, _i64, _vp, _i32]),
+            "orc_run": (_i32, [_i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _dbl, _i64, _i32, _i64,
+                               _u64, _u32, _i32, _vp, _i64, _vp, _i32]),
             "orc_bruteforce_maxcut": (_dbl, [_i32, _vp, _vp, _vp, _vp]),
             "orc_bruteforce_min_conflicts": (_dbl, [_i32, _i32, _vp, _vp, _vp, _vp]),
             "orc_adjoint": (_i32, [_i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _dbl, _i64, _i32,
@@ -167,8 +167,11 @@ def derivative(g, q: int, theta: np.ndarray, K: float, Ks: float) -> np.ndarray:
 
 
 def run(g, q: int, K, Ks, Kn, dt: float, T: int, R: int, seed: int, graph: int = 0,
-        theta0: np.ndarray | None = None, readout_every: int = 0, nthreads: int = 0):
-    """Simulate R replicas for T steps.  Returns (theta[R, n], trace[R, T//readout_every])."""
+        theta0: np.ndarray | None = None, readout_every: int = 0, nthreads: int = 0,
+        replica_offset: int = 0):
+    """Simulate replicas replica_offset .. replica_offset+R-1 for T steps.
+
+    Returns (theta[R, n], trace[R, T//readout_every])."""
     g = Graph.of(g)
     K = np.ascontiguousarray(np.broadcast_to(np.asarray(K, dtype=np.float64), (T,)))
     Ks = np.ascontiguousarray(np.broadcast_to(np.asarray(Ks, dtype=np.float64), (T,)))
@@ -181,8 +184,8 @@ def run(g, q: int, K, Ks, Kn, dt: float, T: int, R: int, seed: int, graph: int =
     nro = T // readout_every if readout_every > 0 else 0
     trace = np.zeros((R, max(nro, 1)), dtype=np.float64)
     rc = _load().orc_run(g.n, q, _p(g.row_ptr), _p(g.col), _p(g.w), _p(K), _p(Ks), _p(Kn),
-                         float(dt), int(T), int(R), int(seed), int(graph), init_given, _p(theta),
-                         int(readout_every), _p(trace), int(nthreads))
+                         float(dt), int(T), int(R), int(replica_offset), int(seed), int(graph),
+                         init_given, _p(theta), int(readout_every), _p(trace), int(nthreads))
     if rc != 0:
         raise RuntimeError(f"orc_run failed with {rc}")
     return theta, trace[:, :nro]

@@ -260,18 +260,22 @@ double orc_lyapunov(int32_t n, int32_t q, const int64_t* row_ptr, const int32_t*
     return K / ORC_TWO_PI * E - Ks / (ORC_TWO_PI * (double)q) * shil;
 }
 
-/* Full simulation of R replicas for T steps (Algorithm 1).  theta is [R][n]; when
- * init_given is zero it is first filled from the INIT stream.  Every
+/* Full simulation of R replicas for T steps (Algorithm 1).  Row r of theta[R][n]
+ * is replica r0 + r of the run (its random streams use that index); when
+ * init_given is zero theta is first filled from the INIT stream.  Every
  * readout_every steps (after the update of step t with (t+1) % readout_every == 0)
  * the FP64 readout and its score are written to trace[r*n_readouts + k].
  * Replicas are independent and run in parallel on nthreads host threads. */
 int orc_run(int32_t n, int32_t q, const int64_t* row_ptr, const int32_t* col, const double* w,
             const double* K, const double* Ks, const double* Kn, double dt, int64_t T,
-            int32_t R, uint64_t seed, uint32_t graph, int32_t init_given, double* theta,
-            int64_t readout_every, double* trace, int32_t nthreads)
+            int32_t R, int64_t r0, uint64_t seed, uint32_t graph, int32_t init_given,
+            double* theta, int64_t readout_every, double* trace, int32_t nthreads)
 {
-    if (n <= 0 || q < 2 || R <= 0 || T < 0) return -1;
-    if (!init_given) orc_init_phases(n, R, seed, graph, theta);
+    if (n <= 0 || q < 2 || R <= 0 || T < 0 || r0 < 0) return -1;
+    if (!init_given)
+        for (int32_t r = 0; r < R; ++r)
+            for (int32_t i = 0; i < n; ++i)
+                theta[(int64_t)r * n + i] = orc_init_phase(seed, graph, i, r0 + r);
     int64_t n_readouts = (readout_every > 0) ? T / readout_every : 0;
     int failed = 0;
 #ifdef _OPENMP
@@ -287,7 +291,7 @@ int orc_run(int32_t n, int32_t q, const int64_t* row_ptr, const int32_t* col, co
         } else {
             int64_t k = 0;
             for (int64_t t = 0; t < T; ++t) {
-                orc_step_one(n, q, row_ptr, col, w, K[t], Ks[t], Kn[t], dt, seed, graph, t, r,
+                orc_step_one(n, q, row_ptr, col, w, K[t], Ks[t], Kn[t], dt, seed, graph, t, r0 + r,
                              th, scratch);
                 if (readout_every > 0 && (t + 1) % readout_every == 0 && trace) {
                     for (int32_t i = 0; i < n; ++i) sp[i] = (int8_t)orc_spin_f64(th[i], q);

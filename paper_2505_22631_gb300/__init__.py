@@ -1,0 +1,170 @@
+"""GB300 (sm_103a) simulator of the oscillator Ising/Potts machine (arXiv 2505.22631).
+
+The C ABI lives in ``include/oim.h`` / ``liboim.so``; ``capi`` binds every entry
+point under the same name.  ``Problem`` and ``Run`` below are convenience
+wrappers that own the handles and marshal numpy arrays and torch tensors.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import capi
+from .capi import (FORMS, PRECISIONS, OimError, oim_create_batch, oim_create_problem,
+                   oim_debug_derivative, oim_default_opts, oim_destroy_problem, oim_destroy_run,
+                   oim_get_phases, oim_last_error, oim_problem_info, oim_readout, oim_rerun,
+                   oim_run, oim_run_info, oim_run_sync, oim_version)
+
+__all__ = [
+    "Problem", "Run", "simulate", "OimError", "FORMS", "PRECISIONS", "oim_create_problem",
+    "oim_create_batch", "oim_problem_info", "oim_destroy_problem", "oim_run", "oim_rerun",
+    "oim_run_sync", "oim_readout", "oim_run_info", "oim_get_phases", "oim_debug_derivative",
+    "oim_destroy_run", "oim_default_opts", "oim_version", "oim_last_error",
+]
+
+
+class Problem:
+    """One graph (or a batch of graphs) uploaded to the GPU."""
+
+    def __init__(self, handle, graphs: int, sizes: list[int], q: int, members=()):
+        self.handle = handle
+        self.graphs = graphs
+        self.sizes = list(sizes)
+        self.q = q
+        self._members = list(members)   # keep batch members alive for their lifetime
+
+    @classmethod
+    def from_csr(cls, n, q, row_ptr, col, w=None, flags=0) -> "Problem":
+        row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64) if isinstance(row_ptr, np.ndarray) else row_ptr
+        col = np.ascontiguousarray(col, dtype=np.int32) if isinstance(col, np.ndarray) else col
+        if isinstance(w, np.ndarray):
+            w = np.ascontiguousarray(w, dtype=np.float32)
+        nnz = int(col.shape[0])
+        h = oim_create_problem(n, q, nnz, row_ptr, col, w, flags)
+        return cls(h, 1, [int(n)], q)
+
+    @classmethod
+    def from_graph(cls, g, q: int) -> "Problem":
+        return cls.from_csr(g.n, q, g.row_ptr, g.col, g.w)
+
+    @classmethod
+    def batch(cls, problems: list["Problem"]) -> "Problem":
+        h = oim_create_batch([p.handle for p in problems])
+        return cls(h, len(problems), [s for p in problems for s in p.sizes], problems[0].q,
+                   problems)
+
+    @property
+    def nodes(self) -> int:
+        return sum(self.sizes)
+
+    def close(self):
+        if self.handle:
+            oim_destroy_problem(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _stream_ptr(stream):
+    if stream is not None:
+        return int(getattr(stream, "cuda_stream", stream))
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return int(torch.cuda.current_stream().cuda_stream)
+    except Exception:
+        pass
+    return 0
+
+
+def _schedule(x, graphs, steps):
+    """Broadcast a scalar / [steps] / [graphs, steps] schedule to float32 [graphs*steps]."""
+    if hasattr(x, "data_ptr") and not isinstance(x, np.ndarray):
+        return x   # torch tensor already laid out by the caller
+    a = np.asarray(x, dtype=np.float32)
+    return np.ascontiguousarray(np.broadcast_to(a, (graphs, steps)) if a.ndim <= 1 or a.shape[0] == 1
+                                else a.reshape(graphs, steps)).reshape(-1)
+
+
+class Run:
+    """A simulation of R replicas of every graph of a Problem (owns device state)."""
+
+    def __init__(self, problem: Problem, K, Ks, Kn, dt, steps, replicas, seed, form="auto",
+                 precision="auto", readout_every=0, stream=None, use_graph=True,
+                 replicas_per_block=0, threads_per_block=0):
+        self.problem = problem
+        o = oim_default_opts()
+        o.form = FORMS[form] if isinstance(form, str) else int(form)
+        o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        o.readout_every = int(readout_every)
+        o.stream = _stream_ptr(stream)
+        o.use_graph = int(bool(use_graph))
+        o.replicas_per_block = int(replicas_per_block)
+        o.threads_per_block = int(threads_per_block)
+        self.opts = o
+        G = problem.graphs
+        self._sched = [_schedule(s, G, steps) for s in (K, Ks, Kn)]
+        self.handle = oim_run(problem.handle, *self._sched, dt, steps, replicas, seed, o)
+        self.replicas = int(replicas)
+
+    def rerun(self, K, Ks, Kn, dt, steps, seed):
+        G = self.problem.graphs
+        self._sched = [_schedule(s, G, steps) for s in (K, Ks, Kn)]
+        oim_rerun(self.handle, *self._sched, dt, steps, seed)
+
+    def info(self) -> dict:
+        steps, reps, nro, form, prec = oim_run_info(self.handle)
+        return {"steps": steps, "replicas": reps, "n_readouts": nro, "form": form,
+                "precision": prec}
+
+    def sync(self):
+        oim_run_sync(self.handle)
+
+    def readout(self, spins=True, trace=True, energy=False) -> dict:
+        """Host copies: spins [graphs][R][n_g] flattened, score [G, R], best [G], trace, energy."""
+        G, R = self.problem.graphs, self.replicas
+        nro = self.info()["n_readouts"]
+        out = {"score": np.zeros((G, R)), "best_replica": np.zeros(G, dtype=np.int32)}
+        if spins:
+            out["spins"] = np.zeros(self.problem.nodes * R, dtype=np.int8)
+        if trace and nro > 0:
+            out["trace"] = np.zeros((G, nro, R))
+        if energy:
+            out["energy"] = np.zeros((G, R))
+        oim_readout(self.handle, out.get("spins"), out["score"], out["best_replica"],
+                    out.get("trace"), out.get("energy"))
+        if spins:
+            flat, parts, off = out["spins"], [], 0
+            for n in self.problem.sizes:
+                parts.append(flat[off:off + n * R].reshape(R, n))
+                off += n * R
+            out["spins"] = parts
+        return out
+
+    def phases(self) -> list[np.ndarray]:
+        R = self.replicas
+        flat = np.zeros(self.problem.nodes * R, dtype=np.float32)
+        oim_get_phases(self.handle, flat)
+        parts, off = [], 0
+        for n in self.problem.sizes:
+            parts.append(flat[off:off + n * R].reshape(R, n))
+            off += n * R
+        return parts
+
+    def close(self):
+        if self.handle:
+            oim_destroy_run(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def simulate(problem: Problem, K, Ks, Kn, dt, steps, replicas, seed, **kw) -> Run:
+    return Run(problem, K, Ks, Kn, dt, steps, replicas, seed, **kw)

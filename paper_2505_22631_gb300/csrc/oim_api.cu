@@ -1,0 +1,710 @@
+// oim_api.cu -- the C ABI of liboim (declared in include/oim.h): argument
+// validation, device allocation, choice of the integration form and the launch
+// sequence of a run.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "oim_internal.h"
+
+namespace oim {
+
+static thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+    g_last_error = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? OIM_ENOMEM : OIM_ECUDA;
+}
+
+// implemented in the kernel translation units
+cudaError_t launch_score(const oim_run_s& r, const float* theta, int64_t k, cudaStream_t s);
+cudaError_t launch_finalize(const oim_run_s& r, int64_t k, double* score, cudaStream_t s);
+cudaError_t launch_energy_of(const oim_run_s& r, const float* theta, double* energy, cudaStream_t s);
+cudaError_t launch_gather(const oim_run_s& r, const float* theta, int8_t* spins, float* th_out,
+                          cudaStream_t s);
+cudaError_t launch_resident_impl(const oim_run_s& r, const int4* d_items, cudaStream_t s);
+cudaError_t launch_derivative(const oim_problem_s& p, const float* theta, int32_t R, float K,
+                              float Ks, float* f, cudaStream_t s);
+size_t resident_cache_bytes(int32_t prec);
+
+}  // namespace oim
+
+using namespace oim;
+
+#define OIM_CUDA(call, what)                          \
+    do {                                              \
+        cudaError_t e__ = (call);                     \
+        if (e__ != cudaSuccess) return cuda_fail(e__, what); \
+    } while (0)
+
+namespace {
+
+template <typename T>
+cudaError_t dev_alloc(T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+}
+
+template <typename T>
+void dev_free(T*& p) {
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+// True when p is device (or managed) memory.  Without a usable driver every
+// pointer is taken as host memory, so argument validation runs anywhere.
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+}
+
+// copy count elements from host or device memory into a host vector
+template <typename T>
+cudaError_t fetch(std::vector<T>& out, const T* src, size_t count) {
+    out.resize(count);
+    if (count == 0) return cudaSuccess;
+    if (!is_device_ptr(src)) {
+        std::memcpy(out.data(), src, count * sizeof(T));
+        return cudaSuccess;
+    }
+    return cudaMemcpy(out.data(), src, count * sizeof(T), cudaMemcpyDeviceToHost);
+}
+
+void free_problem(oim_problem_s* p);
+
+int upload_problem(oim_problem_s* p) {
+    OIM_CUDA(dev_alloc(&p->d_rowp, p->h_rowp.size()), "cudaMalloc(row_ptr)");
+    OIM_CUDA(dev_alloc(&p->d_col, p->h_col.size()), "cudaMalloc(col)");
+    OIM_CUDA(dev_alloc(&p->d_w, p->h_w.size()), "cudaMalloc(w)");
+    OIM_CUDA(dev_alloc(&p->d_node_graph, (size_t)p->nodes), "cudaMalloc(node_graph)");
+    OIM_CUDA(dev_alloc(&p->d_graphs, p->graphs.size()), "cudaMalloc(graphs)");
+    std::vector<int32_t> ng((size_t)p->nodes);
+    for (int g = 0; g < p->G; ++g)
+        std::fill(ng.begin() + p->graphs[g].node_off,
+                  ng.begin() + p->graphs[g].node_off + p->graphs[g].n, g);
+    OIM_CUDA(cudaMemcpy(p->d_rowp, p->h_rowp.data(), p->h_rowp.size() * 4, cudaMemcpyHostToDevice),
+             "upload row_ptr");
+    if (!p->h_col.empty())
+        OIM_CUDA(cudaMemcpy(p->d_col, p->h_col.data(), p->h_col.size() * 4, cudaMemcpyHostToDevice),
+                 "upload col");
+    if (!p->h_w.empty())
+        OIM_CUDA(cudaMemcpy(p->d_w, p->h_w.data(), p->h_w.size() * 4, cudaMemcpyHostToDevice),
+                 "upload w");
+    OIM_CUDA(cudaMemcpy(p->d_node_graph, ng.data(), ng.size() * 4, cudaMemcpyHostToDevice),
+             "upload node_graph");
+    OIM_CUDA(cudaMemcpy(p->d_graphs, p->graphs.data(), p->graphs.size() * sizeof(GraphDev),
+                        cudaMemcpyHostToDevice),
+             "upload graphs");
+    p->uploaded = true;
+    return OIM_OK;
+}
+
+int ensure_uploaded(oim_problem_s* p) {
+    if (p->uploaded) return OIM_OK;
+    int rc = upload_problem(p);
+    if (rc != OIM_OK) free_problem(p);
+    return rc;
+}
+
+void free_problem(oim_problem_s* p) {
+    p->uploaded = false;
+    dev_free(p->d_rowp);
+    dev_free(p->d_col);
+    dev_free(p->d_w);
+    dev_free(p->d_node_graph);
+    dev_free(p->d_graphs);
+}
+
+// Pack columns: global node index, and for +-1 weights the sign in bit 31.
+void pack_columns(oim_problem_s* p) {
+    p->h_col.resize(p->h_col_plain.size());
+    for (size_t e = 0; e < p->h_col_plain.size(); ++e) {
+        uint32_t c = (uint32_t)p->h_col_plain[e];
+        if (p->unit_weights && p->h_w[e] < 0.f) c |= kSignBit;
+        p->h_col[e] = c;
+    }
+}
+
+void free_run_buffers(oim_run_s* r) {
+    dev_free(r->d_theta[0]);
+    dev_free(r->d_theta[1]);
+    if (r->d_cs[0]) cudaFree(r->d_cs[0]);
+    if (r->d_cs[1]) cudaFree(r->d_cs[1]);
+    r->d_cs[0] = r->d_cs[1] = nullptr;
+    dev_free(r->d_sched);
+    dev_free(r->d_spins);
+    dev_free(r->d_trace);
+    dev_free(r->d_score);
+    dev_free(r->d_energy);
+    dev_free(r->d_err);
+    dev_free(r->d_t0);
+    dev_free(r->d_items);
+    if (r->chunk_exec) cudaGraphExecDestroy(r->chunk_exec);
+    r->chunk_exec = nullptr;
+}
+
+int validate_schedule_args(float dt, int64_t steps) {
+    if (!(dt > 0.f) || !std::isfinite(dt)) return fail(OIM_EINVAL, "dt must be finite and > 0");
+    if (steps < 0 || steps >= ((int64_t)1 << 32)) return fail(OIM_EINVAL, "steps out of range");
+    return OIM_OK;
+}
+
+// (Re)allocate the buffers whose size depends on steps / readouts.
+int ensure_step_buffers(oim_run_s* r, int64_t steps) {
+    const int G = r->p->G;
+    const int64_t n_ro = r->readout_every > 0 ? steps / r->readout_every : 0;
+    if (steps > r->steps_cap || !r->d_sched) {
+        dev_free(r->d_sched);
+        r->steps_cap = std::max<int64_t>(steps, 1);
+        OIM_CUDA(dev_alloc(&r->d_sched, (size_t)3 * G * r->steps_cap), "cudaMalloc(schedules)");
+    }
+    const int64_t ro_need = n_ro + 1;   // one extra row for the final scores
+    if (ro_need > r->readouts_cap || !r->d_trace) {
+        dev_free(r->d_trace);
+        r->readouts_cap = ro_need;
+        OIM_CUDA(dev_alloc(&r->d_trace, (size_t)G * r->readouts_cap * r->R_pad), "cudaMalloc(trace)");
+    }
+    return OIM_OK;
+}
+
+int choose_form(oim_run_s* r) {
+    int form = r->opts.form;
+    int prec = r->opts.precision;
+    if (form < OIM_FORM_AUTO || form > OIM_FORM_GEMM) return fail(OIM_EINVAL, "unknown form");
+    if (prec < OIM_PREC_AUTO || prec > OIM_PREC_FP16) return fail(OIM_EINVAL, "unknown precision");
+    if (form == OIM_FORM_GEMM) return fail(OIM_EUNSUPPORTED, "the tensor-core form is not built");
+    if (prec == OIM_PREC_AUTO) prec = OIM_PREC_FP32;
+    if (form == OIM_FORM_AUTO) {
+        int32_t k, th, it;
+        size_t sm;
+        form = resident_shape(*r->p, r->R_pad, prec, r->opts.replicas_per_block,
+                              r->opts.threads_per_block, &k, &th, &it, &sm) == cudaSuccess
+                   ? OIM_FORM_RESIDENT
+                   : OIM_FORM_STREAM;
+    }
+    if (form == OIM_FORM_STREAM && prec != OIM_PREC_FP32)
+        return fail(OIM_EUNSUPPORTED, "the stream form stores its cache in FP32 only");
+    r->form = form;
+    r->prec = prec;
+    if (form == OIM_FORM_RESIDENT) {
+        cudaError_t e = resident_shape(*r->p, r->R_pad, prec, r->opts.replicas_per_block,
+                                       r->opts.threads_per_block, &r->res_k, &r->res_threads,
+                                       &r->res_items, &r->res_smem);
+        if (e != cudaSuccess)
+            return fail(OIM_EUNSUPPORTED,
+                        "resident form: a replica pair of the largest graph does not fit in "
+                        "shared memory, or the requested shape is invalid");
+    }
+    return OIM_OK;
+}
+
+int allocate_run(oim_run_s* r) {
+    const size_t state = (size_t)r->p->nodes * r->R_pad;
+    const int G = r->p->G;
+    OIM_CUDA(dev_alloc(&r->d_theta[0], state), "cudaMalloc(theta)");
+    OIM_CUDA(dev_alloc(&r->d_spins, state), "cudaMalloc(spins)");
+    OIM_CUDA(dev_alloc(&r->d_score, (size_t)G * r->R_pad), "cudaMalloc(score)");
+    OIM_CUDA(dev_alloc(&r->d_energy, (size_t)G * r->R_pad), "cudaMalloc(energy)");
+    OIM_CUDA(dev_alloc(&r->d_err, 1), "cudaMalloc(err)");
+    OIM_CUDA(dev_alloc(&r->d_t0, 1), "cudaMalloc(t0)");
+    if (r->form == OIM_FORM_STREAM) {
+        OIM_CUDA(dev_alloc(&r->d_theta[1], state), "cudaMalloc(theta)");
+        OIM_CUDA(cudaMalloc(&r->d_cs[0], state * sizeof(float2)), "cudaMalloc(cs)");
+        OIM_CUDA(cudaMalloc(&r->d_cs[1], state * sizeof(float2)), "cudaMalloc(cs)");
+    }
+    if (r->form == OIM_FORM_RESIDENT) {
+        std::vector<int4> items;
+        for (int g = 0; g < G; ++g)
+            for (int r0 = 0; r0 < r->R_pad; r0 += r->res_k)
+                items.push_back(make_int4(g, r0, std::min(r->res_k, r->R_pad - r0), 0));
+        r->res_items = (int32_t)items.size();
+        OIM_CUDA(dev_alloc(&r->d_items, items.size()), "cudaMalloc(items)");
+        OIM_CUDA(cudaMemcpy(r->d_items, items.data(), items.size() * sizeof(int4),
+                            cudaMemcpyHostToDevice),
+                 "upload items");
+    }
+    OIM_CUDA(cudaMemset(r->d_err, 0, sizeof(int32_t)), "cudaMemset(err)");
+    return OIM_OK;
+}
+
+// Queue the stream form: init, then every step, with a score pass after each
+// readout step.  When capture is on, the whole sequence is recorded once into a
+// CUDA graph (kernel arguments baked in) and replayed on later identical runs.
+int enqueue_stream_form(oim_run_s* r) {
+    auto body = [&](cudaStream_t s) -> cudaError_t {
+        cudaError_t e = launch_init_stream(*r, s);
+        for (int64_t t = 0; t < r->steps && e == cudaSuccess; ++t) {
+            e = launch_step_stream(*r, t, nullptr, s);
+            if (e == cudaSuccess && r->readout_every > 0 && (t + 1) % r->readout_every == 0)
+                e = launch_score(*r, r->d_theta[(t + 1) & 1], (t + 1) / r->readout_every - 1, s);
+        }
+        return e;
+    };
+    if (!r->opts.use_graph) {
+        cudaError_t e = body(r->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "stream-form launch");
+        return OIM_OK;
+    }
+    const bool same = r->chunk_exec && r->graph_steps == r->steps && r->graph_seed == r->seed &&
+                      r->graph_dt == r->dt;
+    if (!same) {
+        if (r->chunk_exec) cudaGraphExecDestroy(r->chunk_exec);
+        r->chunk_exec = nullptr;
+        // record on a private stream (the caller's may be the legacy default stream,
+        // which cannot be captured); the graph is then launched on the caller's stream
+        cudaStream_t cap = nullptr;
+        OIM_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "create capture stream");
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            e = body(cap);
+            cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+            if (e == cudaSuccess) e = e2;
+        }
+        cudaStreamDestroy(cap);
+        if (e != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return cuda_fail(e, "capture stream form");
+        }
+        e = cudaGraphInstantiate(&r->chunk_exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(e, "instantiate graph");
+        r->graph_steps = r->steps;
+        r->graph_seed = r->seed;
+        r->graph_dt = r->dt;
+    }
+    OIM_CUDA(cudaGraphLaunch(r->chunk_exec, r->stream), "graph launch");
+    return OIM_OK;
+}
+
+int execute(oim_run_s* r, const float* K, const float* Ks, const float* Kn) {
+    const int G = r->p->G;
+    cudaStream_t s = r->stream;
+    const size_t row = (size_t)G * r->steps;
+    // schedules are [G][steps] per array; the device copy keeps the stride steps_cap
+    for (int a = 0; a < 3; ++a) {
+        const float* src = a == 0 ? K : (a == 1 ? Ks : Kn);
+        if (r->steps == 0) break;
+        float* dst = r->d_sched + (size_t)a * G * r->steps_cap;
+        if (r->steps_cap == r->steps) {
+            OIM_CUDA(cudaMemcpyAsync(dst, src, row * sizeof(float), cudaMemcpyDefault, s),
+                     "copy schedule");
+        } else {
+            OIM_CUDA(cudaMemcpy2DAsync(dst, r->steps_cap * sizeof(float), src,
+                                       r->steps * sizeof(float), r->steps * sizeof(float), G,
+                                       cudaMemcpyDefault, s),
+                     "copy schedule");
+        }
+    }
+    OIM_CUDA(cudaMemsetAsync(r->d_trace, 0, (size_t)G * r->readouts_cap * r->R_pad * sizeof(double), s),
+             "clear trace");
+    if (r->form == OIM_FORM_RESIDENT) {
+        cudaError_t e = launch_resident_impl(*r, r->d_items, s);
+        if (e != cudaSuccess) return cuda_fail(e, "resident launch");
+        r->final_buf = 0;
+    } else {
+        int rc = enqueue_stream_form(r);
+        if (rc != OIM_OK) return rc;
+        r->final_buf = (int)(r->steps & 1);
+    }
+    r->ran = true;
+    return OIM_OK;
+}
+
+int set_device_of(const oim_problem_s* p) {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != p->device) OIM_CUDA(cudaSetDevice(p->device), "cudaSetDevice");
+    return OIM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void oim_default_opts(oim_run_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->form = OIM_FORM_AUTO;
+    o->precision = OIM_PREC_AUTO;
+    o->readout_every = 0;
+    o->stream = nullptr;
+    o->use_graph = 1;
+}
+
+const char* oim_version(void) { return "liboim 0.1 (sm_103a)"; }
+
+const char* oim_last_error(void) { return g_last_error.c_str(); }
+
+int oim_create_problem(int32_t n, int32_t q, int64_t nnz, const int64_t* row_ptr,
+                       const int32_t* col_idx, const float* weights, uint32_t flags,
+                       oim_problem_t* out) {
+    g_last_error.clear();
+    if (!out) return fail(OIM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n < 1 || n >= (1 << 30)) return fail(OIM_EINVAL, "n out of range");
+    if (q < 2 || q > 16) return fail(OIM_EINVAL, "q must be in [2, 16]");
+    if (nnz < 0 || nnz >= ((int64_t)1 << 31)) return fail(OIM_EINVAL, "nnz out of range");
+    if (!row_ptr || (nnz > 0 && !col_idx)) return fail(OIM_EINVAL, "NULL CSR array");
+    std::vector<int64_t> rp;
+    std::vector<int32_t> ci;
+    std::vector<float> w;
+    OIM_CUDA(fetch(rp, row_ptr, (size_t)n + 1), "read row_ptr");
+    OIM_CUDA(fetch(ci, col_idx, (size_t)nnz), "read col_idx");
+    if (weights) {
+        OIM_CUDA(fetch(w, weights, (size_t)nnz), "read weights");
+    } else {
+        w.assign((size_t)nnz, 1.0f);
+    }
+    if (rp[0] != 0 || rp[n] != nnz) return fail(OIM_EINVAL, "row_ptr[0] must be 0 and row_ptr[n] = nnz");
+    int32_t max_deg = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        if (rp[i + 1] < rp[i]) return fail(OIM_EINVAL, "row_ptr must be nondecreasing");
+        max_deg = std::max<int32_t>(max_deg, (int32_t)(rp[i + 1] - rp[i]));
+        for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
+            const int32_t j = ci[e];
+            if (j < 0 || j >= n) return fail(OIM_EINVAL, "column index out of range");
+            if (j == i) return fail(OIM_EINVAL, "diagonal entry (self coupling) in row " + std::to_string(i));
+            if (e > rp[i] && ci[e - 1] >= j) return fail(OIM_EINVAL, "columns must increase within a row");
+            if (!std::isfinite(w[e])) return fail(OIM_EINVAL, "non-finite weight");
+        }
+    }
+    if (!(flags & OIM_FLAG_SKIP_SYMMETRY_CHECK)) {
+        for (int32_t i = 0; i < n; ++i)
+            for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
+                const int32_t j = ci[e];
+                const int32_t* b = ci.data() + rp[j];
+                const int32_t* en = ci.data() + rp[j + 1];
+                const int32_t* f = std::lower_bound(b, en, i);
+                if (f == en || *f != i || w[f - ci.data()] != w[e])
+                    return fail(OIM_EINVAL, "coupling matrix is not symmetric at (" + std::to_string(i) +
+                                                ", " + std::to_string(j) + ")");
+            }
+    }
+    oim_problem_s* p = new (std::nothrow) oim_problem_s();
+    if (!p) return fail(OIM_ENOMEM, "host allocation");
+    cudaGetDevice(&p->device);
+    p->q = q;
+    p->G = 1;
+    p->nodes = n;
+    p->nnz = nnz;
+    p->max_n = n;
+    GraphDev gd{};
+    gd.n = n;
+    gd.node_off = 0;
+    gd.edge_off = 0;
+    gd.max_deg = max_deg;
+    double wt = 0.0;
+    for (int32_t i = 0; i < n; ++i)
+        for (int64_t e = rp[i]; e < rp[i + 1]; ++e)
+            if (ci[e] > i) wt += (double)w[e];
+    gd.wtot = wt;
+    p->graphs.push_back(gd);
+    p->h_rowp.resize((size_t)n + 1);
+    for (int32_t i = 0; i <= n; ++i) p->h_rowp[i] = (int32_t)rp[i];
+    p->h_col_plain = ci;
+    p->h_w = w;
+    for (float x : w) {
+        if (std::fabs(x) != 1.0f) p->unit_weights = false;
+        if (x != std::floor(x)) p->integer_weights = false;
+    }
+    pack_columns(p);
+    if (!(flags & OIM_FLAG_DEFER_UPLOAD)) {
+        int rc = upload_problem(p);
+        if (rc != OIM_OK) {
+            free_problem(p);
+            delete p;
+            return rc;
+        }
+    }
+    *out = p;
+    return OIM_OK;
+}
+
+int oim_create_batch(int32_t count, const oim_problem_t* problems, oim_problem_t* out) {
+    g_last_error.clear();
+    if (!out) return fail(OIM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (count < 1 || !problems) return fail(OIM_EINVAL, "count must be >= 1");
+    for (int32_t k = 0; k < count; ++k) {
+        if (!problems[k]) return fail(OIM_EINVAL, "NULL problem in batch");
+        if (problems[k]->G != 1) return fail(OIM_EINVAL, "a batch cannot contain a batch");
+        if (problems[k]->q != problems[0]->q) return fail(OIM_EINVAL, "mixed q in batch");
+    }
+    int64_t nodes = 0, nnz = 0;
+    for (int32_t k = 0; k < count; ++k) {
+        nodes += problems[k]->nodes;
+        nnz += problems[k]->nnz;
+    }
+    if (nodes >= (1 << 30) || nnz >= ((int64_t)1 << 31)) return fail(OIM_EINVAL, "batch too large");
+    oim_problem_s* p = new (std::nothrow) oim_problem_s();
+    if (!p) return fail(OIM_ENOMEM, "host allocation");
+    cudaGetDevice(&p->device);
+    p->q = problems[0]->q;
+    p->G = count;
+    p->nodes = nodes;
+    p->nnz = nnz;
+    p->h_rowp.reserve((size_t)nodes + 1);
+    p->h_rowp.push_back(0);
+    int64_t noff = 0, eoff = 0;
+    for (int32_t k = 0; k < count; ++k) {
+        const oim_problem_s* s = problems[k];
+        GraphDev gd = s->graphs[0];
+        gd.node_off = (int32_t)noff;
+        gd.edge_off = (int32_t)eoff;
+        p->graphs.push_back(gd);
+        p->max_n = std::max(p->max_n, gd.n);
+        for (int32_t i = 0; i < gd.n; ++i) p->h_rowp.push_back((int32_t)(eoff + s->h_rowp[i + 1]));
+        for (size_t e = 0; e < s->h_col_plain.size(); ++e) {
+            p->h_col_plain.push_back((int32_t)(s->h_col_plain[e] + noff));
+            p->h_w.push_back(s->h_w[e]);
+        }
+        p->unit_weights = p->unit_weights && s->unit_weights;
+        p->integer_weights = p->integer_weights && s->integer_weights;
+        noff += gd.n;
+        eoff += s->nnz;
+    }
+    pack_columns(p);
+    int rc = upload_problem(p);
+    if (rc != OIM_OK) {
+        free_problem(p);
+        delete p;
+        return rc;
+    }
+    *out = p;
+    return OIM_OK;
+}
+
+int oim_problem_info(oim_problem_t p, int32_t* graphs, int64_t* nodes, int64_t* nnz, int32_t* q) {
+    if (!p) return fail(OIM_EINVAL, "NULL problem");
+    if (graphs) *graphs = p->G;
+    if (nodes) *nodes = p->nodes;
+    if (nnz) *nnz = p->nnz;
+    if (q) *q = p->q;
+    return OIM_OK;
+}
+
+void oim_destroy_problem(oim_problem_t p) {
+    if (!p) return;
+    free_problem(p);
+    delete p;
+}
+
+int oim_run(oim_problem_t p, const float* K, const float* Ks, const float* Kn, float dt,
+            int64_t steps, int32_t replicas, uint64_t seed, const oim_run_opts* opts,
+            oim_run_t* out) {
+    g_last_error.clear();
+    if (!out) return fail(OIM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!p) return fail(OIM_EINVAL, "NULL problem");
+    if (replicas < 1 || replicas > (1 << 20)) return fail(OIM_EINVAL, "replicas out of range");
+    int rc = validate_schedule_args(dt, steps);
+    if (rc != OIM_OK) return rc;
+    if (steps > 0 && (!K || !Ks || !Kn)) return fail(OIM_EINVAL, "NULL schedule");
+    oim_run_opts o;
+    if (opts) o = *opts; else oim_default_opts(&o);
+    if (o.readout_every < 0) return fail(OIM_EINVAL, "readout_every must be >= 0");
+    rc = set_device_of(p);
+    if (rc != OIM_OK) return rc;
+    rc = ensure_uploaded(p);
+    if (rc != OIM_OK) return rc;
+    oim_run_s* r = new (std::nothrow) oim_run_s();
+    if (!r) return fail(OIM_ENOMEM, "host allocation");
+    r->p = p;
+    r->opts = o;
+    r->R = replicas;
+    r->R_pad = (replicas + 3) & ~3;
+    r->readout_every = o.readout_every;
+    r->stream = static_cast<cudaStream_t>(o.stream);
+    r->device = p->device;
+    r->steps = steps;
+    r->seed = seed;
+    r->dt = dt;
+    r->n_readouts = r->readout_every > 0 ? steps / r->readout_every : 0;
+    rc = choose_form(r);
+    if (rc == OIM_OK) rc = allocate_run(r);
+    if (rc == OIM_OK) rc = ensure_step_buffers(r, steps);
+    if (rc == OIM_OK) rc = execute(r, K, Ks, Kn);
+    if (rc != OIM_OK) {
+        free_run_buffers(r);
+        delete r;
+        return rc;
+    }
+    *out = r;
+    return OIM_OK;
+}
+
+int oim_rerun(oim_run_t r, const float* K, const float* Ks, const float* Kn, float dt, int64_t steps,
+              uint64_t seed) {
+    g_last_error.clear();
+    if (!r) return fail(OIM_EINVAL, "NULL run");
+    int rc = validate_schedule_args(dt, steps);
+    if (rc != OIM_OK) return rc;
+    if (steps > 0 && (!K || !Ks || !Kn)) return fail(OIM_EINVAL, "NULL schedule");
+    rc = set_device_of(r->p);
+    if (rc != OIM_OK) return rc;
+    r->steps = steps;
+    r->seed = seed;
+    r->dt = dt;
+    r->n_readouts = r->readout_every > 0 ? steps / r->readout_every : 0;
+    rc = ensure_step_buffers(r, steps);
+    if (rc != OIM_OK) return rc;
+    return execute(r, K, Ks, Kn);
+}
+
+int oim_run_sync(oim_run_t r) {
+    if (!r) return fail(OIM_EINVAL, "NULL run");
+    OIM_CUDA(cudaStreamSynchronize(r->stream), "synchronize");
+    int32_t err = 0;
+    OIM_CUDA(cudaMemcpy(&err, r->d_err, sizeof(err), cudaMemcpyDeviceToHost), "read error word");
+    if (err != 0) return fail(OIM_ETIMEOUT, "a device-side wait gave up (error word " + std::to_string(err) + ")");
+    return OIM_OK;
+}
+
+int oim_run_info(oim_run_t r, int64_t* steps, int32_t* replicas, int64_t* n_readouts, int32_t* form,
+                 int32_t* precision) {
+    if (!r) return fail(OIM_EINVAL, "NULL run");
+    if (steps) *steps = r->steps;
+    if (replicas) *replicas = r->R;
+    if (n_readouts) *n_readouts = r->n_readouts;
+    if (form) *form = r->form;
+    if (precision) *precision = r->prec;
+    return OIM_OK;
+}
+
+int oim_readout(oim_run_t r, int8_t* spins, double* score, int32_t* best_replica, double* trace,
+                double* energy) {
+    g_last_error.clear();
+    if (!r) return fail(OIM_EINVAL, "NULL run");
+    if (!r->ran) return fail(OIM_ESTATE, "run has not executed");
+    int rc = set_device_of(r->p);
+    if (rc != OIM_OK) return rc;
+    cudaStream_t s = r->stream;
+    const int G = r->p->G;
+    const float* theta = r->d_theta[r->final_buf];
+    const int64_t k_final = r->readouts_cap - 1;   // spare row for the final scores
+    if (score || best_replica) {
+        for (int g = 0; g < G; ++g)
+            OIM_CUDA(cudaMemsetAsync(r->d_trace + ((size_t)g * r->readouts_cap + k_final) * r->R_pad, 0,
+                                     (size_t)r->R_pad * sizeof(double), s),
+                     "clear final row");
+        OIM_CUDA(launch_score(*r, theta, k_final, s), "score launch");
+        OIM_CUDA(launch_finalize(*r, k_final, r->d_score, s), "finalize launch");
+    }
+    if (energy) {
+        OIM_CUDA(cudaMemsetAsync(r->d_energy, 0, (size_t)G * r->R_pad * sizeof(double), s), "clear energy");
+        OIM_CUDA(launch_energy_of(*r, theta, r->d_energy, s), "energy launch");
+    }
+    if (spins) OIM_CUDA(launch_gather(*r, theta, r->d_spins, nullptr, s), "gather launch");
+    rc = oim_run_sync(r);
+    if (rc != OIM_OK) return rc;
+    const size_t GR = (size_t)G * r->R;
+    std::vector<double> host_score;
+    if (score || best_replica) {
+        host_score.resize(GR);
+        OIM_CUDA(cudaMemcpy(host_score.data(), r->d_score, GR * sizeof(double), cudaMemcpyDeviceToHost),
+                 "read scores");
+        if (score) OIM_CUDA(cudaMemcpy(score, host_score.data(), GR * sizeof(double), cudaMemcpyDefault),
+                            "write scores");
+        if (best_replica) {
+            std::vector<int32_t> best((size_t)G);
+            for (int g = 0; g < G; ++g) {
+                int b = 0;
+                for (int x = 1; x < r->R; ++x) {
+                    const double v = host_score[(size_t)g * r->R + x], bv = host_score[(size_t)g * r->R + b];
+                    if (r->p->q == 2 ? v > bv : v < bv) b = x;
+                }
+                best[g] = b;
+            }
+            OIM_CUDA(cudaMemcpy(best_replica, best.data(), G * sizeof(int32_t), cudaMemcpyDefault),
+                     "write best replica");
+        }
+    }
+    if (spins)
+        OIM_CUDA(cudaMemcpy(spins, r->d_spins, (size_t)r->p->nodes * r->R, cudaMemcpyDefault), "write spins");
+    if (energy) {
+        std::vector<double> e((size_t)G * r->R_pad), o(GR);
+        OIM_CUDA(cudaMemcpy(e.data(), r->d_energy, e.size() * sizeof(double), cudaMemcpyDeviceToHost),
+                 "read energy");
+        for (int g = 0; g < G; ++g)
+            for (int x = 0; x < r->R; ++x) o[(size_t)g * r->R + x] = e[(size_t)g * r->R_pad + x];
+        OIM_CUDA(cudaMemcpy(energy, o.data(), GR * sizeof(double), cudaMemcpyDefault), "write energy");
+    }
+    if (trace && r->n_readouts > 0) {
+        std::vector<double> raw((size_t)G * r->readouts_cap * r->R_pad);
+        OIM_CUDA(cudaMemcpy(raw.data(), r->d_trace, raw.size() * sizeof(double), cudaMemcpyDeviceToHost),
+                 "read trace");
+        std::vector<double> o((size_t)G * r->n_readouts * r->R);
+        for (int g = 0; g < G; ++g)
+            for (int64_t k = 0; k < r->n_readouts; ++k)
+                for (int x = 0; x < r->R; ++x) {
+                    const double a = raw[((size_t)g * r->readouts_cap + k) * r->R_pad + x];
+                    o[((size_t)g * r->n_readouts + k) * r->R + x] =
+                        r->p->q == 2 ? r->p->graphs[g].wtot - a : a;
+                }
+        OIM_CUDA(cudaMemcpy(trace, o.data(), o.size() * sizeof(double), cudaMemcpyDefault), "write trace");
+    }
+    return OIM_OK;
+}
+
+int oim_get_phases(oim_run_t r, float* theta) {
+    g_last_error.clear();
+    if (!r || !theta) return fail(OIM_EINVAL, "NULL argument");
+    if (!r->ran) return fail(OIM_ESTATE, "run has not executed");
+    int rc = set_device_of(r->p);
+    if (rc != OIM_OK) return rc;
+    float* tmp = nullptr;
+    const size_t count = (size_t)r->p->nodes * r->R;
+    OIM_CUDA(cudaMalloc(&tmp, count * sizeof(float)), "cudaMalloc(phases)");
+    cudaError_t e = launch_gather(*r, r->d_theta[r->final_buf], nullptr, tmp, r->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(r->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(theta, tmp, count * sizeof(float), cudaMemcpyDefault);
+    cudaFree(tmp);
+    if (e != cudaSuccess) return cuda_fail(e, "get phases");
+    return oim_run_sync(r);
+}
+
+int oim_debug_derivative(oim_problem_t p, const float* theta, int32_t replicas, float K, float Ks,
+                         float* f_out) {
+    g_last_error.clear();
+    if (!p || !theta || !f_out) return fail(OIM_EINVAL, "NULL argument");
+    if (p->G != 1) return fail(OIM_EINVAL, "debug derivative takes a single graph");
+    if (replicas < 1) return fail(OIM_EINVAL, "replicas must be >= 1");
+    int rc = set_device_of(p);
+    if (rc == OIM_OK) rc = ensure_uploaded(p);
+    if (rc != OIM_OK) return rc;
+    const size_t count = (size_t)p->nodes * replicas;
+    float *d_th = nullptr, *d_f = nullptr;
+    OIM_CUDA(cudaMalloc(&d_th, count * sizeof(float)), "cudaMalloc");
+    cudaError_t e = cudaMalloc(&d_f, count * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpy(d_th, theta, count * sizeof(float), cudaMemcpyDefault);
+    if (e == cudaSuccess) e = launch_derivative(*p, d_th, replicas, K, Ks, d_f, nullptr);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(f_out, d_f, count * sizeof(float), cudaMemcpyDefault);
+    cudaFree(d_th);
+    if (d_f) cudaFree(d_f);
+    if (e != cudaSuccess) return cuda_fail(e, "debug derivative");
+    return OIM_OK;
+}
+
+void oim_destroy_run(oim_run_t r) {
+    if (!r) return;
+    cudaStreamSynchronize(r->stream);
+    free_run_buffers(r);
+    delete r;
+}
+
+}  // extern "C"

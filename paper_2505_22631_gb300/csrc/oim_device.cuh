@@ -1,0 +1,103 @@
+// oim_device.cuh -- device helpers shared by the step, readout and adjoint kernels.
+//
+// Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random
+// numbers: as easy as 1, 2, 3", SC'11, Sec. 4.2), counter-based so that every
+// draw is a pure function of (seed, graph, stream, node, step, replica) and no
+// generator state is stored (the paper keeps per-thread cuRAND states, Sec. III-B).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace oim {
+
+constexpr uint32_t kStreamInit = 0;
+constexpr uint32_t kStreamNoise = 1;
+
+// Ten Philox rounds: per round the pair products of c0 and c2 with the two
+// multipliers are taken, their high halves are mixed with c1/c3 and the key,
+// and the key advances by the two Weyl increments.
+__device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint32_t lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// Block of four words for (node i, step t, replica quad rq) of one graph/stream.
+__device__ __forceinline__ uint4 draw_block(uint64_t seed, uint32_t graph, uint32_t stream,
+                                            uint32_t i, uint32_t t, uint32_t rq) {
+    return philox10(make_uint4(i, t, rq, (graph << 1) | stream), (uint32_t)seed,
+                    (uint32_t)(seed >> 32));
+}
+
+// ((x >> 9) + 1/2) * 2^-23: an odd multiple of 2^-24 in (0,1), exact in FP32.
+__device__ __forceinline__ float u01(uint32_t x) {
+    return __fmaf_rn((float)(x >> 9), 0x1p-23f, 0x1p-24f);
+}
+
+// Box-Muller: rho = sqrt(-2 ln ua); (rho cos 2 pi ub, rho sin 2 pi ub).
+__device__ __forceinline__ float2 box_muller(uint32_t xa, uint32_t xb) {
+    const float ua = u01(xa);
+    const float ub = u01(xb);
+    const float rho = sqrtf(-2.0f * logf(ua));
+    float s, c;
+    sincospif(2.0f * ub, &s, &c);
+    return make_float2(rho * c, rho * s);
+}
+
+// Normals for the replica pair (r, r+1), r even: lanes (r&3, r&3 + 1).
+__device__ __forceinline__ float2 noise_pair(uint64_t seed, uint32_t graph, uint32_t i,
+                                             uint32_t t, uint32_t r) {
+    const uint4 x = draw_block(seed, graph, kStreamNoise, i, t, r >> 2);
+    return (r & 2) ? box_muller(x.z, x.w) : box_muller(x.x, x.y);
+}
+
+// Initial phases of the replica pair (r, r+1), r even.
+__device__ __forceinline__ float2 init_pair(uint64_t seed, uint32_t graph, uint32_t i,
+                                            uint32_t r) {
+    const uint4 x = draw_block(seed, graph, kStreamInit, i, 0, r >> 2);
+    return (r & 2) ? make_float2(u01(x.z), u01(x.w)) : make_float2(u01(x.x), u01(x.y));
+}
+
+// theta - floor(theta) in [0,1); a tiny negative theta rounds up to 1.0f and maps to 0.
+__device__ __forceinline__ float wrap01(float x) {
+    float y = x - floorf(x);
+    return (y >= 1.0f) ? 0.0f : y;
+}
+
+// sin(2 pi q theta) from (c, s) = (cos 2 pi theta, sin 2 pi theta).
+__device__ __forceinline__ float sin_q(int q, float c, float s) {
+    if (q == 2) return 2.0f * s * c;
+    if (q == 3) return s * __fmaf_rn(-4.0f * s, s, 3.0f);
+    // sin((m+1)x) = 2 cos(x) sin(mx) - sin((m-1)x)
+    float prev = 0.0f, cur = s;
+    for (int m = 1; m < q; ++m) {
+        const float nxt = __fmaf_rn(2.0f * c, cur, -prev);
+        prev = cur;
+        cur = nxt;
+    }
+    return cur;
+}
+
+// Nearest stable phase k/q: floor(q*theta + 1/2) mod q, each operation rounded
+// to FP32 separately (no contraction) so that host and device decide alike.
+__device__ __forceinline__ int spin_of(float theta, int q) {
+    const float a = __fmul_rn((float)q, theta);
+    const float b = __fadd_rn(a, 0.5f);
+    const int k = (int)floorf(b);
+    return (k >= q) ? k - q : k;
+}
+
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+    return __ffma2_rn(a, b, c);
+}
+
+}  // namespace oim

@@ -1,0 +1,126 @@
+// oim_internal.h -- host-side structures shared by the translation units of liboim.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "oim.h"
+
+namespace oim {
+
+// Packed column entry: bit 31 holds the sign of a +-1 weight, the rest the node.
+constexpr uint32_t kSignBit = 0x80000000u;
+
+// Per-graph descriptor, readable by kernels.
+struct GraphDev {
+    int32_t n;          // nodes of this graph
+    int32_t node_off;   // first node in the concatenated node arrays
+    int32_t edge_off;   // first entry in the concatenated CSR arrays
+    int32_t max_deg;    // largest row length
+    double  wtot;       // sum_{i<j} w_ij (cut = wtot - agreeing weight)
+};
+
+// Schedules and scalars of one launch; K/Ks/Kn point at [graph][steps] arrays.
+struct StepParams {
+    const float* K;
+    const float* Ks;
+    const float* Kn;
+    int64_t steps;
+    float dt;
+    float sqrt_dt;
+    uint64_t seed;
+    int32_t q;
+    int32_t R;          // replicas
+    int32_t R_pad;      // leading dimension of the replica axis
+};
+
+struct CSRDev {
+    const int32_t* rowp;        // [nodes + 1] global entry offsets
+    const uint32_t* col;        // [nnz] global node index, sign bit for +-1 weights
+    const float* w;             // [nnz] or nullptr when every |w| == 1
+    const int32_t* node_graph;  // [nodes] graph of each node
+    const GraphDev* graphs;     // [G]
+    int32_t G;
+    int32_t nodes;
+};
+
+}  // namespace oim
+
+struct oim_problem_s {
+    int32_t q = 2;
+    int32_t G = 0;
+    int64_t nodes = 0, nnz = 0;
+    bool unit_weights = true;      // every |w| == 1: signs packed into col
+    bool integer_weights = true;   // every w an integer: exact integer scores
+    int device = 0;
+    bool uploaded = false;         // device arrays valid
+    std::vector<oim::GraphDev> graphs;
+    std::vector<int32_t> h_rowp;   // [nodes+1]
+    std::vector<uint32_t> h_col;   // [nnz] packed
+    std::vector<int32_t> h_col_plain;  // [nnz] global node index
+    std::vector<float> h_w;        // [nnz]
+    int32_t* d_rowp = nullptr;
+    uint32_t* d_col = nullptr;
+    float* d_w = nullptr;
+    int32_t* d_node_graph = nullptr;
+    oim::GraphDev* d_graphs = nullptr;
+    int32_t max_n = 0;             // largest graph
+    oim::CSRDev csr() const {
+        return oim::CSRDev{d_rowp, d_col, unit_weights ? nullptr : d_w, d_node_graph, d_graphs,
+                           G, (int32_t)nodes};
+    }
+};
+
+struct oim_run_s {
+    oim_problem_t p = nullptr;
+    int32_t R = 0, R_pad = 0;
+    int64_t steps = 0, n_readouts = 0, readout_every = 0;
+    uint64_t seed = 0;
+    float dt = 0.f;
+    oim_run_opts opts{};
+    int32_t form = OIM_FORM_STREAM;
+    int32_t prec = OIM_PREC_FP32;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    // device state
+    float* d_theta[2] = {nullptr, nullptr};   // [nodes][R_pad]
+    void* d_cs[2] = {nullptr, nullptr};       // [nodes][R_pad] (cos, sin) cache
+    int final_buf = 0;                        // theta buffer holding the final state
+    float* d_sched = nullptr;                 // [3][G][steps_cap]
+    int64_t steps_cap = 0;
+    int8_t* d_spins = nullptr;                // [nodes][R_pad]
+    double* d_trace = nullptr;                // [G][n_readouts_cap][R_pad]
+    int64_t readouts_cap = 0;
+    double* d_score = nullptr;                // [G][R_pad] scratch for scores
+    double* d_energy = nullptr;               // [G][R_pad]
+    int32_t* d_err = nullptr;                 // device error word
+    // resident-form launch shape
+    int32_t res_k = 0, res_threads = 0, res_items = 0;
+    size_t res_smem = 0;
+    int4* d_items = nullptr;                  // [res_items] (graph, first replica, count, 0)
+    // stream-form CUDA graph of a whole run, reused while its shape is unchanged
+    cudaGraphExec_t chunk_exec = nullptr;
+    int64_t graph_steps = -1;
+    uint64_t graph_seed = 0;
+    float graph_dt = 0.f;
+    int32_t* d_t0 = nullptr;                  // device step counter (graph replays)
+    bool ran = false;
+};
+
+namespace oim {
+
+// error reporting (thread-local message)
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+// launchers (return cudaError_t of the launch)
+cudaError_t launch_init_stream(const oim_run_s& r, cudaStream_t s);
+cudaError_t launch_step_stream(const oim_run_s& r, int64_t t, const int32_t* d_t0, cudaStream_t s);
+cudaError_t resident_shape(const oim_problem_s& p, int32_t R, int32_t prec, int32_t want_k,
+                           int32_t want_threads, int32_t* k, int32_t* threads, int32_t* items,
+                           size_t* smem);
+
+}  // namespace oim

@@ -1,0 +1,189 @@
+// readout.cu -- phase threshold, cut / conflict scores and the Eq. 6 energy.
+//
+// The paper's phase threshold kernel maps each phase to the nearest stable
+// phase k/q (Sec. III-B); the score of a spin assignment is the cut weight
+// (Ising max-cut, Eq. 1) or the weight of monochromatic edges (Potts colouring,
+// Eq. 2).  Scores are accumulated as the weight of agreeing edges,
+// sum_{i<j} w_ij [s_i == s_j], in FP64; the cut is wtot - agree.  With integer
+// weights every partial sum is an integer below 2^53, so the result is exact
+// whatever the order of the additions.
+#include "oim_device.cuh"
+#include "oim_internal.h"
+
+namespace oim {
+
+namespace {
+
+constexpr int kNodesPerThread = 16;
+
+// Thread = (replica quad, chunk of kNodesPerThread consecutive nodes).  Each
+// thread sums the agreeing weight of the upper-triangle edges of its nodes for
+// its four replicas, and flushes with one FP64 atomic per replica whenever the
+// graph changes or the chunk ends.
+__global__ void __launch_bounds__(256) score_kernel(CSRDev csr, const float* __restrict__ theta,
+                                                    int R_pad, int q,
+                                                    double* __restrict__ agree,
+                                                    int64_t row_stride, int64_t k) {
+    const int quads = R_pad >> 2;
+    const int quad = blockIdx.x * blockDim.x + threadIdx.x;
+    if (quad >= quads) return;
+    const int first = blockIdx.y * kNodesPerThread;
+    const int last = min(first + kNodesPerThread, csr.nodes);
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    int g_cur = -1;
+    auto flush = [&]() {
+        if (g_cur < 0) return;
+        double* dst = agree + ((int64_t)g_cur * row_stride + k) * R_pad + 4 * quad;
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            if (acc[c] != 0.0) atomicAdd(dst + c, acc[c]);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[c] = 0.0;
+    };
+    for (int node = first; node < last; ++node) {
+        const int g = csr.node_graph[node];
+        if (g != g_cur) {
+            flush();
+            g_cur = g;
+        }
+        const float4 ti = *reinterpret_cast<const float4*>(theta + (size_t)node * R_pad + 4 * quad);
+        const int si0 = spin_of(ti.x, q), si1 = spin_of(ti.y, q), si2 = spin_of(ti.z, q),
+                  si3 = spin_of(ti.w, q);
+        float f0 = 0.f, f1 = 0.f, f2 = 0.f, f3 = 0.f;
+        const int e_end = csr.rowp[node + 1];
+        for (int e = csr.rowp[node]; e < e_end; ++e) {
+            const uint32_t cw = csr.col[e];
+            const uint32_t j = csr.w ? cw : (cw & ~kSignBit);
+            if ((int)j <= node) continue;
+            const float w = csr.w ? csr.w[e] : ((cw & kSignBit) ? -1.0f : 1.0f);
+            const float4 tj = *reinterpret_cast<const float4*>(theta + (size_t)j * R_pad + 4 * quad);
+            // per node the sum has at most max_deg terms; FP32 is exact for integer w
+            // below 2^24 / max_deg and close otherwise, the FP64 sum carries it on
+            f0 += (si0 == spin_of(tj.x, q)) ? w : 0.f;
+            f1 += (si1 == spin_of(tj.y, q)) ? w : 0.f;
+            f2 += (si2 == spin_of(tj.z, q)) ? w : 0.f;
+            f3 += (si3 == spin_of(tj.w, q)) ? w : 0.f;
+        }
+        acc[0] += f0;
+        acc[1] += f1;
+        acc[2] += f2;
+        acc[3] += f3;
+    }
+    flush();
+}
+
+// E_r = sum_{i<j} w_ij cos(2 pi (theta_i - theta_j)) with FP32 terms, FP64 sum.
+__global__ void __launch_bounds__(256) energy_kernel(CSRDev csr, const float* __restrict__ theta,
+                                                     int R_pad, double* __restrict__ energy) {
+    const int quads = R_pad >> 2;
+    const int quad = blockIdx.x * blockDim.x + threadIdx.x;
+    if (quad >= quads) return;
+    const int first = blockIdx.y * kNodesPerThread;
+    const int last = min(first + kNodesPerThread, csr.nodes);
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    int g_cur = -1;
+    auto flush = [&]() {
+        if (g_cur < 0) return;
+        double* dst = energy + (int64_t)g_cur * R_pad + 4 * quad;
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            if (acc[c] != 0.0) atomicAdd(dst + c, acc[c]);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[c] = 0.0;
+    };
+    for (int node = first; node < last; ++node) {
+        const int g = csr.node_graph[node];
+        if (g != g_cur) {
+            flush();
+            g_cur = g;
+        }
+        const float4 ti = *reinterpret_cast<const float4*>(theta + (size_t)node * R_pad + 4 * quad);
+        const int e_end = csr.rowp[node + 1];
+        for (int e = csr.rowp[node]; e < e_end; ++e) {
+            const uint32_t cw = csr.col[e];
+            const uint32_t j = csr.w ? cw : (cw & ~kSignBit);
+            if ((int)j <= node) continue;
+            const float w = csr.w ? csr.w[e] : ((cw & kSignBit) ? -1.0f : 1.0f);
+            const float4 tj = *reinterpret_cast<const float4*>(theta + (size_t)j * R_pad + 4 * quad);
+            acc[0] += (double)(w * cospif(2.0f * (ti.x - tj.x)));
+            acc[1] += (double)(w * cospif(2.0f * (ti.y - tj.y)));
+            acc[2] += (double)(w * cospif(2.0f * (ti.z - tj.z)));
+            acc[3] += (double)(w * cospif(2.0f * (ti.w - tj.w)));
+        }
+    }
+    flush();
+}
+
+// score[g][r] from the agreeing weight: q == 2 the cut wtot - agree, else agree.
+__global__ void finalize_kernel(const GraphDev* __restrict__ graphs, int G, int q, int R, int R_pad,
+                                const double* __restrict__ agree, int64_t row_stride, int64_t k,
+                                double* __restrict__ score) {
+    const int g = blockIdx.y;
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= G || r >= R) return;
+    const double a = agree[((int64_t)g * row_stride + k) * R_pad + r];
+    score[(int64_t)g * R + r] = (q == 2) ? graphs[g].wtot - a : a;
+}
+
+// theta[node][R_pad] -> out[g][r][i] for spins (FP32 readout) and / or phases.
+__global__ void gather_kernel(CSRDev csr, const float* __restrict__ theta, int R, int R_pad, int q,
+                              int8_t* __restrict__ spins, float* __restrict__ th_out) {
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= (int64_t)csr.nodes * R) return;
+    // output index order: graph, replica, node
+    // find the graph by scanning node offsets (G is small)
+    int64_t rem = gid;
+    int g = 0;
+    for (; g < csr.G; ++g) {
+        const int64_t span = (int64_t)csr.graphs[g].n * R;
+        if (rem < span) break;
+        rem -= span;
+    }
+    const int n = csr.graphs[g].n;
+    const int r = (int)(rem / n);
+    const int i = (int)(rem - (int64_t)r * n);
+    const int node = csr.graphs[g].node_off + i;
+    const float th = theta[(size_t)node * R_pad + r];
+    if (spins) spins[gid] = (int8_t)spin_of(th, q);
+    if (th_out) th_out[gid] = th;
+}
+
+}  // namespace
+
+cudaError_t launch_score(const oim_run_s& r, const float* theta, int64_t k, cudaStream_t s) {
+    const int quads = r.R_pad / 4;
+    dim3 block(min(256, ((quads + 31) / 32) * 32));
+    dim3 grid((quads + block.x - 1) / block.x,
+              (unsigned)((r.p->nodes + kNodesPerThread - 1) / kNodesPerThread));
+    score_kernel<<<grid, block, 0, s>>>(r.p->csr(), theta, r.R_pad, r.p->q, r.d_trace,
+                                        r.readouts_cap, k);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const oim_run_s& r, int64_t k, double* score, cudaStream_t s) {
+    dim3 block(128);
+    dim3 grid((r.R + 127) / 128, r.p->G);
+    finalize_kernel<<<grid, block, 0, s>>>(r.p->d_graphs, r.p->G, r.p->q, r.R, r.R_pad, r.d_trace,
+                                           r.readouts_cap, k, score);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_energy_of(const oim_run_s& r, const float* theta, double* energy, cudaStream_t s) {
+    const int quads = r.R_pad / 4;
+    dim3 block(min(256, ((quads + 31) / 32) * 32));
+    dim3 grid((quads + block.x - 1) / block.x,
+              (unsigned)((r.p->nodes + kNodesPerThread - 1) / kNodesPerThread));
+    energy_kernel<<<grid, block, 0, s>>>(r.p->csr(), theta, r.R_pad, energy);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather(const oim_run_s& r, const float* theta, int8_t* spins, float* th_out,
+                          cudaStream_t s) {
+    const int64_t total = r.p->nodes * r.R;
+    const int threads = 256;
+    gather_kernel<<<(unsigned)((total + threads - 1) / threads), threads, 0, s>>>(
+        r.p->csr(), theta, r.R, r.R_pad, r.p->q, spins, th_out);
+    return cudaGetLastError();
+}
+
+}  // namespace oim

@@ -1,0 +1,244 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances:
+  - initial phases: bit-exact (both sides produce odd multiples of 2^-24);
+  - noise draws: |xi32 - xi64| <= 4e-6 (FP32 Box-Muller plus phase quantisation);
+  - drift: |f32 - f64| <= 1e-5 (K sum_j |w_ij| + Ks + |f64|);
+  - phases: within 1e-3 rad after 100 steps (K = 1/mean degree, where the FP64
+    dynamics amplify an FP32-ulp perturbation of the start to ~4e-6 rad) and after
+    50 steps at the production coupling K = 16/mean degree (measured ~9e-5 rad);
+  - spins and cut / conflict scores from the same phases: bit-exact;
+  - 16-bit (cos, sin) cache: coupling within 1e-2 of the row norm of the FP64 (A, B).
+"""
+import numpy as np
+import pytest
+
+from gpu_common import circ, gpu_run, oracle_phases, rad_dist, require_gpu
+from workloads import (constant, csr_from_edges, erdos_renyi, linear_ramp, make_workload,
+                       planted_partition, torus)
+
+pytestmark = pytest.mark.gpu
+
+FORMS = ["stream", "resident"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    require_gpu()
+
+
+@pytest.fixture(scope="module")
+def c1():
+    return make_workload("er800")
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("R", [8, 6])
+def test_initial_phases_bitexact(orc, c1, form, R):
+    g = c1.graphs[0]
+    run = gpu_run(g, 2, 0.0, 0.0, 0.0, 0.01, 0, R, seed=77, form=form)
+    th = run.phases()[0]
+    ref = orc.init_phases(g.n, R, 77).astype(np.float32)
+    assert np.array_equal(th, ref)
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_noise_draws_match_oracle(orc, form):
+    n, R, kick = 1000, 12, 0.05
+    g = csr_from_edges(n, np.zeros(0, int), np.zeros(0, int))
+    run = gpu_run(g, 2, 0.0, 0.0, kick, 1.0, 1, R, seed=5, form=form)
+    th1 = run.phases()[0].astype(np.float64)
+    th0 = orc.init_phases(n, R, 5)
+    xi = circ(th1 - th0) / kick
+    ref = orc.noise_block(n, R, 5, 0)
+    assert np.max(np.abs(xi - ref)) <= 4e-6
+
+
+def test_drift_matches_fp64(orc, c1):
+    from paper_2505_22631_gb300 import Problem, oim_debug_derivative
+    g = c1.graphs[0]
+    prob = Problem.from_graph(g, 2)
+    rng = np.random.default_rng(3)
+    R = 3
+    th = rng.random((R, g.n)).astype(np.float32)
+    K, Ks = 0.33, 1.3
+    f = np.zeros((R, g.n), np.float32)
+    oim_debug_derivative(prob.handle, th, R, K, Ks, f)
+    absw = np.bincount(np.repeat(np.arange(g.n), g.degrees()), weights=np.abs(g.w), minlength=g.n)
+    for r in range(R):
+        ref = orc.derivative(g, 2, th[r].astype(np.float64), np.float32(K), np.float32(Ks))
+        scale = np.float32(K) * absw + np.float32(Ks) + np.abs(ref)
+        assert np.max(np.abs(f[r] - ref) / scale) <= 1e-5
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_phases_after_100_steps(orc, c1, form):
+    g = c1.graphs[0]
+    T, R, seed = 100, 8, 11
+    K = constant(T, 1.0 / g.mean_degree)
+    Ks, Kn = c1.Ks[0][:T], c1.Kn[0][:T]
+    run = gpu_run(g, 2, K, Ks, Kn, c1.dt, T, R, seed, form=form)
+    ref = oracle_phases(orc, g, 2, K, Ks, Kn, c1.dt, T, R, seed, nthreads=8)
+    assert rad_dist(run.phases()[0], ref).max() <= 1e-3
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_phases_production_coupling(orc, c1, form):
+    g = c1.graphs[0]
+    T, R, seed = 50, 8, 12
+    run = gpu_run(g, 2, c1.K[0][:T], c1.Ks[0][:T], c1.Kn[0][:T], c1.dt, T, R, seed, form=form)
+    ref = oracle_phases(orc, g, 2, c1.K[0][:T], c1.Ks[0][:T], c1.Kn[0][:T], c1.dt, T, R, seed,
+                        nthreads=8)
+    assert rad_dist(run.phases()[0], ref).max() <= 1e-3
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("wl", ["er800", "planted600"])
+def test_readout_and_scores_bitexact(orc, form, wl):
+    w = make_workload(wl)
+    g = w.graphs[0]
+    T, R = (1000, 8) if wl == "er800" else (600, 12)
+    run = gpu_run(g, w.q, w.K[0][:T], w.Ks[0][:T], w.Kn[0][:T], w.dt, T, R, seed=21, form=form,
+                  readout_every=100)
+    out = run.readout(energy=True)
+    th = run.phases()[0]
+    spins = orc.readout_f32(w.q, th)
+    assert np.array_equal(out["spins"][0], spins)
+    sc = orc.scores(g, w.q, spins)
+    assert np.array_equal(out["score"][0], sc)
+    assert np.array_equal(out["trace"][0, -1], sc)          # last readout is the final state
+    best = int(np.argmax(sc)) if w.q == 2 else int(np.argmin(sc))
+    assert out["best_replica"][0] == best
+    E = orc.energy(g, th.astype(np.float64))
+    assert np.max(np.abs(out["energy"][0] - E)) <= 1e-5 * np.abs(g.w).sum()
+
+
+def test_forms_agree(c1):
+    g = c1.graphs[0]
+    T, R = 100, 8
+    K = constant(T, 1.0 / g.mean_degree)
+    a = gpu_run(g, 2, K, c1.Ks[0][:T], c1.Kn[0][:T], c1.dt, T, R, 4, form="stream").phases()[0]
+    b = gpu_run(g, 2, K, c1.Ks[0][:T], c1.Kn[0][:T], c1.dt, T, R, 4, form="resident").phases()[0]
+    assert rad_dist(a, b).max() <= 1e-4
+
+
+def test_resident_block_shape_does_not_change_results(c1):
+    g = c1.graphs[0]
+    T, R = 200, 16
+    args = (g, 2, c1.K[0][:T], c1.Ks[0][:T], c1.Kn[0][:T], c1.dt, T, R, 9)
+    a = gpu_run(*args, form="resident", replicas_per_block=2).phases()[0]
+    b = gpu_run(*args, form="resident", replicas_per_block=16, threads_per_block=256).phases()[0]
+    c = gpu_run(*args, form="resident", replicas_per_block=6).phases()[0]
+    assert np.array_equal(a, b) and np.array_equal(a, c)
+
+
+def test_stream_graph_capture_matches_direct_launches(c1):
+    g = c1.graphs[0]
+    T, R = 120, 8
+    args = (g, 2, c1.K[0][:T], c1.Ks[0][:T], c1.Kn[0][:T], c1.dt, T, R, 9)
+    a = gpu_run(*args, form="stream", use_graph=True, readout_every=40)
+    b = gpu_run(*args, form="stream", use_graph=False, readout_every=40)
+    assert np.array_equal(a.phases()[0], b.phases()[0])
+    assert np.array_equal(a.readout()["trace"], b.readout()["trace"])
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_batch_uses_graph_index_streams(orc, form):
+    g0 = erdos_renyi(300, 0.05, 1, "+1")
+    g1 = torus(10, 12, 2, "pm1")
+    T, R = 60, 6
+    K = [constant(T, 4.0 / g.mean_degree) for g in (g0, g1)]
+    Ks, Kn = linear_ramp(T, 0, 1), constant(T, 0.1)
+    run = gpu_run([g0, g1], 2, K, Ks, Kn, 0.01, T, R, 31, form=form, readout_every=20)
+    ph = run.phases()
+    out = run.readout()
+    for gi, g in enumerate((g0, g1)):
+        ref = oracle_phases(orc, g, 2, K[gi], Ks, Kn, 0.01, T, R, 31, graph=gi)
+        assert rad_dist(ph[gi], ref).max() <= 1e-3
+        assert np.array_equal(out["score"][gi], orc.scores(g, 2, orc.readout_f32(2, ph[gi])))
+    # graph 0 of the batch is the same trajectory as graph 0 run on its own
+    alone = gpu_run(g0, 2, K[0], Ks, Kn, 0.01, T, R, 31, form=form).phases()[0]
+    assert np.array_equal(alone, ph[0])
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("kind", ["float", "integer"])
+def test_ragged_sizes_and_general_weights(orc, form, kind):
+    rng = np.random.default_rng(5)
+    g = erdos_renyi(37, 0.2, 8, "+1")
+    i, j, _ = g.edges()
+    w = rng.uniform(-2, 2, i.shape[0]) if kind == "float" else rng.choice([-2, -1, 1, 3], i.shape[0])
+    g = csr_from_edges(37, i, j, w.astype(np.float32))
+    T, R = 60, 5
+    K, Ks, Kn = constant(T, 0.1), linear_ramp(T, 0, 1.5), constant(T, 0.1)
+    run = gpu_run(g, 2, K, Ks, Kn, 0.01, T, R, 3, form=form)
+    th = run.phases()[0]
+    assert rad_dist(th, oracle_phases(orc, g, 2, K, Ks, Kn, 0.01, T, R, 3)).max() <= 1e-3
+    sc = run.readout()["score"][0]
+    ref = orc.scores(g, 2, orc.readout_f32(2, th))
+    if kind == "integer":
+        assert np.array_equal(sc, ref)
+    else:
+        assert np.allclose(sc, ref, rtol=1e-6, atol=1e-5)
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("q", [3, 5])
+def test_potts_orders(orc, form, q):
+    g = planted_partition(90, 3, 4.0, 6)
+    T, R = 50, 4
+    K, Ks, Kn = constant(T, 8.0 / g.mean_degree), linear_ramp(T, 0, 2), constant(T, 0.1)
+    run = gpu_run(g, q, K, Ks, Kn, 0.01, T, R, 8, form=form)
+    th = run.phases()[0]
+    assert rad_dist(th, oracle_phases(orc, g, q, K, Ks, Kn, 0.01, T, R, 8)).max() <= 1e-3
+    assert np.array_equal(run.readout()["score"][0], orc.scores(g, q, orc.readout_f32(q, th)))
+
+
+@pytest.mark.parametrize("precision", ["fp16", "bf16"])
+def test_half_cache_coupling_within_1e2_per_row(orc, c1, precision):
+    g = c1.graphs[0]
+    R, dt, K = 16, 1e-3, 1.0
+    run = gpu_run(g, 2, K, 0.0, 0.0, dt, 1, R, 13, form="resident", precision=precision)
+    th0 = orc.init_phases(g.n, R, 13)
+    D = circ(run.phases()[0].astype(np.float64) - th0) / (np.float32(dt) * K)
+    A = np.zeros((R, g.n))
+    B = np.zeros((R, g.n))
+    rows = np.repeat(np.arange(g.n), g.degrees())
+    for r in range(R):
+        np.add.at(A[r], rows, g.w * np.cos(2 * np.pi * th0[r, g.col]))
+        np.add.at(B[r], rows, g.w * np.sin(2 * np.pi * th0[r, g.col]))
+    D64 = np.stack([orc.coupling(g, th0[r]) for r in range(R)])
+    err = np.linalg.norm(D - D64, axis=0)
+    ref = np.sqrt(np.sum(A**2 + B**2, axis=0))
+    assert np.max(err / ref) <= 1e-2
+
+
+def test_empty_graph_zero_steps_and_single_node(orc):
+    g = csr_from_edges(1, np.zeros(0, int), np.zeros(0, int))
+    for form in FORMS:
+        run = gpu_run(g, 2, 0.0, 1.0, 0.0, 0.01, 0, 3, 1, form=form)
+        out = run.readout()
+        assert out["score"].shape == (1, 3) and np.all(out["score"] == 0)
+        run = gpu_run(g, 3, 0.0, 1.0, 0.1, 0.01, 40, 3, 1, form=form)
+        ref = oracle_phases(orc, g, 3, 0.0, 1.0, 0.1, 0.01, 40, 3, 1)
+        assert rad_dist(run.phases()[0], ref).max() <= 1e-3
+
+
+def test_resident_single_replica_blocks_for_large_graph(orc):
+    g = torus(160, 160, 4, "pm1")   # 25600 nodes: one FP32 replica (200 KB) per block
+    T, R = 20, 3
+    K, Ks, Kn = constant(T, 4.0), linear_ramp(T, 0, 1), constant(T, 0.1)
+    run = gpu_run(g, 2, K, Ks, Kn, 0.01, T, R, 2, form="resident")
+    assert run.info()["form"] == 2
+    ref = oracle_phases(orc, g, 2, K, Ks, Kn, 0.01, T, R, 2, nthreads=8)
+    assert rad_dist(run.phases()[0], ref).max() <= 1e-3
+
+
+def test_invalid_form_requests():
+    from paper_2505_22631_gb300 import OimError
+    g = torus(300, 300, 1, "pm1")   # too large for a resident FP32 replica
+    with pytest.raises(OimError) as ei:
+        gpu_run(g, 2, 1.0, 1.0, 0.1, 0.01, 2, 4, 1, form="resident")
+    assert ei.value.code == -5
+    with pytest.raises(OimError):
+        gpu_run(torus(4, 4, 1), 2, 1.0, 1.0, 0.1, 0.01, 2, 4, 1, form="stream", precision="bf16")

@@ -1,0 +1,131 @@
+"""The C-ABI library builds, loads and exports every entry point include/oim.h declares.
+
+These run without a GPU: no call here launches device work.  Argument
+validation happens on the host before any device call, so malformed inputs are
+rejected with OIM_EINVAL on any machine.
+"""
+import ctypes
+import os
+import re
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "oim.h")
+
+
+@pytest.fixture(scope="module")
+def capi():
+    from paper_2505_22631_gb300 import build, capi
+    build.build()
+    capi.load()
+    return capi
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:int|void|const char\*)\s+(oim_\w+)\s*\(", text, flags=re.M)))
+
+
+def test_every_declared_symbol_is_exported(capi):
+    decl = declared_functions()
+    assert len(decl) >= 15
+    out = subprocess.run(["nm", "-D", "--defined-only", capi.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r" T (oim_\w+)$", out, flags=re.M))
+    missing = [f for f in decl if f not in exported]
+    assert not missing, missing
+    # and the Python binding declares each one with the same name
+    assert sorted(capi.SIGNATURES) == decl
+
+
+def test_opts_struct_layout_matches_header(capi):
+    src = r"""
+    #include <stdio.h>
+    #include <stddef.h>
+    #include "oim.h"
+    int main(void) {
+        printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(oim_run_opts),
+               offsetof(oim_run_opts, readout_every), offsetof(oim_run_opts, stream),
+               offsetof(oim_run_opts, use_graph), offsetof(oim_run_opts, replicas_per_block),
+               offsetof(oim_run_opts, threads_per_block), offsetof(oim_run_opts, checkpoint_every),
+               offsetof(oim_run_opts, reserved));
+        return 0;
+    }
+    """
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        exe = os.path.join(d, "t")
+        open(c, "w").write(src)
+        subprocess.run(["gcc", "-I" + os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+        vals = [int(x) for x in subprocess.run([exe], capture_output=True, text=True,
+                                               check=True).stdout.split()]
+    S = capi.oim_run_opts
+    got = [ctypes.sizeof(S), S.readout_every.offset, S.stream.offset, S.use_graph.offset,
+           S.replicas_per_block.offset, S.threads_per_block.offset, S.checkpoint_every.offset,
+           S.reserved.offset]
+    assert got == vals
+
+
+def test_default_opts_and_version(capi):
+    o = capi.oim_default_opts()
+    assert o.form == capi.OIM_FORM_AUTO and o.precision == capi.OIM_PREC_AUTO
+    assert o.use_graph == 1 and o.readout_every == 0
+    assert "sm_103a" in capi.oim_version()
+
+
+def _csr(n, edges, w=None):
+    from workloads import csr_from_edges
+    e = np.array(edges)
+    return csr_from_edges(n, e[:, 0], e[:, 1], w)
+
+
+@pytest.mark.parametrize("case", ["diag", "range", "unsorted", "asym", "rowptr", "q", "n", "nan"])
+def test_malformed_problems_rejected(capi, case):
+    g = _csr(4, [(0, 1), (1, 2), (2, 3)], [1.0, 2.0, 3.0])
+    n, q = 4, 2
+    rp, col, w = g.row_ptr.copy(), g.col.copy(), g.w.copy()
+    if case == "diag":
+        col[0] = 0
+    elif case == "range":
+        col[-1] = 7
+    elif case == "unsorted":
+        rp = np.array([0, 1, 3, 5, 6], dtype=np.int64)
+        col = np.array([1, 2, 0, 3, 1, 2], dtype=np.int32)   # row 1 = [2, 0]
+        w = np.ones(6, dtype=np.float32)
+    elif case == "asym":
+        w[0] = 5.0
+    elif case == "rowptr":
+        rp[2] = rp[1] - 1
+    elif case == "q":
+        q = 1
+    elif case == "n":
+        n = 0
+    elif case == "nan":
+        w[1] = np.nan
+    with pytest.raises(capi.OimError) as ei:
+        capi.oim_create_problem(n, q, col.shape[0], rp, col, w)
+    assert ei.value.code == capi.OIM_EINVAL
+    assert capi.oim_last_error() != ""
+
+
+def test_null_handles_rejected(capi):
+    with pytest.raises(capi.OimError) as ei:
+        capi.oim_run_sync(None)
+    assert ei.value.code == capi.OIM_EINVAL
+    with pytest.raises(capi.OimError):
+        capi.oim_create_batch([])
+
+
+def test_library_package_does_not_touch_the_oracle():
+    pkg = os.path.join(ROOT, "paper_2505_22631_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in text and "from oracle" not in text, f
+                assert "oim_oracle" not in text and "orc_" not in text, f
