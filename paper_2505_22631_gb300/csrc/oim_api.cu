@@ -90,6 +90,8 @@ int upload_problem(oim_problem_s* p) {
     OIM_CUDA(dev_alloc(&p->d_col, p->h_col.size()), "cudaMalloc(col)");
     OIM_CUDA(dev_alloc(&p->d_w, p->h_w.size()), "cudaMalloc(w)");
     OIM_CUDA(dev_alloc(&p->d_node_graph, (size_t)p->nodes), "cudaMalloc(node_graph)");
+    OIM_CUDA(dev_alloc(&p->d_split, (size_t)p->nodes), "cudaMalloc(split)");
+    OIM_CUDA(dev_alloc(&p->d_order, (size_t)p->nodes), "cudaMalloc(order)");
     OIM_CUDA(dev_alloc(&p->d_graphs, p->graphs.size()), "cudaMalloc(graphs)");
     std::vector<int32_t> ng((size_t)p->nodes);
     for (int g = 0; g < p->G; ++g)
@@ -105,6 +107,10 @@ int upload_problem(oim_problem_s* p) {
                  "upload w");
     OIM_CUDA(cudaMemcpy(p->d_node_graph, ng.data(), ng.size() * 4, cudaMemcpyHostToDevice),
              "upload node_graph");
+    OIM_CUDA(cudaMemcpy(p->d_split, p->h_split.data(), p->h_split.size() * 4, cudaMemcpyHostToDevice),
+             "upload split");
+    OIM_CUDA(cudaMemcpy(p->d_order, p->h_order.data(), p->h_order.size() * 4, cudaMemcpyHostToDevice),
+             "upload order");
     OIM_CUDA(cudaMemcpy(p->d_graphs, p->graphs.data(), p->graphs.size() * sizeof(GraphDev),
                         cudaMemcpyHostToDevice),
              "upload graphs");
@@ -125,6 +131,8 @@ void free_problem(oim_problem_s* p) {
     dev_free(p->d_col);
     dev_free(p->d_w);
     dev_free(p->d_node_graph);
+    dev_free(p->d_split);
+    dev_free(p->d_order);
     dev_free(p->d_graphs);
 }
 
@@ -186,27 +194,29 @@ int choose_form(oim_run_s* r) {
     if (form < OIM_FORM_AUTO || form > OIM_FORM_GEMM) return fail(OIM_EINVAL, "unknown form");
     if (prec < OIM_PREC_AUTO || prec > OIM_PREC_FP16) return fail(OIM_EINVAL, "unknown precision");
     if (form == OIM_FORM_GEMM) return fail(OIM_EUNSUPPORTED, "the tensor-core form is not built");
-    if (prec == OIM_PREC_AUTO) prec = OIM_PREC_FP32;
+    // AUTO precision: the resident form keeps its (cos, sin) cache in FP16 (twice
+    // the replicas per block of FP32, coupling error ~1e-4 relative); the stream
+    // form is FP32 only.
+    if (prec == OIM_PREC_AUTO) prec = (form == OIM_FORM_STREAM) ? OIM_PREC_FP32 : OIM_PREC_FP16;
     if (form == OIM_FORM_AUTO) {
-        int32_t k, th, it;
-        size_t sm;
-        form = resident_shape(*r->p, r->R_pad, prec, r->opts.replicas_per_block,
-                              r->opts.threads_per_block, &k, &th, &it, &sm) == cudaSuccess
+        ResidentPlan tmp;
+        form = plan_resident(*r->p, r->R_pad, prec, r->opts.replicas_per_block,
+                             r->opts.threads_per_block, &tmp) == cudaSuccess
                    ? OIM_FORM_RESIDENT
                    : OIM_FORM_STREAM;
+        if (form == OIM_FORM_STREAM && r->opts.precision == OIM_PREC_AUTO) prec = OIM_PREC_FP32;
     }
     if (form == OIM_FORM_STREAM && prec != OIM_PREC_FP32)
         return fail(OIM_EUNSUPPORTED, "the stream form stores its cache in FP32 only");
     r->form = form;
     r->prec = prec;
     if (form == OIM_FORM_RESIDENT) {
-        cudaError_t e = resident_shape(*r->p, r->R_pad, prec, r->opts.replicas_per_block,
-                                       r->opts.threads_per_block, &r->res_k, &r->res_threads,
-                                       &r->res_items, &r->res_smem);
+        cudaError_t e = plan_resident(*r->p, r->R_pad, prec, r->opts.replicas_per_block,
+                                      r->opts.threads_per_block, &r->plan);
         if (e != cudaSuccess)
             return fail(OIM_EUNSUPPORTED,
-                        "resident form: a replica pair of the largest graph does not fit in "
-                        "shared memory, or the requested shape is invalid");
+                        "resident form: one replica of the largest graph does not fit in "
+                        "shared memory, or the requested replicas per block is invalid");
     }
     return OIM_OK;
 }
@@ -226,11 +236,7 @@ int allocate_run(oim_run_s* r) {
         OIM_CUDA(cudaMalloc(&r->d_cs[1], state * sizeof(float2)), "cudaMalloc(cs)");
     }
     if (r->form == OIM_FORM_RESIDENT) {
-        std::vector<int4> items;
-        for (int g = 0; g < G; ++g)
-            for (int r0 = 0; r0 < r->R_pad; r0 += r->res_k)
-                items.push_back(make_int4(g, r0, std::min(r->res_k, r->R_pad - r0), 0));
-        r->res_items = (int32_t)items.size();
+        const auto& items = r->plan.items;
         OIM_CUDA(dev_alloc(&r->d_items, items.size()), "cudaMalloc(items)");
         OIM_CUDA(cudaMemcpy(r->d_items, items.data(), items.size() * sizeof(int4),
                             cudaMemcpyHostToDevice),
@@ -415,12 +421,34 @@ int oim_create_problem(int32_t n, int32_t q, int64_t nnz, const int64_t* row_ptr
     p->graphs.push_back(gd);
     p->h_rowp.resize((size_t)n + 1);
     for (int32_t i = 0; i <= n; ++i) p->h_rowp[i] = (int32_t)rp[i];
-    p->h_col_plain = ci;
-    p->h_w = w;
     for (float x : w) {
         if (std::fabs(x) != 1.0f) p->unit_weights = false;
         if (x != std::floor(x)) p->integer_weights = false;
     }
+    // With +-1 weights each row is stored positive entries first (each part in
+    // ascending column order), so the coupling gather is two sign-free loops.
+    p->h_col_plain.resize((size_t)nnz);
+    p->h_w.resize((size_t)nnz);
+    p->h_split.resize((size_t)n);
+    for (int32_t i = 0; i < n; ++i) {
+        int64_t at = rp[i];
+        for (int pass = 0; pass < 2; ++pass) {
+            if (pass == 1) p->h_split[i] = (int32_t)at;
+            for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
+                const bool neg = p->unit_weights && w[e] < 0.f;
+                if (neg != (pass == 1)) continue;
+                p->h_col_plain[at] = ci[e];
+                p->h_w[at] = w[e];
+                ++at;
+            }
+        }
+        if (!p->unit_weights) p->h_split[i] = (int32_t)rp[i + 1];
+    }
+    p->h_order.resize((size_t)n);
+    for (int32_t i = 0; i < n; ++i) p->h_order[i] = i;
+    std::stable_sort(p->h_order.begin(), p->h_order.end(), [&](int32_t a, int32_t b) {
+        return rp[a + 1] - rp[a] > rp[b + 1] - rp[b];
+    });
     pack_columns(p);
     if (!(flags & OIM_FLAG_DEFER_UPLOAD)) {
         int rc = upload_problem(p);
@@ -467,7 +495,11 @@ int oim_create_batch(int32_t count, const oim_problem_t* problems, oim_problem_t
         gd.edge_off = (int32_t)eoff;
         p->graphs.push_back(gd);
         p->max_n = std::max(p->max_n, gd.n);
-        for (int32_t i = 0; i < gd.n; ++i) p->h_rowp.push_back((int32_t)(eoff + s->h_rowp[i + 1]));
+        for (int32_t i = 0; i < gd.n; ++i) {
+            p->h_rowp.push_back((int32_t)(eoff + s->h_rowp[i + 1]));
+            p->h_split.push_back((int32_t)(eoff + s->h_split[i]));
+            p->h_order.push_back(s->h_order[i]);
+        }
         for (size_t e = 0; e < s->h_col_plain.size(); ++e) {
             p->h_col_plain.push_back((int32_t)(s->h_col_plain[e] + noff));
             p->h_w.push_back(s->h_w[e]);

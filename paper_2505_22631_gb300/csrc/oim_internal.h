@@ -37,11 +37,23 @@ struct StepParams {
     int32_t R_pad;      // leading dimension of the replica axis
 };
 
+// Launch plan of the resident form.
+struct ResidentPlan {
+    int unit = 4;                  // replicas per thread item: 4 (quad kernel), 2 or 1
+    bool csr_smem = false;         // graph structure staged in shared memory
+    int threads = 0;
+    size_t smem = 0;
+    std::vector<int> k_of_graph;   // replicas per block, per graph
+    std::vector<int4> items;       // per block: (graph, first replica, replicas, 0)
+};
+
 struct CSRDev {
     const int32_t* rowp;        // [nodes + 1] global entry offsets
     const uint32_t* col;        // [nnz] global node index, sign bit for +-1 weights
     const float* w;             // [nnz] or nullptr when every |w| == 1
     const int32_t* node_graph;  // [nodes] graph of each node
+    const int32_t* split;       // [nodes] first negative-weight entry of each row
+    const int32_t* order;       // [nodes] per graph: local node indices by decreasing degree
     const GraphDev* graphs;     // [G]
     int32_t G;
     int32_t nodes;
@@ -62,15 +74,20 @@ struct oim_problem_s {
     std::vector<uint32_t> h_col;   // [nnz] packed
     std::vector<int32_t> h_col_plain;  // [nnz] global node index
     std::vector<float> h_w;        // [nnz]
+    std::vector<int32_t> h_split;  // [nodes] first entry with a negative weight in each row
+                                   // (rows hold positive weights first when all |w| == 1)
+    std::vector<int32_t> h_order;  // [nodes] local node indices of each graph by decreasing degree
     int32_t* d_rowp = nullptr;
     uint32_t* d_col = nullptr;
     float* d_w = nullptr;
     int32_t* d_node_graph = nullptr;
+    int32_t* d_split = nullptr;
+    int32_t* d_order = nullptr;
     oim::GraphDev* d_graphs = nullptr;
     int32_t max_n = 0;             // largest graph
     oim::CSRDev csr() const {
-        return oim::CSRDev{d_rowp, d_col, unit_weights ? nullptr : d_w, d_node_graph, d_graphs,
-                           G, (int32_t)nodes};
+        return oim::CSRDev{d_rowp, d_col, unit_weights ? nullptr : d_w, d_node_graph, d_split,
+                           d_order, d_graphs, G, (int32_t)nodes};
     }
 };
 
@@ -97,10 +114,9 @@ struct oim_run_s {
     double* d_score = nullptr;                // [G][R_pad] scratch for scores
     double* d_energy = nullptr;               // [G][R_pad]
     int32_t* d_err = nullptr;                 // device error word
-    // resident-form launch shape
-    int32_t res_k = 0, res_threads = 0, res_items = 0;
-    size_t res_smem = 0;
-    int4* d_items = nullptr;                  // [res_items] (graph, first replica, count, 0)
+    // resident-form launch plan
+    oim::ResidentPlan plan;
+    int4* d_items = nullptr;                  // plan.items on the device
     // stream-form CUDA graph of a whole run, reused while its shape is unchanged
     cudaGraphExec_t chunk_exec = nullptr;
     int64_t graph_steps = -1;
@@ -119,8 +135,7 @@ int cuda_fail(cudaError_t e, const char* what);
 // launchers (return cudaError_t of the launch)
 cudaError_t launch_init_stream(const oim_run_s& r, cudaStream_t s);
 cudaError_t launch_step_stream(const oim_run_s& r, int64_t t, const int32_t* d_t0, cudaStream_t s);
-cudaError_t resident_shape(const oim_problem_s& p, int32_t R, int32_t prec, int32_t want_k,
-                           int32_t want_threads, int32_t* k, int32_t* threads, int32_t* items,
-                           size_t* smem);
+cudaError_t plan_resident(const oim_problem_s& p, int32_t R_pad, int32_t prec, int32_t want_k,
+                          int32_t want_threads, ResidentPlan* plan);
 
 }  // namespace oim

@@ -264,50 +264,434 @@ cudaError_t launch_u(int U, bool unit, const ResidentArgs& a, int blocks, int th
                 : launch_one<1, false, Cache>(a, blocks, threads, smem, s);
 }
 
+
+// ---------------------------------------------------------------------------
+// Quad kernel: a thread owns one node and a quad of four replicas (one Philox
+// block per node and step, one CSR read per four replicas).  When the graph's
+// structure fits, it is copied once into shared memory as 16-bit local column
+// indices with the sign of the +-1 weight in the top bit, so a step never
+// leaves the SM except for the owned phases.
+// ---------------------------------------------------------------------------
+// Transcendentals of a step: accurate library functions with the FP32 cache,
+// hardware approximations with a 16-bit cache (whose rounding, 2^-12, is far
+// above the approximations' ~1e-6).
+struct MathAccurate {
+    __device__ static float2 cs(float th) { return cos_sin_2pi(th); }
+    __device__ static float2 bm(uint32_t a, uint32_t b) { return box_muller(a, b); }
+};
+struct MathFast {
+    __device__ static float2 cs(float th) { return cos_sin_2pi_fast(th); }
+    __device__ static float2 bm(uint32_t a, uint32_t b) { return box_muller_fast(a, b); }
+};
+
+
+struct QuadF32 {
+    using Math = MathAccurate;
+    struct __align__(16) T { float4 lo, hi; };   // (c0, s0, c1, s1), (c2, s2, c3, s3)
+    __device__ static T pack(const float2 (&cs)[4]) {
+        return T{make_float4(cs[0].x, cs[0].y, cs[1].x, cs[1].y),
+                 make_float4(cs[2].x, cs[2].y, cs[3].x, cs[3].y)};
+    }
+    __device__ static void unpack(const T& v, float2 (&cs)[4]) {
+        cs[0] = make_float2(v.lo.x, v.lo.y);
+        cs[1] = make_float2(v.lo.z, v.lo.w);
+        cs[2] = make_float2(v.hi.x, v.hi.y);
+        cs[3] = make_float2(v.hi.z, v.hi.w);
+    }
+    // acc[v] += (c_v, s_v)
+    __device__ static void accumulate(float2 (&acc)[4], const T& v) {
+        acc[0] = __fadd2_rn(acc[0], make_float2(v.lo.x, v.lo.y));
+        acc[1] = __fadd2_rn(acc[1], make_float2(v.lo.z, v.lo.w));
+        acc[2] = __fadd2_rn(acc[2], make_float2(v.hi.x, v.hi.y));
+        acc[3] = __fadd2_rn(acc[3], make_float2(v.hi.z, v.hi.w));
+    }
+};
+// acc += (lo, hi) of a packed 16-bit pair, each half widened inside the add
+// (PTX mixed-precision add: f32 = f16 + f32, exact widening, one rounding).
+__device__ __forceinline__ void add_f16x2(float2& acc, uint32_t h2) {
+    asm("{\n\t.reg .b16 l, h;\n\tmov.b32 {l, h}, %2;\n\t"
+        "add.rn.f32.f16 %0, l, %0;\n\tadd.rn.f32.f16 %1, h, %1;\n\t}"
+        : "+f"(acc.x), "+f"(acc.y) : "r"(h2));
+}
+__device__ __forceinline__ void add_bf16x2(float2& acc, uint32_t h2) {
+    asm("{\n\t.reg .b16 l, h;\n\tmov.b32 {l, h}, %2;\n\t"
+        "add.rn.f32.bf16 %0, l, %0;\n\tadd.rn.f32.bf16 %1, h, %1;\n\t}"
+        : "+f"(acc.x), "+f"(acc.y) : "r"(h2));
+}
+
+template <typename H2, typename Cvt>
+struct QuadHalf {
+    using Math = MathFast;
+    using T = uint4;   // four 16-bit (c, s) pairs
+    __device__ static T pack(const float2 (&cs)[4]) {
+        uint32_t w[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            H2 h = Cvt::to(cs[v]);
+            w[v] = *reinterpret_cast<uint32_t*>(&h);
+        }
+        return make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    __device__ static void unpack(const T& q, float2 (&cs)[4]) {
+        const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int v = 0; v < 4; ++v) cs[v] = Cvt::from(*reinterpret_cast<const H2*>(&w[v]));
+    }
+    __device__ static void accumulate(float2 (&acc)[4], const T& q) {
+        Cvt::add(acc[0], q.x);
+        Cvt::add(acc[1], q.y);
+        Cvt::add(acc[2], q.z);
+        Cvt::add(acc[3], q.w);
+    }
+};
+struct CvtF16 {
+    __device__ static __half2 to(float2 x) { return __floats2half2_rn(x.x, x.y); }
+    __device__ static float2 from(__half2 h) { return __half22float2(h); }
+    __device__ static void add(float2& acc, uint32_t h2) { add_f16x2(acc, h2); }
+};
+struct CvtBF16 {
+    __device__ static __nv_bfloat162 to(float2 x) { return __floats2bfloat162_rn(x.x, x.y); }
+    __device__ static float2 from(__nv_bfloat162 h) { return __bfloat1622float2(h); }
+    __device__ static void add(float2& acc, uint32_t h2) { add_bf16x2(acc, h2); }
+};
+using QuadF16 = QuadHalf<__half2, CvtF16>;
+using QuadBF16 = QuadHalf<__nv_bfloat162, CvtBF16>;
+
+constexpr uint16_t kLocalSign = 0x8000u;
+
+
+__host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+template <typename Quad, bool kSmemCSR, bool kUnit>
+__global__ void __launch_bounds__(1024, 1) resident_quad_kernel(ResidentArgs a) {
+    using T = typename Quad::T;
+    using M = typename Quad::Math;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[64];
+
+    const int4 item = a.items[blockIdx.x];
+    const int g = item.x, r0 = item.y, kk = item.z;
+    const GraphDev gd = a.csr.graphs[g];
+    const int n = gd.n, noff = gd.node_off, e0 = gd.edge_off;
+    const int units = kk >> 2;
+    const int NS = blockDim.x / units;
+    const int u = threadIdx.x % units;
+    const int slot = threadIdx.x / units;
+    const int i_begin = slot < NS ? slot : n;
+    const int rq = (r0 >> 2) + u;               // replica quad index
+    const StepParams& P = a.P;
+    const int R_pad = P.R_pad;
+    float* theta = a.theta + r0 + 4 * u;
+
+    T* cache = reinterpret_cast<T*>(smem_raw);                  // [n][units]
+    int32_t* s_rowp = reinterpret_cast<int32_t*>(smem_raw + align16((size_t)n * units * sizeof(T)));
+    int32_t* s_split = reinterpret_cast<int32_t*>(reinterpret_cast<unsigned char*>(s_rowp) +
+                                                  align16((size_t)(n + 1) * 4));
+    uint16_t* s_order = reinterpret_cast<uint16_t*>(reinterpret_cast<unsigned char*>(s_split) +
+                                                    align16((size_t)n * 4));
+    uint16_t* s_col = reinterpret_cast<uint16_t*>(reinterpret_cast<unsigned char*>(s_order) +
+                                                  align16((size_t)n * 2));
+    if (kSmemCSR) {
+        for (int i = threadIdx.x; i <= n; i += blockDim.x) s_rowp[i] = a.csr.rowp[noff + i] - e0;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            s_split[i] = a.csr.split[noff + i] - e0;
+            s_order[i] = (uint16_t)a.csr.order[noff + i];
+        }
+        const int nnz_g = a.csr.rowp[noff + n] - e0;
+        for (int e = threadIdx.x; e < nnz_g; e += blockDim.x) {
+            const uint32_t cw = a.csr.col[e0 + e];
+            s_col[e] = (uint16_t)(((cw & ~kSignBit) - (uint32_t)noff) | ((cw & kSignBit) ? kLocalSign : 0u));
+        }
+    }
+    for (int i = i_begin; i < n; i += NS) {
+        const uint4 x = draw_block(P.seed, (uint32_t)g, kStreamInit, (uint32_t)i, 0, (uint32_t)rq);
+        const float4 th = make_float4(u01(x.x), u01(x.y), u01(x.z), u01(x.w));
+        *reinterpret_cast<float4*>(theta + (size_t)(noff + i) * R_pad) = th;
+        const float2 cs[4] = {M::cs(th.x), M::cs(th.y), M::cs(th.z), M::cs(th.w)};
+        cache[i * units + u] = Quad::pack(cs);
+    }
+    __syncthreads();
+
+    const float sdt = P.sqrt_dt;
+    const size_t sbase = (size_t)g * P.steps;
+    int64_t next_readout = a.readout_every > 0 ? a.readout_every : -1;
+    for (int64_t t = 0; t < P.steps; ++t) {
+        const float K = __ldg(P.K + sbase + t), Ks = __ldg(P.Ks + sbase + t);
+        const float Kn = __ldg(P.Kn + sbase + t);
+        const float dtK = P.dt * K, dtKs = P.dt * Ks, kick = Kn * sdt;
+        for (int slot_i = i_begin; slot_i < n; slot_i += NS) {
+            // nodes in order of degree, so the lanes of a warp run rows of equal length
+            const int i = kSmemCSR ? (int)s_order[slot_i] : a.csr.order[noff + slot_i];
+            const int node = noff + i;
+            const float4 th = *reinterpret_cast<const float4*>(theta + (size_t)node * R_pad);
+            float2 own[4];
+            Quad::unpack(cache[i * units + u], own);
+            float2 acc[4];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[v] = make_float2(0.f, 0.f);
+            if (kSmemCSR) {
+                // rows hold the +1 entries first, then the -1 entries
+                const int eb = s_rowp[i], es = s_split[i], ee = s_rowp[i + 1];
+                const T* row = cache + u;
+#pragma unroll 4
+                for (int e = eb; e < es; ++e)
+                    Quad::accumulate(acc, row[(s_col[e] & 0x7FFFu) * units]);
+                if (es < ee) {   // -1 entries: -( -acc + sum )
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) acc[v] = make_float2(-acc[v].x, -acc[v].y);
+#pragma unroll 4
+                    for (int e = es; e < ee; ++e)
+                        Quad::accumulate(acc, row[(s_col[e] & 0x7FFFu) * units]);
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) acc[v] = make_float2(-acc[v].x, -acc[v].y);
+                }
+            } else {
+                const int ee = __ldg(a.csr.rowp + node + 1);
+                for (int e = __ldg(a.csr.rowp + node); e < ee; ++e) {
+                    const uint32_t cw = __ldg(a.csr.col + e);
+                    float w;
+                    int jj;
+                    if (kUnit) {
+                        jj = (int)(cw & ~kSignBit) - noff;
+                        w = (cw & kSignBit) ? -1.0f : 1.0f;
+                    } else {
+                        jj = (int)cw - noff;
+                        w = __ldg(a.csr.w + e);
+                    }
+                    float2 nb[4];
+                    Quad::unpack(cache[jj * units + u], nb);
+                    const float2 ww = make_float2(w, w);
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) acc[v] = ffma2(nb[v], ww, acc[v]);
+                }
+            }
+            const uint4 x = draw_block(P.seed, (uint32_t)g, kStreamNoise, (uint32_t)i, (uint32_t)t,
+                                       (uint32_t)rq);
+            const float2 z01 = M::bm(x.x, x.y);
+            const float2 z23 = M::bm(x.z, x.w);
+            const float z[4] = {z01.x, z01.y, z23.x, z23.y};
+            const float t0[4] = {th.x, th.y, th.z, th.w};
+            float tn[4];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const float d = own[v].y * acc[v].x - own[v].x * acc[v].y;
+                tn[v] = wrap01(t0[v] + (dtK * d - dtKs * sin_q(P.q, own[v].x, own[v].y)) + kick * z[v]);
+            }
+            *reinterpret_cast<float4*>(theta + (size_t)node * R_pad) = make_float4(tn[0], tn[1], tn[2], tn[3]);
+        }
+        __syncthreads();
+        for (int i = i_begin; i < n; i += NS) {
+            const float4 th = *reinterpret_cast<const float4*>(theta + (size_t)(noff + i) * R_pad);
+            const float2 cs[4] = {M::cs(th.x), M::cs(th.y), M::cs(th.z), M::cs(th.w)};
+            cache[i * units + u] = Quad::pack(cs);
+        }
+        __syncthreads();
+
+        if (t + 1 == next_readout) {
+            const int64_t k = next_readout / a.readout_every - 1;
+            next_readout += a.readout_every;
+            if (threadIdx.x < kk) red[threadIdx.x] = 0.0;
+            for (int i = i_begin; i < n; i += NS) {
+                const float4 th = *reinterpret_cast<const float4*>(theta + (size_t)(noff + i) * R_pad);
+                char4 sp;
+                sp.x = (char)spin_of(th.x, P.q);
+                sp.y = (char)spin_of(th.y, P.q);
+                sp.z = (char)spin_of(th.z, P.q);
+                sp.w = (char)spin_of(th.w, P.q);
+                *reinterpret_cast<char4*>(a.spins + (size_t)(noff + i) * R_pad + r0 + 4 * u) = sp;
+            }
+            __syncthreads();
+            float f[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int i = i_begin; i < n; i += NS) {
+                const int node = noff + i;
+                const char4 si = *reinterpret_cast<const char4*>(a.spins + (size_t)node * R_pad + r0 + 4 * u);
+                const int eb = kSmemCSR ? s_rowp[i] : a.csr.rowp[node] - e0;
+                const int ee = kSmemCSR ? s_rowp[i + 1] : a.csr.rowp[node + 1] - e0;
+                for (int e = eb; e < ee; ++e) {
+                    int jl;
+                    float w;
+                    if (kSmemCSR) {
+                        const uint32_t c = s_col[e];
+                        jl = (int)(c & 0x7FFFu);
+                        w = (c & kLocalSign) ? -1.0f : 1.0f;
+                    } else {
+                        const uint32_t cw = a.csr.col[e0 + e];
+                        jl = (int)(kUnit ? (cw & ~kSignBit) : cw) - noff;
+                        w = kUnit ? ((cw & kSignBit) ? -1.0f : 1.0f) : a.csr.w[e0 + e];
+                    }
+                    if (jl <= i) continue;
+                    const char4 sj = *reinterpret_cast<const char4*>(a.spins + (size_t)(noff + jl) * R_pad + r0 + 4 * u);
+                    f[0] += (si.x == sj.x) ? w : 0.f;
+                    f[1] += (si.y == sj.y) ? w : 0.f;
+                    f[2] += (si.z == sj.z) ? w : 0.f;
+                    f[3] += (si.w == sj.w) ? w : 0.f;
+                }
+            }
+            if ((units & (units - 1)) == 0 && units <= 32) {
+                // lanes lane ^ m (m >= units) hold the same replicas: reduce before the atomics
+                // (idle lanes carry zeros; integer-valued sums stay exact in FP32 up to 2^24)
+#pragma unroll
+                for (int m = 16; m >= 1; m >>= 1)
+                    if (m >= units)
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) f[v] += __shfl_xor_sync(0xffffffffu, f[v], m);
+                if ((threadIdx.x & 31) < units && slot < NS) {
+#pragma unroll
+                    for (int v = 0; v < 4; ++v)
+                        if (f[v] != 0.f) atomicAdd(&red[4 * u + v], (double)f[v]);
+                }
+            } else if (slot < NS) {
+#pragma unroll
+                for (int v = 0; v < 4; ++v)
+                    if (f[v] != 0.f) atomicAdd(&red[4 * u + v], (double)f[v]);
+            }
+            __syncthreads();
+            if (threadIdx.x < kk)
+                a.agree[((int64_t)g * a.row_stride + k) * R_pad + r0 + threadIdx.x] = red[threadIdx.x];
+        }
+    }
+}
+
+template <typename Quad, bool kSmemCSR, bool kUnit>
+cudaError_t launch_quad(const ResidentArgs& a, int blocks, int threads, size_t smem, cudaStream_t s) {
+    auto fn = resident_quad_kernel<Quad, kSmemCSR, kUnit>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    fn<<<blocks, threads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename Quad>
+cudaError_t launch_quad_v(bool smem_csr, bool unit, const ResidentArgs& a, int blocks, int threads,
+                          size_t smem, cudaStream_t s) {
+    if (smem_csr) return launch_quad<Quad, true, true>(a, blocks, threads, smem, s);
+    return unit ? launch_quad<Quad, false, true>(a, blocks, threads, smem, s)
+                : launch_quad<Quad, false, false>(a, blocks, threads, smem, s);
+}
+
 }  // namespace
 
 size_t resident_cache_bytes(int32_t prec) { return prec == OIM_PREC_FP32 ? 8 : 4; }
 
 constexpr size_t kSmemBudget = 227 * 1024 - 1024;
 
-// Shape of a resident launch: replicas per block k (at most 64; even unless a
-// single replica is all that fits), threads and dynamic shared memory.  Fails
-// when not even one replica of the largest graph fits in shared memory.
-cudaError_t resident_shape(const oim_problem_s& p, int32_t R_pad, int32_t prec, int32_t want_k,
-                           int32_t want_threads, int32_t* k_out, int32_t* threads_out,
-                           int32_t* items_out, size_t* smem_out) {
+// Cost of one block (relative units) holding k replicas of graph g for one step:
+// per node-replica work (noise, trig, update) plus per edge-update work.
+static double block_cost(const GraphDev& gd, int64_t nnz_g, int k, int32_t prec) {
+    const double per_node = 60.0, per_edge = (prec == OIM_PREC_FP32) ? 3.0 : 2.6;
+    return (double)k * ((double)gd.n * per_node + (double)nnz_g * per_edge);
+}
+
+// Plan a resident launch: the kernel variant, per-graph replicas per block and
+// the block list.  Quad kernel when four replicas of the largest graph fit;
+// otherwise the pair/single kernel.  Without a requested k, each graph gets the
+// k (multiple of the unit) that makes every block cost about the same while
+// the whole grid stays within one wave of the SMs, as far as shared memory allows.
+cudaError_t plan_resident(const oim_problem_s& p, int32_t R_pad, int32_t prec, int32_t want_k,
+                          int32_t want_threads, ResidentPlan* plan) {
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const size_t rep_bytes = resident_cache_bytes(prec) * (size_t)p.max_n;
-    int k_fit = (int)std::min<size_t>(64, kSmemBudget / rep_bytes);
-    if (k_fit >= 2) k_fit &= ~1;
-    if (k_fit < 1) return cudaErrorInvalidValue;
-    int k;
-    if (want_k > 0) {
-        k = want_k;
-        if (k > k_fit || (k > 1 && (k & 1))) return cudaErrorInvalidValue;
-    } else {
-        // enough blocks to give every SM one, as few replicas per block as that allows
-        const int64_t total = (int64_t)p.G * R_pad;
-        const int64_t per = (total + sms - 1) / sms;
-        k = (int)std::min<int64_t>(k_fit, std::max<int64_t>(1, per));
-        if (k > 1) k = std::min(k_fit, (k + 1) & ~1);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        sms = 148;
     }
-    k = std::min(k, R_pad);
-    const int U = (k % 2 == 0) ? 2 : 1;
-    const int units = k / U;
+    const size_t cb = resident_cache_bytes(prec);
+    const int G = p.G;
+    std::vector<int64_t> nnz_g(G);
+    for (int g = 0; g < G; ++g) {
+        const int64_t end = (g + 1 < G) ? p.graphs[g + 1].edge_off : p.nnz;
+        nnz_g[g] = end - p.graphs[g].edge_off;
+    }
+    // can the structure go to shared memory?  (+-1 weights, 15-bit local indices)
+    bool csr_ok = p.unit_weights;
+    std::vector<size_t> csr_bytes(G, 0);
+    for (int g = 0; g < G; ++g) {
+        if (p.graphs[g].n > 32767) csr_ok = false;
+        csr_bytes[g] = align16((size_t)(p.graphs[g].n + 1) * 4) + align16((size_t)p.graphs[g].n * 4) +
+                       align16((size_t)p.graphs[g].n * 2) + align16((size_t)nnz_g[g] * 2);
+    }
+    auto k_fit = [&](int g, bool with_csr) -> int {
+        const size_t avail = kSmemBudget - (with_csr ? csr_bytes[g] : 0);
+        if (avail > kSmemBudget) return 0;
+        return (int)std::min<size_t>(64, avail / (cb * (size_t)p.graphs[g].n));
+    };
+    // unit: 4 (quad kernel) when every graph fits a quad, else 2 or 1
+    int unit = 4;
+    bool use_csr = csr_ok;
+    for (int g = 0; g < G; ++g) {
+        if (use_csr && k_fit(g, true) < 4) use_csr = false;
+    }
+    for (int g = 0; g < G; ++g) {
+        const int f = k_fit(g, use_csr);
+        if (f < unit) unit = f >= 2 ? 2 : (f >= 1 ? 1 : 0);
+    }
+    if (unit == 0) return cudaErrorInvalidValue;
+    if (unit < 4) use_csr = false;
+    std::vector<int> kg(G);
+    for (int g = 0; g < G; ++g) kg[g] = (k_fit(g, use_csr) / unit) * unit;
+    if (want_k > 0) {
+        if (want_k % unit != 0) return cudaErrorInvalidValue;
+        for (int g = 0; g < G; ++g) {
+            if (want_k > kg[g]) return cudaErrorInvalidValue;
+            kg[g] = want_k;
+        }
+    } else {
+        // balance: smallest per-block cost tau such that the blocks fit in one wave
+        auto blocks_for = [&](double tau, std::vector<int>& ks) {
+            int64_t total = 0;
+            for (int g = 0; g < G; ++g) {
+                int k = unit;
+                while (k + unit <= kg[g] && block_cost(p.graphs[g], nnz_g[g], k + unit, prec) <= tau)
+                    k += unit;
+                ks[g] = std::min(k, std::max(unit, R_pad));
+                total += (R_pad + ks[g] - 1) / ks[g];
+            }
+            return total;
+        };
+        std::vector<int> ks(G);
+        double lo = 0.0, hi = 0.0;
+        for (int g = 0; g < G; ++g) hi = std::max(hi, block_cost(p.graphs[g], nnz_g[g], kg[g], prec));
+        if (blocks_for(hi, ks) > sms) {
+            blocks_for(hi, kg);   // more than one wave even at the largest k
+        } else {
+            for (int it = 0; it < 60; ++it) {
+                const double mid = 0.5 * (lo + hi);
+                if (blocks_for(mid, ks) <= sms) hi = mid; else lo = mid;
+            }
+            blocks_for(hi, kg);
+        }
+    }
+    plan->unit = unit;
+    plan->csr_smem = use_csr;
+    plan->k_of_graph = kg;
+    plan->items.clear();
+    size_t smem = 0;
+    int max_units = 1;
+    std::vector<std::pair<double, int4>> order;
+    for (int g = 0; g < G; ++g) {
+        const int k = std::min(kg[g], R_pad);
+        for (int r0 = 0; r0 < R_pad; r0 += k) {
+            const int kk = std::min(k, R_pad - r0);
+            order.push_back({block_cost(p.graphs[g], nnz_g[g], kk, prec), make_int4(g, r0, kk, 0)});
+        }
+        smem = std::max(smem, (unit == 4 ? align16(cb * (size_t)p.graphs[g].n * k) : cb * (size_t)p.graphs[g].n * k) +
+                                  (use_csr ? csr_bytes[g] : 0));
+        max_units = std::max(max_units, k / unit);
+    }
+    // longest blocks first, so that a second wave (if any) fills in behind them
+    std::stable_sort(order.begin(), order.end(),
+                     [](const std::pair<double, int4>& x, const std::pair<double, int4>& y) {
+                         return x.first > y.first;
+                     });
+    for (auto& o : order) plan->items.push_back(o.second);
     int threads = want_threads > 0 ? want_threads : 1024;
-    threads = std::min(1024, std::max(threads, 32 * ((units + 31) / 32)));
-    // no more threads than (node, unit) items of the largest graph
-    const int64_t work = (int64_t)p.max_n * units;
-    if (want_threads <= 0 && work < threads) threads = std::max(32, (int)((work + 31) / 32) * 32);
-    int items = 0;
-    for (int g = 0; g < p.G; ++g) items += (R_pad + k - 1) / k;
-    *k_out = k;
-    *threads_out = threads;
-    *items_out = items;
-    *smem_out = rep_bytes * (size_t)k;
+    threads = std::min(1024, std::max(threads, 32 * ((max_units + 31) / 32)));
+    if (want_threads <= 0) {
+        const int64_t work = (int64_t)p.max_n * max_units;
+        if (work < threads) threads = std::max(32, (int)((work + 31) / 32) * 32);
+    }
+    plan->threads = threads;
+    plan->smem = smem;
     return cudaSuccess;
 }
 
@@ -323,13 +707,21 @@ cudaError_t launch_resident_impl(const oim_run_s& r, const int4* d_items, cudaSt
     a.agree = r.d_trace;
     a.row_stride = r.readouts_cap;
     a.readout_every = r.readout_every;
-    const int U = (r.res_k % 2 == 0) ? 2 : 1;
+    const ResidentPlan& pl = r.plan;
+    const int blocks = (int)pl.items.size();
     const bool unit = r.p->unit_weights;
+    if (pl.unit == 4) {
+        if (r.prec == OIM_PREC_FP32)
+            return launch_quad_v<QuadF32>(pl.csr_smem, unit, a, blocks, pl.threads, pl.smem, s);
+        if (r.prec == OIM_PREC_FP16)
+            return launch_quad_v<QuadF16>(pl.csr_smem, unit, a, blocks, pl.threads, pl.smem, s);
+        return launch_quad_v<QuadBF16>(pl.csr_smem, unit, a, blocks, pl.threads, pl.smem, s);
+    }
     if (r.prec == OIM_PREC_FP32)
-        return launch_u<CacheF32>(U, unit, a, r.res_items, r.res_threads, r.res_smem, s);
+        return launch_u<CacheF32>(pl.unit, unit, a, blocks, pl.threads, pl.smem, s);
     if (r.prec == OIM_PREC_FP16)
-        return launch_u<CacheF16>(U, unit, a, r.res_items, r.res_threads, r.res_smem, s);
-    return launch_u<CacheBF16>(U, unit, a, r.res_items, r.res_threads, r.res_smem, s);
+        return launch_u<CacheF16>(pl.unit, unit, a, blocks, pl.threads, pl.smem, s);
+    return launch_u<CacheBF16>(pl.unit, unit, a, blocks, pl.threads, pl.smem, s);
 }
 
 }  // namespace oim

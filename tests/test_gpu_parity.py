@@ -54,6 +54,21 @@ def test_noise_draws_match_oracle(orc, form):
     assert np.max(np.abs(xi - ref)) <= 4e-6
 
 
+@pytest.mark.parametrize("precision", ["fp16", "bf16"])
+def test_fast_noise_draws_of_16bit_forms(orc, precision):
+    # the 16-bit forms draw Box-Muller with the hardware log2 / sqrt / sin / cos
+    n, R, kick = 2000, 64, 0.05
+    g = csr_from_edges(n, np.zeros(0, int), np.zeros(0, int))
+    run = gpu_run(g, 2, 0.0, 0.0, kick, 1.0, 1, R, seed=6, form="resident", precision=precision)
+    th1 = run.phases()[0].astype(np.float64)
+    th0 = orc.init_phases(n, R, 6)
+    err = np.abs(circ(th1 - th0) / kick - orc.noise_block(n, R, 6, 0))
+    print(f"fast Box-Muller |dxi|: max {err.max():.3e}  p99.99 {np.quantile(err, 0.9999):.3e}  "
+          f"median {np.median(err):.3e}")
+    assert np.quantile(err, 0.9999) <= 5e-6
+    assert err.max() <= 2e-5
+
+
 def test_drift_matches_fp64(orc, c1):
     from paper_2505_22631_gb300 import Problem, oim_debug_derivative
     g = c1.graphs[0]
@@ -122,14 +137,31 @@ def test_forms_agree(c1):
     assert rad_dist(a, b).max() <= 1e-4
 
 
-def test_resident_block_shape_does_not_change_results(c1):
+@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+def test_resident_block_shape_does_not_change_results(c1, precision):
     g = c1.graphs[0]
-    T, R = 200, 16
+    T, R = 200, 24
     args = (g, 2, c1.K[0][:T], c1.Ks[0][:T], c1.Kn[0][:T], c1.dt, T, R, 9)
-    a = gpu_run(*args, form="resident", replicas_per_block=2).phases()[0]
-    b = gpu_run(*args, form="resident", replicas_per_block=16, threads_per_block=256).phases()[0]
-    c = gpu_run(*args, form="resident", replicas_per_block=6).phases()[0]
-    assert np.array_equal(a, b) and np.array_equal(a, c)
+    kw = dict(form="resident", precision=precision, readout_every=50)
+    a = gpu_run(*args, replicas_per_block=4, **kw)
+    b = gpu_run(*args, replicas_per_block=16, threads_per_block=256, **kw)
+    c = gpu_run(*args, replicas_per_block=12, **kw)
+    assert np.array_equal(a.phases()[0], b.phases()[0])
+    assert np.array_equal(a.phases()[0], c.phases()[0])
+    assert np.array_equal(a.readout()["trace"], c.readout()["trace"])
+
+
+def test_resident_pair_kernel_for_mid_size_graph(orc):
+    g = torus(100, 100, 6, "pm1")   # 10000 nodes: two FP32 replicas per block, not four
+    T, R = 20, 6
+    K, Ks, Kn = constant(T, 4.0), linear_ramp(T, 0, 1), constant(T, 0.1)
+    run = gpu_run(g, 2, K, Ks, Kn, 0.01, T, R, 2, form="resident", readout_every=10)
+    ref = oracle_phases(orc, g, 2, K, Ks, Kn, 0.01, T, R, 2, nthreads=8)
+    th = run.phases()[0]
+    assert rad_dist(th, ref).max() <= 1e-3
+    out = run.readout()
+    assert np.array_equal(out["score"][0], orc.scores(g, 2, orc.readout_f32(2, th)))
+    assert np.array_equal(out["trace"][0, -1], out["score"][0])
 
 
 def test_stream_graph_capture_matches_direct_launches(c1):
