@@ -207,6 +207,42 @@ int oim_debug_derivative(oim_problem_t p, const float* theta, int32_t replicas, 
 
 void oim_destroy_run(oim_run_t r);
 
+/*
+ * oim_score_phases_noalloc -- the cut / conflict scores of oim_readout, for
+ * phases the caller supplies, computed without allocating any device memory.
+ * (The paper has no counterpart: this is an interface for embedding.)
+ *
+ * Some callers cannot have a library call cudaMalloc or cudaFree: a server that
+ * reserves all device memory up front and runs with a fixed footprint, an
+ * application whose own allocator (a caching or arena allocator) owns every
+ * byte of the device, or code on a latency path that cannot afford the device
+ * synchronisation an allocation may cause.  This entry point uses only the
+ * memory the caller passes plus a fixed scratch area that lives in the library
+ * itself: OIM_NOALLOC_MAX_ACCUM doubles (1 MiB) of file-scope device memory,
+ * held by every GPU that loads the library until the process exits.
+ *
+ *   p         problem (one graph or a batch) whose graph is on the device
+ *             (not created with OIM_FLAG_DEFER_UPLOAD, or already run once)
+ *   theta     device float[nodes][ld]: phase of replica r of global node v
+ *             (graphs concatenated in batch order) at theta[v * ld + r], in [0,1)
+ *   replicas  1 <= replicas <= ld;  ld a multiple of 4
+ *   score     device double[graphs][replicas]: as oim_readout's score (spins
+ *             thresholded in FP32, cut for q == 2, conflict weight for q >= 3)
+ *   stream    cudaStream_t to queue the work on (NULL = legacy default stream)
+ * The work is queued asynchronously; score is valid once the stream is synchronised.
+ * Errors: OIM_EINVAL (NULL or host pointers, bad replicas / ld, or
+ * graphs * ld > OIM_NOALLOC_MAX_ACCUM), OIM_ESTATE (graph not on the device),
+ * OIM_ECUDA.
+ * Every call shares the one scratch area and clears the part it uses before
+ * use; calls whose work overlaps on the GPU (other streams, other host threads)
+ * race on it and must be serialised by the caller.  The first call on a device
+ * looks up the scratch area's device address (once per device, with that device
+ * current); make that first call before any stream capture.
+ */
+#define OIM_NOALLOC_MAX_ACCUM 131072
+int oim_score_phases_noalloc(oim_problem_t p, const float* theta, int32_t replicas, int32_t ld,
+                             double* score, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -35,6 +35,8 @@ OIM_PREC_BF16 = 2
 OIM_PREC_FP16 = 3
 
 OIM_FLAG_SKIP_SYMMETRY_CHECK = 1
+OIM_FLAG_DEFER_UPLOAD = 2
+OIM_NOALLOC_MAX_ACCUM = 131072
 
 FORMS = {"auto": OIM_FORM_AUTO, "stream": OIM_FORM_STREAM, "resident": OIM_FORM_RESIDENT,
          "gemm": OIM_FORM_GEMM}
@@ -84,6 +86,7 @@ SIGNATURES = {
     "oim_get_phases": (ctypes.c_int, [_vp, _vp]),
     "oim_debug_derivative": (ctypes.c_int, [_vp, _vp, _i32, _f32, _f32, _vp]),
     "oim_destroy_run": (None, [_vp]),
+    "oim_score_phases_noalloc": (ctypes.c_int, [_vp, _vp, _i32, _i32, _vp, _vp]),
 }
 
 _lock = threading.Lock()
@@ -228,3 +231,9 @@ def oim_debug_derivative(p, theta, replicas, K, Ks, f_out):
 def oim_destroy_run(r):
     if r:
         load().oim_destroy_run(r)
+
+
+def oim_score_phases_noalloc(p, theta, replicas, ld, score, stream=None):
+    """Scores of caller-supplied device phases [nodes][ld]; allocates no device memory."""
+    _check(load().oim_score_phases_noalloc(p, ptr(theta, np.float32), int(replicas), int(ld),
+                                           ptr(score, np.float64), stream))
