@@ -47,6 +47,36 @@ def load_peaks():
         return p
 
 
+KERNEL_SOURCES = ["paper_2505_22631_gb300/csrc/step_resident.cu",
+                  "paper_2505_22631_gb300/csrc/oim_device.cuh",
+                  "paper_2505_22631_gb300/csrc/step_stream.cu"]
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha1()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel, workload):
+    """DRAM bytes per launch of `kernel` on `workload` from a committed ncu summary,
+    or None when no summary matches the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    want = kernel_source_hash()
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        f = dict(kv.split("=", 1) for kv in line.split())
+        if f.get("kernel") == kernel and f.get("workload") == workload and f.get("sources") == want:
+            return float(f["dram_bytes_per_launch"])
+    return None
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -292,18 +322,25 @@ def main():
     edge_updates = w.edge_updates() * world
     value = edge_updates / (ms_step / 1e3)
 
-    # roofline of the dominant kernel (one launch per step in the resident form)
+    # roofline of the dominant kernel.  Algorithmic bytes per node-replica-step
+    # are the state a step must move if nothing stays on chip: read and write the
+    # phase (4 + 4 B), write and read the (cos, sin) cache (8 + 8 B in FP32, 4 + 4 B
+    # in 16 bits), plus the CSR structure once per graph and step.
     peaks = load_peaks()
     node_replica_steps = w.nodes * w.replicas * w.steps
     csr_bytes = sum(4 * g.nnz + 8 * (g.n + 1) for g in w.graphs) * w.steps
-    bytes_per_unit = 24 if info["precision"] in (1,) else 16
+    bytes_per_unit = 24 if info["precision"] == 1 else 16
     alg_bytes = node_replica_steps * bytes_per_unit + csr_bytes
     achieved = alg_bytes / (ms_step / 1e3) / 1e9
+    prec_name = {1: "fp32", 2: "bf16", 3: "fp16"}.get(info["precision"])
+    kname = (f"resident_quad_kernel<{prec_name}>" if info["form"] == 2 else "step_stream_kernel")
+    traffic = profiled_traffic(kname, w.name)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-                "kernel": "resident_kernel" if info["form"] == 2 else "step_stream_kernel",
-                "peak_source": peaks["source"],
-                "algorithmic_bytes_per_launch": alg_bytes}
+                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "kernel": kname,
+                "peak_source": peaks["source"], "algorithmic_bytes_per_launch": alg_bytes,
+                "bytes_per_node_replica_step": bytes_per_unit,
+                "kernel_time": "CUDA events around each run (one launch of the resident "
+                               "kernel plus a 1.6 MB memset and schedule copies)"}
 
     # end to end through the C ABI with host buffers: upload graphs and schedules,
     # simulate, read spins and scores back, free everything
