@@ -205,6 +205,21 @@ int oim_get_phases(oim_run_t r, float* theta);
 int oim_debug_derivative(oim_problem_t p, const float* theta, int32_t replicas, float K, float Ks,
                          float* f_out);
 
+/*
+ * oim_backward -- gradients of the relaxed loss L_g = (1/R) sum_r E_g(theta_T^r)
+ * (Eq. 6 energy of the final phases, before thresholding) with respect to the
+ * per-step schedules K_t, Ks_t, Kn_t of each graph, by the adjoint of the
+ * forward-Euler map of Algorithm 1 (pattern "differentiable schedules": the
+ * paper tunes K, Ks, Kn by hand, Sec. IV-B).  The noise enters pathwise: the
+ * gradient is that of the trajectory with the run's own Philox draws.
+ * The run must use the stream form in FP32 with checkpoint_every > 0; phases are
+ * recomputed between checkpoints, so memory is checkpoint_every x state.
+ *   dK, dKs, dKn  double[graphs][steps] each (host or device, may be NULL)
+ *   loss          double[graphs] (host or device, may be NULL): L_g
+ * Synchronous.  Errors: OIM_ESTATE (no checkpoints, wrong form), OIM_ENOMEM, OIM_ECUDA.
+ */
+int oim_backward(oim_run_t r, double* dK, double* dKs, double* dKn, double* loss);
+
 void oim_destroy_run(oim_run_t r);
 
 /*

@@ -85,6 +85,7 @@ SIGNATURES = {
     "oim_run_info": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "oim_get_phases": (ctypes.c_int, [_vp, _vp]),
     "oim_debug_derivative": (ctypes.c_int, [_vp, _vp, _i32, _f32, _f32, _vp]),
+    "oim_backward": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "oim_destroy_run": (None, [_vp]),
     "oim_score_phases_noalloc": (ctypes.c_int, [_vp, _vp, _i32, _i32, _vp, _vp]),
 }
@@ -226,6 +227,11 @@ def oim_get_phases(r, theta):
 def oim_debug_derivative(p, theta, replicas, K, Ks, f_out):
     _check(load().oim_debug_derivative(p, ptr(theta, np.float32), int(replicas), float(K),
                                        float(Ks), ptr(f_out, np.float32)))
+
+
+def oim_backward(r, dK=None, dKs=None, dKn=None, loss=None):
+    _check(load().oim_backward(r, ptr(dK, np.float64), ptr(dKs, np.float64), ptr(dKn, np.float64),
+                               ptr(loss, np.float64)))
 
 
 def oim_destroy_run(r):

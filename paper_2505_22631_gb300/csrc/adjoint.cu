@@ -1,0 +1,187 @@
+// adjoint.cu -- gradients of the relaxed energy with respect to the schedules.
+//
+// Loss of graph g: L_g = (1/R) sum_r E_g(theta_T^r), E of Eq. 6 on the final
+// phases.  The forward map of one step (Algorithm 1, Eq. 5) is
+//   theta_{t+1} = wrap(theta_t + dt f(theta_t; K_t, Ks_t) + Kn_t sqrt(dt) xi_t),
+// whose wrap has unit derivative (every function of the phases is 1-periodic).
+// With lambda_t = dL/dtheta_t:
+//   lambda_T   = -(2 pi / R) D(theta_T),  D_i = sum_j w_ij sin 2 pi (theta_i - theta_j)
+//   lambda_t,j = lambda_{t+1,j} + dt [ lambda_{t+1,j} (2 pi K_t S_j - 2 pi q Ks_t cos 2 pi q theta_j)
+//                                      - 2 pi K_t C_j ]
+//   S_j = sum_k w_jk cos 2 pi (theta_j - theta_k) = c_j A_j + s_j B_j
+//   C_j = sum_k w_jk lambda_{t+1,k} cos 2 pi (theta_k - theta_j) = c_j P_j + s_j Q_j
+// where (A, B, P, Q)_j = sum_k w_jk (c_k, s_k, lambda_k c_k, lambda_k s_k), all at theta_t.
+// Schedule gradients, summed over nodes and replicas of each graph in FP64:
+//   dL/dK_t = dt sum lambda_{t+1} D(theta_t),  dL/dKs_t = -dt sum lambda_{t+1} sin 2 pi q theta_t,
+//   dL/dKn_t = sqrt(dt) sum lambda_{t+1} xi_t  (pathwise: the same Philox draws as the forward).
+// Layout as the stream form: [node][R_pad], replicas contiguous, a thread per (node, quad).
+#include "oim_device.cuh"
+#include "oim_internal.h"
+
+namespace oim {
+
+namespace {
+
+constexpr float kTwoPi = 6.28318530717958647f;
+
+// (c, s, lambda c, lambda s) of every node-replica at theta_t.
+__global__ void __launch_bounds__(256) adj_prep_kernel(int nodes, int R_pad, const float* __restrict__ theta,
+                                                       const float* __restrict__ lam, float4* __restrict__ Y) {
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= (int64_t)nodes * R_pad) return;
+    float s, c;
+    sincospif(2.0f * theta[gid], &s, &c);
+    const float l = lam[gid];
+    Y[gid] = make_float4(c, s, l * c, l * s);
+}
+
+// D(theta) * scale into lam (the terminal adjoint, scale = -2 pi / R), and the
+// per-graph FP64 sum of E = 1/2 sum_i (c_i A_i + s_i B_i) over the real replicas.
+__global__ void __launch_bounds__(256) adj_terminal_kernel(CSRDev csr, int R, int R_pad, float scale,
+                                                           const float4* __restrict__ Y,
+                                                           float* __restrict__ lam,
+                                                           double* __restrict__ loss) {
+    const int quads = R_pad >> 2;
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double e = 0.0;
+    int g = -1;
+    if (gid < (int64_t)csr.nodes * quads) {
+        const int node = (int)(gid / quads);
+        const int quad = (int)(gid - (int64_t)node * quads);
+        g = csr.node_graph[node];
+        const size_t at = (size_t)node * R_pad + 4 * quad;
+        float A[4] = {0, 0, 0, 0}, B[4] = {0, 0, 0, 0};
+        for (int ei = csr.rowp[node]; ei < csr.rowp[node + 1]; ++ei) {
+            const uint32_t cw = csr.col[ei];
+            const uint32_t j = csr.w ? cw : (cw & ~kSignBit);
+            const float w = csr.w ? csr.w[ei] : ((cw & kSignBit) ? -1.0f : 1.0f);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const float4 y = Y[(size_t)j * R_pad + 4 * quad + v];
+                A[v] = fmaf(w, y.x, A[v]);
+                B[v] = fmaf(w, y.y, B[v]);
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const float4 y = Y[at + v];
+            lam[at + v] = scale * (y.y * A[v] - y.x * B[v]);
+            if (4 * quad + v < R) e += 0.5 * (double)(y.x * A[v] + y.y * B[v]);
+        }
+    }
+    // block reduce per graph: blocks may straddle graphs, so reduce by atomics per thread group
+    if (g >= 0 && e != 0.0) atomicAdd(loss + g, e);
+}
+
+// One adjoint step: lambda_out = lambda_t from lambda_in = lambda_{t+1} at theta_t,
+// and the step's gradient terms added to dK[g][t], dKs[g][t], dKn[g][t].
+__global__ void __launch_bounds__(256) adj_step_kernel(CSRDev csr, StepParams P, int64_t t,
+                                                       const float* __restrict__ theta,
+                                                       const float4* __restrict__ Y,
+                                                       const float* __restrict__ lam_in,
+                                                       float* __restrict__ lam_out,
+                                                       double* __restrict__ dK, double* __restrict__ dKs,
+                                                       double* __restrict__ dKn, int64_t T) {
+    const int quads = P.R_pad >> 2;
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = gid < (int64_t)csr.nodes * quads;   // no early exit: the warp shuffles below
+    int g = -1;
+    double gK = 0.0, gS = 0.0, gN = 0.0;
+    if (valid) {
+        const int node = (int)(gid / quads);
+        const int quad = (int)(gid - (int64_t)node * quads);
+        g = csr.node_graph[node];
+        const int i = node - csr.graphs[g].node_off;
+        const size_t sidx = (size_t)g * P.steps + t;
+        const float K = P.K[sidx], Ks = P.Ks[sidx];
+        const size_t at = (size_t)node * P.R_pad + 4 * quad;
+        float A[4] = {0, 0, 0, 0}, B[4] = {0, 0, 0, 0}, Pp[4] = {0, 0, 0, 0}, Q[4] = {0, 0, 0, 0};
+        for (int ei = csr.rowp[node]; ei < csr.rowp[node + 1]; ++ei) {
+            const uint32_t cw = csr.col[ei];
+            const uint32_t j = csr.w ? cw : (cw & ~kSignBit);
+            const float w = csr.w ? csr.w[ei] : ((cw & kSignBit) ? -1.0f : 1.0f);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const float4 y = Y[(size_t)j * P.R_pad + 4 * quad + v];
+                A[v] = fmaf(w, y.x, A[v]);
+                B[v] = fmaf(w, y.y, B[v]);
+                Pp[v] = fmaf(w, y.z, Pp[v]);
+                Q[v] = fmaf(w, y.w, Q[v]);
+            }
+        }
+        const uint4 x = draw_block(P.seed, (uint32_t)g, kStreamNoise, (uint32_t)i, (uint32_t)t,
+                                   (uint32_t)quad);
+        const float2 z01 = box_muller(x.x, x.y);
+        const float2 z23 = box_muller(x.z, x.w);
+        const float z[4] = {z01.x, z01.y, z23.x, z23.y};
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const float4 y = Y[at + v];
+            const float c = y.x, s = y.y;
+            const float l = lam_in[at + v];
+            const float S = c * A[v] + s * B[v];
+            const float Cc = c * Pp[v] + s * Q[v];
+            const float th = theta[at + v];
+            float sq, cq;
+            sincospif(2.0f * (float)P.q * th, &sq, &cq);
+            const float diag = kTwoPi * K * S - kTwoPi * (float)P.q * Ks * cq;
+            lam_out[at + v] = l + P.dt * (l * diag - kTwoPi * K * Cc);
+            if (4 * quad + v < P.R) {
+                const float D = s * A[v] - c * B[v];
+                gK += (double)(l * D);
+                gS += (double)(l * sq);
+                gN += (double)(l * z[v]);
+            }
+        }
+    }
+    // warp reduction when every lane belongs to the same graph, else per-lane atomics
+    const unsigned full = 0xffffffffu;
+    const int g0 = __shfl_sync(full, g, 0);
+    if (__all_sync(full, g == g0)) {
+        for (int m = 16; m >= 1; m >>= 1) {
+            gK += __shfl_xor_sync(full, gK, m);
+            gS += __shfl_xor_sync(full, gS, m);
+            gN += __shfl_xor_sync(full, gN, m);
+        }
+        if ((threadIdx.x & 31) != 0 || g < 0) return;
+    } else if (g < 0) {
+        return;
+    }
+    atomicAdd(dK + (size_t)g * T + t, (double)P.dt * gK);
+    atomicAdd(dKs + (size_t)g * T + t, -(double)P.dt * gS);
+    atomicAdd(dKn + (size_t)g * T + t, (double)P.sqrt_dt * gN);
+}
+
+}  // namespace
+
+StepParams make_params(const oim_run_s& r);
+
+// Y from (theta, lambda).
+cudaError_t launch_adj_prep(const oim_run_s& r, const float* theta, const float* lam, float4* Y,
+                            cudaStream_t s) {
+    const int64_t total = r.p->nodes * r.R_pad;
+    adj_prep_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>((int)r.p->nodes, r.R_pad, theta, lam, Y);
+    return cudaGetLastError();
+}
+
+// lambda_T and the loss sums from Y(theta_T) (its lambda columns are unused).
+cudaError_t launch_adj_terminal(const oim_run_s& r, const float4* Y, float* lam, double* loss,
+                                cudaStream_t s) {
+    const int64_t total = r.p->nodes * (r.R_pad / 4);
+    const float scale = -6.28318530717958647f / (float)r.R;
+    adj_terminal_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(r.p->csr(), r.R, r.R_pad, scale, Y,
+                                                                       lam, loss);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_step(const oim_run_s& r, int64_t t, const float* theta, const float4* Y,
+                            const float* lam_in, float* lam_out, double* dK, double* dKs, double* dKn,
+                            cudaStream_t s) {
+    const StepParams P = make_params(r);
+    const int64_t total = r.p->nodes * (r.R_pad / 4);
+    adj_step_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(r.p->csr(), P, t, theta, Y, lam_in,
+                                                                   lam_out, dK, dKs, dKn, r.steps);
+    return cudaGetLastError();
+}
+
+}  // namespace oim

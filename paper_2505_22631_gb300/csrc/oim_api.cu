@@ -34,6 +34,17 @@ cudaError_t launch_resident_impl(const oim_run_s& r, const int4* d_items, cudaSt
 cudaError_t launch_derivative(const oim_problem_s& p, const float* theta, int32_t R, float K,
                               float Ks, float* f, cudaStream_t s);
 size_t resident_cache_bytes(int32_t prec);
+cudaError_t launch_cs_from_theta(const oim_run_s& r, const float* theta, float2* cs, cudaStream_t s);
+cudaError_t launch_step_stream_buffers(const oim_run_s& r, int64_t t, const float* th_in,
+                                       const float2* cs_in, float* th_out, float2* cs_out,
+                                       cudaStream_t s);
+cudaError_t launch_adj_prep(const oim_run_s& r, const float* theta, const float* lam, float4* Y,
+                            cudaStream_t s);
+cudaError_t launch_adj_terminal(const oim_run_s& r, const float4* Y, float* lam, double* loss,
+                                cudaStream_t s);
+cudaError_t launch_adj_step(const oim_run_s& r, int64_t t, const float* theta, const float4* Y,
+                            const float* lam_in, float* lam_out, double* dK, double* dKs, double* dKn,
+                            cudaStream_t s);
 
 }  // namespace oim
 
@@ -160,6 +171,7 @@ void free_run_buffers(oim_run_s* r) {
     dev_free(r->d_err);
     dev_free(r->d_t0);
     dev_free(r->d_items);
+    dev_free(r->d_ckpt);
     if (r->chunk_exec) cudaGraphExecDestroy(r->chunk_exec);
     r->chunk_exec = nullptr;
 }
@@ -179,6 +191,14 @@ int ensure_step_buffers(oim_run_s* r, int64_t steps) {
         r->steps_cap = std::max<int64_t>(steps, 1);
         OIM_CUDA(dev_alloc(&r->d_sched, (size_t)3 * G * r->steps_cap), "cudaMalloc(schedules)");
     }
+    if (r->ckpt_every > 0) {
+        const int64_t need = steps / r->ckpt_every + 1;
+        if (need > r->ckpt_cap || !r->d_ckpt) {
+            dev_free(r->d_ckpt);
+            r->ckpt_cap = need;
+            OIM_CUDA(dev_alloc(&r->d_ckpt, (size_t)need * r->p->nodes * r->R_pad), "cudaMalloc(checkpoints)");
+        }
+    }
     const int64_t ro_need = n_ro + 1;   // one extra row for the final scores
     if (ro_need > r->readouts_cap || !r->d_trace) {
         dev_free(r->d_trace);
@@ -194,6 +214,14 @@ int choose_form(oim_run_s* r) {
     if (form < OIM_FORM_AUTO || form > OIM_FORM_GEMM) return fail(OIM_EINVAL, "unknown form");
     if (prec < OIM_PREC_AUTO || prec > OIM_PREC_FP16) return fail(OIM_EINVAL, "unknown precision");
     if (form == OIM_FORM_GEMM) return fail(OIM_EUNSUPPORTED, "the tensor-core form is not built");
+    if (r->opts.checkpoint_every < 0) return fail(OIM_EINVAL, "checkpoint_every must be >= 0");
+    if (r->opts.checkpoint_every > 0) {
+        // the adjoint recomputes segments with the stream kernels: the forward uses them too
+        if (form == OIM_FORM_RESIDENT || (prec != OIM_PREC_AUTO && prec != OIM_PREC_FP32))
+            return fail(OIM_EUNSUPPORTED, "checkpoints (for oim_backward) need the FP32 stream form");
+        form = OIM_FORM_STREAM;
+        prec = OIM_PREC_FP32;
+    }
     // AUTO precision: the resident form keeps its (cos, sin) cache in FP16 (twice
     // the replicas per block of FP32, coupling error ~1e-4 relative); the stream
     // form is FP32 only.
@@ -250,12 +278,18 @@ int allocate_run(oim_run_s* r) {
 // readout step.  When capture is on, the whole sequence is recorded once into a
 // CUDA graph (kernel arguments baked in) and replayed on later identical runs.
 int enqueue_stream_form(oim_run_s* r) {
+    const size_t state_bytes = (size_t)r->p->nodes * r->R_pad * sizeof(float);
     auto body = [&](cudaStream_t s) -> cudaError_t {
         cudaError_t e = launch_init_stream(*r, s);
+        if (e == cudaSuccess && r->ckpt_every > 0)
+            e = cudaMemcpyAsync(r->d_ckpt, r->d_theta[0], state_bytes, cudaMemcpyDeviceToDevice, s);
         for (int64_t t = 0; t < r->steps && e == cudaSuccess; ++t) {
             e = launch_step_stream(*r, t, nullptr, s);
             if (e == cudaSuccess && r->readout_every > 0 && (t + 1) % r->readout_every == 0)
                 e = launch_score(*r, r->d_theta[(t + 1) & 1], (t + 1) / r->readout_every - 1, s);
+            if (e == cudaSuccess && r->ckpt_every > 0 && (t + 1) % r->ckpt_every == 0)
+                e = cudaMemcpyAsync(r->d_ckpt + (size_t)((t + 1) / r->ckpt_every) * r->p->nodes * r->R_pad,
+                                    r->d_theta[(t + 1) & 1], state_bytes, cudaMemcpyDeviceToDevice, s);
         }
         return e;
     };
@@ -566,6 +600,7 @@ int oim_run(oim_problem_t p, const float* K, const float* Ks, const float* Kn, f
     r->seed = seed;
     r->dt = dt;
     r->n_readouts = r->readout_every > 0 ? steps / r->readout_every : 0;
+    r->ckpt_every = o.checkpoint_every;
     rc = choose_form(r);
     if (rc == OIM_OK) rc = allocate_run(r);
     if (rc == OIM_OK) rc = ensure_step_buffers(r, steps);
@@ -729,6 +764,90 @@ int oim_debug_derivative(oim_problem_t p, const float* theta, int32_t replicas, 
     cudaFree(d_th);
     if (d_f) cudaFree(d_f);
     if (e != cudaSuccess) return cuda_fail(e, "debug derivative");
+    return OIM_OK;
+}
+
+int oim_backward(oim_run_t r, double* dK, double* dKs, double* dKn, double* loss) {
+    g_last_error.clear();
+    if (!r) return fail(OIM_EINVAL, "NULL run");
+    if (!r->ran) return fail(OIM_ESTATE, "run has not executed");
+    if (r->form != OIM_FORM_STREAM || r->prec != OIM_PREC_FP32 || r->ckpt_every <= 0 || !r->d_ckpt)
+        return fail(OIM_ESTATE, "oim_backward needs a run with checkpoint_every > 0 (FP32 stream form)");
+    int rc = set_device_of(r->p);
+    if (rc != OIM_OK) return rc;
+    cudaStream_t s = r->stream;
+    const int G = r->p->G;
+    const int64_t T = r->steps, C = r->ckpt_every;
+    const size_t state = (size_t)r->p->nodes * r->R_pad;
+    const int64_t seg_len = std::min<int64_t>(C, std::max<int64_t>(T, 1));
+    float *seg = nullptr, *lam[2] = {nullptr, nullptr};
+    float2* cs[2] = {nullptr, nullptr};
+    float4* Y = nullptr;
+    double *gK = nullptr, *gS = nullptr, *gN = nullptr, *gL = nullptr;
+    cudaError_t e = cudaSuccess;
+    auto cleanup = [&]() {
+        cudaFree(seg); cudaFree(lam[0]); cudaFree(lam[1]); cudaFree(cs[0]); cudaFree(cs[1]);
+        cudaFree(Y); cudaFree(gK); cudaFree(gS); cudaFree(gN); cudaFree(gL);
+    };
+#define OIM_BW(call, what)                     \
+    do {                                       \
+        e = (call);                            \
+        if (e != cudaSuccess) {                \
+            cleanup();                         \
+            return cuda_fail(e, what);         \
+        }                                      \
+    } while (0)
+    OIM_BW(cudaMalloc(&seg, (size_t)seg_len * state * sizeof(float)), "cudaMalloc(segment)");
+    OIM_BW(cudaMalloc(&lam[0], state * sizeof(float)), "cudaMalloc(lambda)");
+    OIM_BW(cudaMalloc(&lam[1], state * sizeof(float)), "cudaMalloc(lambda)");
+    OIM_BW(cudaMalloc(&cs[0], state * sizeof(float2)), "cudaMalloc(cs)");
+    OIM_BW(cudaMalloc(&cs[1], state * sizeof(float2)), "cudaMalloc(cs)");
+    OIM_BW(cudaMalloc(&Y, state * sizeof(float4)), "cudaMalloc(Y)");
+    const size_t gbytes = (size_t)G * std::max<int64_t>(T, 1) * sizeof(double);
+    OIM_BW(cudaMalloc(&gK, gbytes), "cudaMalloc(grad)");
+    OIM_BW(cudaMalloc(&gS, gbytes), "cudaMalloc(grad)");
+    OIM_BW(cudaMalloc(&gN, gbytes), "cudaMalloc(grad)");
+    OIM_BW(cudaMalloc(&gL, (size_t)G * sizeof(double)), "cudaMalloc(loss)");
+    OIM_BW(cudaMemsetAsync(gK, 0, gbytes, s), "clear grad");
+    OIM_BW(cudaMemsetAsync(gS, 0, gbytes, s), "clear grad");
+    OIM_BW(cudaMemsetAsync(gN, 0, gbytes, s), "clear grad");
+    OIM_BW(cudaMemsetAsync(gL, 0, (size_t)G * sizeof(double), s), "clear loss");
+    OIM_BW(cudaMemsetAsync(lam[0], 0, state * sizeof(float), s), "clear lambda");
+    // terminal adjoint and loss from the final phases
+    OIM_BW(launch_adj_prep(*r, r->d_theta[r->final_buf], lam[0], Y, s), "adjoint prep");
+    OIM_BW(launch_adj_terminal(*r, Y, lam[0], gL, s), "adjoint terminal");
+    int cur = 0;
+    const int64_t n_seg = (T + C - 1) / C;
+    for (int64_t sg = n_seg - 1; sg >= 0; --sg) {
+        const int64_t t0 = sg * C, t1 = std::min<int64_t>(t0 + C, T);
+        // recompute theta_t0 .. theta_{t1-1} from the checkpoint with the forward kernel
+        OIM_BW(cudaMemcpyAsync(seg, r->d_ckpt + (size_t)sg * state, state * sizeof(float),
+                               cudaMemcpyDeviceToDevice, s), "load checkpoint");
+        OIM_BW(launch_cs_from_theta(*r, seg, cs[0], s), "recompute cache");
+        for (int64_t m = 0; m + 1 < t1 - t0; ++m)
+            OIM_BW(launch_step_stream_buffers(*r, t0 + m, seg + (size_t)m * state, cs[m & 1],
+                                              seg + (size_t)(m + 1) * state, cs[(m + 1) & 1], s),
+                   "recompute step");
+        for (int64_t t = t1 - 1; t >= t0; --t) {
+            const float* th = seg + (size_t)(t - t0) * state;
+            OIM_BW(launch_adj_prep(*r, th, lam[cur], Y, s), "adjoint prep");
+            OIM_BW(launch_adj_step(*r, t, th, Y, lam[cur], lam[cur ^ 1], gK, gS, gN, s), "adjoint step");
+            cur ^= 1;
+        }
+    }
+    OIM_BW(cudaStreamSynchronize(s), "backward");
+    const size_t gcount = (size_t)G * T;
+    if (dK && T > 0) OIM_BW(cudaMemcpy(dK, gK, gcount * sizeof(double), cudaMemcpyDefault), "write dK");
+    if (dKs && T > 0) OIM_BW(cudaMemcpy(dKs, gS, gcount * sizeof(double), cudaMemcpyDefault), "write dKs");
+    if (dKn && T > 0) OIM_BW(cudaMemcpy(dKn, gN, gcount * sizeof(double), cudaMemcpyDefault), "write dKn");
+    if (loss) {
+        std::vector<double> l((size_t)G);
+        OIM_BW(cudaMemcpy(l.data(), gL, G * sizeof(double), cudaMemcpyDeviceToHost), "read loss");
+        for (auto& x : l) x /= (double)r->R;
+        OIM_BW(cudaMemcpy(loss, l.data(), G * sizeof(double), cudaMemcpyDefault), "write loss");
+    }
+#undef OIM_BW
+    cleanup();
     return OIM_OK;
 }
 

@@ -123,6 +123,10 @@ struct oim_run_s {
     uint64_t graph_seed = 0;
     float graph_dt = 0.f;
     int32_t* d_t0 = nullptr;                  // device step counter (graph replays)
+    // adjoint support: phases every ckpt_every steps ([n_ckpt][nodes][R_pad])
+    int32_t ckpt_every = 0;
+    int64_t ckpt_cap = 0;
+    float* d_ckpt = nullptr;
     bool ran = false;
 };
 

@@ -174,6 +174,39 @@ cudaError_t launch_init_stream(const oim_run_s& r, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// (cos, sin) of every phase, for restarting the stream form from stored phases.
+__global__ void cs_from_theta_kernel(int64_t count, const float* __restrict__ theta,
+                                     float2* __restrict__ cs) {
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= count) return;
+    float s, c;
+    sincospif(2.0f * theta[gid], &s, &c);
+    cs[gid] = make_float2(c, s);
+}
+
+cudaError_t launch_cs_from_theta(const oim_run_s& r, const float* theta, float2* cs, cudaStream_t s) {
+    const int64_t count = r.p->nodes * r.R_pad;
+    cs_from_theta_kernel<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(count, theta, cs);
+    return cudaGetLastError();
+}
+
+// One step t of the stream form between explicit buffers.
+cudaError_t launch_step_stream_buffers(const oim_run_s& r, int64_t t, const float* th_in,
+                                       const float2* cs_in, float* th_out, float2* cs_out,
+                                       cudaStream_t s) {
+    const StepParams P = params_of(r);
+    const int64_t total = r.p->nodes * (r.R_pad / 4);
+    const int threads = 256;
+    const int64_t blocks = (total + threads - 1) / threads;
+    if (r.p->unit_weights)
+        step_stream_kernel<true><<<(unsigned)blocks, threads, 0, s>>>(
+            r.p->csr(), P, th_in, cs_in, th_out, cs_out, t, nullptr, 0);
+    else
+        step_stream_kernel<false><<<(unsigned)blocks, threads, 0, s>>>(
+            r.p->csr(), P, th_in, cs_in, th_out, cs_out, t, nullptr, 0);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_step_stream(const oim_run_s& r, int64_t t, const int32_t* d_t0, cudaStream_t s) {
     // with d_t0 the step is *d_t0 + t (graph replay); otherwise t itself.
     const StepParams P = params_of(r);
