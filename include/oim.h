@@ -223,6 +223,18 @@ int oim_backward(oim_run_t r, double* dK, double* dKs, double* dKn, double* loss
 void oim_destroy_run(oim_run_t r);
 
 /*
+ * oim_debug_tc_gemm -- self-test of the tensor-core path behind the dense coupling
+ * form (the matrix product W * [cos | sin] of Eq. 5's coupling sum): computes
+ * D[m][n] = sum_k A[m][k] B[n][k] with tcgen05.mma, TMA-loaded 128-byte-swizzled
+ * K-major BF16 operands and an FP32 TMEM accumulator.
+ *   A  device bf16[M][K], B device bf16[N][K] (16-byte aligned), D device float[M][N];
+ *   M and N multiples of 128, K a multiple of 64.  Synchronous.
+ * Errors: OIM_EINVAL, OIM_EUNSUPPORTED (no tensor-map support in the driver),
+ * OIM_ETIMEOUT (a pipeline wait gave up), OIM_ECUDA.
+ */
+int oim_debug_tc_gemm(const void* A, const void* B, float* D, int32_t M, int32_t N, int32_t K);
+
+/*
  * oim_score_phases_noalloc -- the cut / conflict scores of oim_readout, for
  * phases the caller supplies, computed without allocating any device memory.
  * (The paper has no counterpart: this is an interface for embedding.)

@@ -86,6 +86,7 @@ SIGNATURES = {
     "oim_get_phases": (ctypes.c_int, [_vp, _vp]),
     "oim_debug_derivative": (ctypes.c_int, [_vp, _vp, _i32, _f32, _f32, _vp]),
     "oim_backward": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "oim_debug_tc_gemm": (ctypes.c_int, [_vp, _vp, _vp, _i32, _i32, _i32]),
     "oim_destroy_run": (None, [_vp]),
     "oim_score_phases_noalloc": (ctypes.c_int, [_vp, _vp, _i32, _i32, _vp, _vp]),
 }
@@ -232,6 +233,11 @@ def oim_debug_derivative(p, theta, replicas, K, Ks, f_out):
 def oim_backward(r, dK=None, dKs=None, dKn=None, loss=None):
     _check(load().oim_backward(r, ptr(dK, np.float64), ptr(dKs, np.float64), ptr(dKn, np.float64),
                                ptr(loss, np.float64)))
+
+
+def oim_debug_tc_gemm(A, B, D, M, N, K):
+    """D = A B^T on the tensor cores (A bf16 [M,K], B bf16 [N,K], D float32 [M,N]; device)."""
+    _check(load().oim_debug_tc_gemm(A.data_ptr(), B.data_ptr(), ptr(D, np.float32), int(M), int(N), int(K)))
 
 
 def oim_destroy_run(r):
