@@ -1,0 +1,329 @@
+// gemm_step.cu -- the dense coupling form: one Euler-Maruyama step per launch with
+// the coupling sums on the tensor cores.
+//
+// With X^T = [cos 2 pi theta ; sin 2 pi theta] (rows 2r and 2r + 1 for replica r,
+// columns = nodes, BF16) and W the dense coupling matrix (BF16; +-1 weights are
+// exact), one step needs D^T = X^T W, i.e. D^T[2r][i] = A_{i,r} = sum_j w_ij c_j,r and
+// D^T[2r+1][i] = B_{i,r}; W is symmetric, so W itself is the K-major B operand.
+// A CTA computes a 128 x BN tile of D^T with tcgen05.mma (FP32 accumulator in
+// TMEM) from TMA-loaded 128-byte-swizzled tiles, then its eight warps finish the
+// step for the tile's (node, replica) pairs: coupling s A - c B, injection,
+// Philox noise, Euler update and wrap (Eq. 5, Algorithm 1), and write the new
+// FP32 phases ([R_pad][n_pad], replica-major) and the next step's BF16 X^T.
+// The trigonometry and Box-Muller use the hardware approximations (the BF16
+// operands round at 2^-9, far above their ~1e-6 error).
+#include <cuda_bf16.h>
+
+#include <string>
+
+#include "oim_device.cuh"
+#include "oim_internal.h"
+#include "tc_common.cuh"
+
+namespace oim {
+
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+int make_map_bf16(CUtensorMap* m, const void* base, uint64_t cols, uint64_t rows, uint64_t pitch,
+                  uint32_t box_rows);
+
+namespace {
+
+constexpr int kBM = 128, kBK = 64, kABytes = kBM * 128;
+
+struct GemmArgs {
+    float* theta;               // [R_pad][n_pad], updated in place
+    __nv_bfloat16* x_out;       // [2 R_pad][n_pad], next step's X^T
+    const float* K;             // schedules of this graph, indexed by t
+    const float* Ks;
+    const float* Kn;
+    int64_t t;
+    float dt, sqrt_dt;
+    uint64_t seed;
+    int32_t graph, q, n, n_pad;
+    int32_t* err;
+};
+
+__device__ __forceinline__ float noise_of(uint64_t seed, uint32_t g, uint32_t i, uint32_t t, uint32_t r) {
+    const uint4 x = draw_block(seed, g, kStreamNoise, i, t, r >> 2);
+    const float2 z = (r & 2) ? box_muller_fast(x.z, x.w) : box_muller_fast(x.x, x.y);
+    return (r & 1) ? z.y : z.x;
+}
+
+template <int BN, int S>
+__global__ void __launch_bounds__(256, 1)
+    gemm_step_kernel(const __grid_constant__ CUtensorMap mX, const __grid_constant__ CUtensorMap mW,
+                     GemmArgs a) {
+    using namespace tc;
+    constexpr int kBBytes = BN * 128;
+    constexpr uint32_t kCols = BN <= 64 ? 64 : (BN <= 128 ? 128 : 256);
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* base =
+        reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    unsigned char* sA = base;
+    unsigned char* sB = base + S * kABytes;
+    __shared__ __align__(8) uint64_t full[S], empty[S], done;
+    __shared__ uint32_t tmem_slot;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * BN;
+    const int KB = a.n_pad / kBK;
+    if (threadIdx.x == 0) {
+        prefetch_map(&mX);
+        prefetch_map(&mW);
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(&done, 1);
+        fence_barrier_init();
+    }
+    if (warp == 0) tmem_alloc(&tmem_slot, kCols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    if (threadIdx.x == 0) {
+        const uint32_t idesc = idesc_bf16_f32(kBM, BN);
+        bool ok = true;
+        for (int kb = 0; kb < KB && kb < S; ++kb) {
+            mbar_arrive_expect_tx(&full[kb], kABytes + kBBytes);
+            tma_load_2d(sA + kb * kABytes, &mX, kb * kBK, m0, &full[kb]);
+            tma_load_2d(sB + kb * kBBytes, &mW, kb * kBK, n0, &full[kb]);
+        }
+        for (int kb = 0; kb < KB && ok; ++kb) {
+            const int s = kb % S;
+            if (!mbar_wait(&full[s], (kb / S) & 1, a.err, kErrFullWait)) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t a0 = smem_u32(sA + s * kABytes), b0 = smem_u32(sB + s * kBBytes);
+#pragma unroll
+            for (int k = 0; k < kBK / 16; ++k)
+                umma_bf16(tmem, sdesc_kmajor_sw128(a0 + 32 * k), sdesc_kmajor_sw128(b0 + 32 * k), idesc,
+                          (kb | k) != 0);
+            umma_commit(&empty[s]);
+            if (kb + S < KB) {
+                if (!mbar_wait(&empty[s], (kb / S) & 1, a.err, kErrEmptyWait)) {
+                    ok = false;
+                    break;
+                }
+                mbar_arrive_expect_tx(&full[s], kABytes + kBBytes);
+                tma_load_2d(sA + s * kABytes, &mX, (kb + S) * kBK, m0, &full[s]);
+                tma_load_2d(sB + s * kBBytes, &mW, (kb + S) * kBK, n0, &full[s]);
+            }
+        }
+        umma_commit(&done);
+    }
+    __syncwarp();
+    const bool have = mbar_wait(&done, 0, a.err, kErrDoneWait);
+    tc_fence_after();
+
+    if (have) {
+        // warp -> TMEM lane quadrant (rows) and half of the tile's columns
+        const int quad = warp & 3, half = warp >> 2;
+        const int row = m0 + quad * 32 + lane;            // row of X^T: 2 r + comp
+        const int r = row >> 1, comp = row & 1;
+        const float K = __ldg(a.K + a.t), Ks = __ldg(a.Ks + a.t), Kn = __ldg(a.Kn + a.t);
+        const float dtK = a.dt * K, dtKs = a.dt * Ks, kick = Kn * a.sqrt_dt;
+        float* th_row = a.theta + (size_t)r * a.n_pad;
+        __nv_bfloat16* xc = a.x_out + (size_t)(2 * r) * a.n_pad;        // cos row of replica r
+        __nv_bfloat16* xs = xc + a.n_pad;                                  // sin row
+        const unsigned full_mask = 0xffffffffu;
+#pragma unroll 1
+        for (int c0 = half * (BN / 2); c0 < (half + 1) * (BN / 2); c0 += 16) {
+            uint32_t v[16];
+            tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0, v);
+            // lane pair (cos row, sin row) of replica r: the cos lane finishes nodes 0..7
+            // of the chunk, the sin lane nodes 8..15; each needs the other's sums
+            float A[8], B[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const float send = __uint_as_float(comp ? v[j] : v[j + 8]);
+                const float recv = __shfl_xor_sync(full_mask, send, 1);
+                A[j] = comp ? recv : __uint_as_float(v[j]);
+                B[j] = comp ? __uint_as_float(v[j + 8]) : recv;
+            }
+            const int i0 = n0 + c0 + 8 * comp;                 // first node of this lane's eight
+            float th[8];
+            const float4 t0 = *reinterpret_cast<const float4*>(th_row + i0);
+            const float4 t1 = *reinterpret_cast<const float4*>(th_row + i0 + 4);
+            th[0] = t0.x; th[1] = t0.y; th[2] = t0.z; th[3] = t0.w;
+            th[4] = t1.x; th[5] = t1.y; th[6] = t1.z; th[7] = t1.w;
+            __align__(16) __nv_bfloat16 oc[8], os[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int i = i0 + j;
+                if (i < a.n) {
+                    const float2 cs = cos_sin_2pi_fast(th[j]);
+                    const float d = cs.y * A[j] - cs.x * B[j];
+                    const float z = noise_of(a.seed, (uint32_t)a.graph, (uint32_t)i, (uint32_t)a.t, (uint32_t)r);
+                    const float tn = wrap01(th[j] + (dtK * d - dtKs * sin_q(a.q, cs.x, cs.y)) + kick * z);
+                    const float2 ncs = cos_sin_2pi_fast(tn);
+                    th[j] = tn;
+                    oc[j] = __float2bfloat16_rn(ncs.x);
+                    os[j] = __float2bfloat16_rn(ncs.y);
+                } else {
+                    th[j] = 0.0f;
+                    oc[j] = __float2bfloat16_rn(0.0f);
+                    os[j] = __float2bfloat16_rn(0.0f);
+                }
+            }
+            *reinterpret_cast<float4*>(th_row + i0) = make_float4(th[0], th[1], th[2], th[3]);
+            *reinterpret_cast<float4*>(th_row + i0 + 4) = make_float4(th[4], th[5], th[6], th[7]);
+            *reinterpret_cast<uint4*>(xc + i0) = *reinterpret_cast<const uint4*>(oc);
+            *reinterpret_cast<uint4*>(xs + i0) = *reinterpret_cast<const uint4*>(os);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, kCols);
+}
+
+// ----------------------------------------------------------------------------- set-up
+__global__ void gemm_init_kernel(int n, int n_pad, int R_pad, uint64_t seed, int graph, float* theta,
+                                 __nv_bfloat16* x) {
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= (int64_t)R_pad * n_pad) return;
+    const int r = (int)(gid / n_pad), i = (int)(gid - (int64_t)r * n_pad);
+    float th = 0.0f, c = 0.0f, s = 0.0f;
+    if (i < n) {
+        const uint4 w = draw_block(seed, (uint32_t)graph, kStreamInit, (uint32_t)i, 0, (uint32_t)(r >> 2));
+        const uint32_t words[4] = {w.x, w.y, w.z, w.w};
+        th = u01(words[r & 3]);
+        const float2 cs = cos_sin_2pi_fast(th);
+        c = cs.x;
+        s = cs.y;
+    }
+    theta[gid] = th;
+    x[(size_t)(2 * r) * n_pad + i] = __float2bfloat16_rn(c);
+    x[(size_t)(2 * r + 1) * n_pad + i] = __float2bfloat16_rn(s);
+}
+
+// dense W[i][j] = w_ij (zero elsewhere, including the padding)
+__global__ void gemm_scatter_kernel(CSRDev csr, int g, int n_pad, __nv_bfloat16* W) {
+    const GraphDev gd = csr.graphs[g];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= gd.n) return;
+    const int node = gd.node_off + i;
+    for (int e = csr.rowp[node]; e < csr.rowp[node + 1]; ++e) {
+        const uint32_t cw = csr.col[e];
+        const int j = (int)(csr.w ? cw : (cw & ~kSignBit)) - gd.node_off;
+        const float w = csr.w ? csr.w[e] : ((cw & kSignBit) ? -1.0f : 1.0f);
+        W[(size_t)i * n_pad + j] = __float2bfloat16_rn(w);
+    }
+}
+
+// theta [R_pad][n_pad] -> the common [node][R_pad] layout (for readout)
+__global__ void gemm_to_common_kernel(int n, int n_pad, int R_pad, int node_off, const float* theta,
+                                      float* out) {
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= (int64_t)n * R_pad) return;
+    const int i = (int)(gid / R_pad), r = (int)(gid - (int64_t)i * R_pad);
+    out[(size_t)(node_off + i) * R_pad + r] = theta[(size_t)r * n_pad + i];
+}
+
+}  // namespace
+
+int gemm_bn_for(int n) { return n >= 1024 ? 256 : 128; }
+int gemm_n_pad(int n) {
+    const int bn = gemm_bn_for(n);
+    return ((n + bn - 1) / bn) * bn;
+}
+
+// Device state of the dense form, one graph (kept in oim_run_s::gemm).
+int gemm_setup(oim_run_s& r) {
+    const GraphDev& gd = r.p->graphs[0];
+    GemmState& st = r.gemm;
+    st.n = gd.n;
+    st.bn = gemm_bn_for(gd.n);
+    st.n_pad = gemm_n_pad(gd.n);
+    const size_t nth = (size_t)r.R_pad * st.n_pad;
+    cudaError_t e = cudaMalloc(&st.theta, nth * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&st.x[0], 2 * nth * sizeof(__nv_bfloat16));
+    if (e == cudaSuccess) e = cudaMalloc(&st.x[1], 2 * nth * sizeof(__nv_bfloat16));
+    if (e == cudaSuccess) e = cudaMalloc(&st.w, (size_t)st.n_pad * st.n_pad * sizeof(__nv_bfloat16));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(dense form)");
+    e = cudaMemset(st.w, 0, (size_t)st.n_pad * st.n_pad * sizeof(__nv_bfloat16));
+    if (e == cudaSuccess) e = cudaMemset(st.x[1], 0, 2 * nth * sizeof(__nv_bfloat16));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemset(dense form)");
+    gemm_scatter_kernel<<<(gd.n + 255) / 256, 256>>>(r.p->csr(), 0, st.n_pad,
+                                                     reinterpret_cast<__nv_bfloat16*>(st.w));
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "dense coupling matrix");
+    int rc = make_map_bf16(&st.map_w, st.w, st.n_pad, st.n_pad, (uint64_t)st.n_pad * 2, st.bn);
+    for (int b = 0; b < 2 && rc == OIM_OK; ++b)
+        rc = make_map_bf16(&st.map_x[b], st.x[b], st.n_pad, 2 * (uint64_t)r.R_pad, (uint64_t)st.n_pad * 2, 128);
+    if (rc != OIM_OK) return rc;
+    // opt in to the large shared-memory footprint once, outside any stream capture
+    constexpr int S = 4;
+    e = cudaFuncSetAttribute(gemm_step_kernel<256, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)((size_t)S * (kABytes + 256 * 128) + 1024));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(gemm_step_kernel<128, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)((size_t)S * (kABytes + 128 * 128) + 1024));
+    if (e != cudaSuccess) return cuda_fail(e, "dense form shared memory");
+    return OIM_OK;
+}
+
+void gemm_free(oim_run_s& r) {
+    GemmState& st = r.gemm;
+    cudaFree(st.theta);
+    cudaFree(st.x[0]);
+    cudaFree(st.x[1]);
+    cudaFree(st.w);
+    st = GemmState{};
+}
+
+StepParams make_params(const oim_run_s& r);
+
+cudaError_t launch_gemm_init(const oim_run_s& r, cudaStream_t s) {
+    const GemmState& st = r.gemm;
+    const int64_t total = (int64_t)r.R_pad * st.n_pad;
+    gemm_init_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
+        st.n, st.n_pad, r.R_pad, r.seed, 0, st.theta, reinterpret_cast<__nv_bfloat16*>(st.x[0]));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_step(const oim_run_s& r, int64_t t, cudaStream_t s) {
+    const GemmState& st = r.gemm;
+    const StepParams P = make_params(r);
+    GemmArgs a;
+    a.theta = st.theta;
+    a.x_out = reinterpret_cast<__nv_bfloat16*>(st.x[(t + 1) & 1]);
+    a.K = P.K;
+    a.Ks = P.Ks;
+    a.Kn = P.Kn;
+    a.t = t;
+    a.dt = P.dt;
+    a.sqrt_dt = P.sqrt_dt;
+    a.seed = P.seed;
+    a.graph = 0;
+    a.q = P.q;
+    a.n = st.n;
+    a.n_pad = st.n_pad;
+    a.err = r.d_err;
+    constexpr int S = 4;
+    dim3 grid(st.n_pad / st.bn, (2 * r.R_pad) / kBM);
+    if (st.bn == 256) {
+        const size_t smem = (size_t)S * (kABytes + 256 * 128) + 1024;
+        gemm_step_kernel<256, S><<<grid, 256, smem, s>>>(st.map_x[t & 1], st.map_w, a);
+    } else {
+        const size_t smem = (size_t)S * (kABytes + 128 * 128) + 1024;
+        gemm_step_kernel<128, S><<<grid, 256, smem, s>>>(st.map_x[t & 1], st.map_w, a);
+    }
+    return cudaGetLastError();
+}
+
+// the dense form's phases into d_theta[buf] in the common layout
+cudaError_t launch_gemm_to_common(const oim_run_s& r, float* out, cudaStream_t s) {
+    const GemmState& st = r.gemm;
+    const int64_t total = (int64_t)st.n * r.R_pad;
+    gemm_to_common_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(st.n, st.n_pad, r.R_pad, 0,
+                                                                         st.theta, out);
+    return cudaGetLastError();
+}
+
+}  // namespace oim

@@ -38,6 +38,11 @@ cudaError_t launch_cs_from_theta(const oim_run_s& r, const float* theta, float2*
 cudaError_t launch_step_stream_buffers(const oim_run_s& r, int64_t t, const float* th_in,
                                        const float2* cs_in, float* th_out, float2* cs_out,
                                        cudaStream_t s);
+int gemm_setup(oim_run_s& r);
+void gemm_free(oim_run_s& r);
+cudaError_t launch_gemm_init(const oim_run_s& r, cudaStream_t s);
+cudaError_t launch_gemm_step(const oim_run_s& r, int64_t t, cudaStream_t s);
+cudaError_t launch_gemm_to_common(const oim_run_s& r, float* out, cudaStream_t s);
 cudaError_t launch_adj_prep(const oim_run_s& r, const float* theta, const float* lam, float4* Y,
                             cudaStream_t s);
 cudaError_t launch_adj_terminal(const oim_run_s& r, const float4* Y, float* lam, double* loss,
@@ -172,6 +177,7 @@ void free_run_buffers(oim_run_s* r) {
     dev_free(r->d_t0);
     dev_free(r->d_items);
     dev_free(r->d_ckpt);
+    gemm_free(*r);
     if (r->chunk_exec) cudaGraphExecDestroy(r->chunk_exec);
     r->chunk_exec = nullptr;
 }
@@ -213,7 +219,17 @@ int choose_form(oim_run_s* r) {
     int prec = r->opts.precision;
     if (form < OIM_FORM_AUTO || form > OIM_FORM_GEMM) return fail(OIM_EINVAL, "unknown form");
     if (prec < OIM_PREC_AUTO || prec > OIM_PREC_FP16) return fail(OIM_EINVAL, "unknown precision");
-    if (form == OIM_FORM_GEMM) return fail(OIM_EUNSUPPORTED, "the tensor-core form is not built");
+    if (form == OIM_FORM_GEMM) {
+        if (r->p->G != 1) return fail(OIM_EUNSUPPORTED, "the dense form takes one graph per run");
+        if (prec != OIM_PREC_AUTO && prec != OIM_PREC_BF16)
+            return fail(OIM_EUNSUPPORTED, "the dense form multiplies BF16 operands");
+        if (r->opts.checkpoint_every > 0)
+            return fail(OIM_EUNSUPPORTED, "checkpoints (for oim_backward) need the FP32 stream form");
+        r->form = OIM_FORM_GEMM;
+        r->prec = OIM_PREC_BF16;
+        r->R_pad = (r->R + 63) & ~63;    // X^T tiles hold 64 replicas (128 rows)
+        return OIM_OK;
+    }
     if (r->opts.checkpoint_every < 0) return fail(OIM_EINVAL, "checkpoint_every must be >= 0");
     if (r->opts.checkpoint_every > 0) {
         // the adjoint recomputes segments with the stream kernels: the forward uses them too
@@ -263,6 +279,10 @@ int allocate_run(oim_run_s* r) {
         OIM_CUDA(cudaMalloc(&r->d_cs[0], state * sizeof(float2)), "cudaMalloc(cs)");
         OIM_CUDA(cudaMalloc(&r->d_cs[1], state * sizeof(float2)), "cudaMalloc(cs)");
     }
+    if (r->form == OIM_FORM_GEMM) {
+        int rc = gemm_setup(*r);
+        if (rc != OIM_OK) return rc;
+    }
     if (r->form == OIM_FORM_RESIDENT) {
         const auto& items = r->plan.items;
         OIM_CUDA(dev_alloc(&r->d_items, items.size()), "cudaMalloc(items)");
@@ -279,7 +299,19 @@ int allocate_run(oim_run_s* r) {
 // CUDA graph (kernel arguments baked in) and replayed on later identical runs.
 int enqueue_stream_form(oim_run_s* r) {
     const size_t state_bytes = (size_t)r->p->nodes * r->R_pad * sizeof(float);
-    auto body = [&](cudaStream_t s) -> cudaError_t {
+    auto body_dense = [&](cudaStream_t s) -> cudaError_t {
+        cudaError_t e = launch_gemm_init(*r, s);
+        for (int64_t t = 0; t < r->steps && e == cudaSuccess; ++t) {
+            e = launch_gemm_step(*r, t, s);
+            if (e == cudaSuccess && r->readout_every > 0 && (t + 1) % r->readout_every == 0) {
+                e = launch_gemm_to_common(*r, r->d_theta[0], s);
+                if (e == cudaSuccess) e = launch_score(*r, r->d_theta[0], (t + 1) / r->readout_every - 1, s);
+            }
+        }
+        if (e == cudaSuccess) e = launch_gemm_to_common(*r, r->d_theta[0], s);
+        return e;
+    };
+    auto body_csr = [&](cudaStream_t s) -> cudaError_t {
         cudaError_t e = launch_init_stream(*r, s);
         if (e == cudaSuccess && r->ckpt_every > 0)
             e = cudaMemcpyAsync(r->d_ckpt, r->d_theta[0], state_bytes, cudaMemcpyDeviceToDevice, s);
@@ -292,6 +324,9 @@ int enqueue_stream_form(oim_run_s* r) {
                                     r->d_theta[(t + 1) & 1], state_bytes, cudaMemcpyDeviceToDevice, s);
         }
         return e;
+    };
+    auto body = [&](cudaStream_t s) -> cudaError_t {
+        return r->form == OIM_FORM_GEMM ? body_dense(s) : body_csr(s);
     };
     if (!r->opts.use_graph) {
         cudaError_t e = body(r->stream);
@@ -358,7 +393,7 @@ int execute(oim_run_s* r, const float* K, const float* Ks, const float* Kn) {
     } else {
         int rc = enqueue_stream_form(r);
         if (rc != OIM_OK) return rc;
-        r->final_buf = (int)(r->steps & 1);
+        r->final_buf = r->form == OIM_FORM_GEMM ? 0 : (int)(r->steps & 1);
     }
     r->ran = true;
     return OIM_OK;

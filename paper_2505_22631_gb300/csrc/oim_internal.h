@@ -1,6 +1,7 @@
 // oim_internal.h -- host-side structures shared by the translation units of liboim.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -45,6 +46,16 @@ struct ResidentPlan {
     size_t smem = 0;
     std::vector<int> k_of_graph;   // replicas per block, per graph
     std::vector<int4> items;       // per block: (graph, first replica, replicas, 0)
+};
+
+// Device state of the dense (tensor-core) form of one graph.
+struct GemmState {
+    int n = 0, n_pad = 0, bn = 0;
+    float* theta = nullptr;            // [R_pad][n_pad] phases, replica-major
+    void* x[2] = {nullptr, nullptr};   // [2 R_pad][n_pad] bf16 (cos; sin) rows, ping-pong
+    void* w = nullptr;                 // [n_pad][n_pad] bf16 coupling matrix
+    CUtensorMap map_x[2];
+    CUtensorMap map_w;
 };
 
 struct CSRDev {
@@ -116,6 +127,8 @@ struct oim_run_s {
     int32_t* d_err = nullptr;                 // device error word
     // resident-form launch plan
     oim::ResidentPlan plan;
+    // dense-form state
+    oim::GemmState gemm;
     int4* d_items = nullptr;                  // plan.items on the device
     // stream-form CUDA graph of a whole run, reused while its shape is unchanged
     cudaGraphExec_t chunk_exec = nullptr;

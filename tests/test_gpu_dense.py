@@ -1,0 +1,78 @@
+"""The dense (tcgen05 tensor-core) coupling form against the FP64 oracle.
+
+Tolerances: the BF16 operands give the coupling sum to within 1e-2 of the row
+norm of the FP64 (A, B) (the stated BF16 criterion); noise draws as the other
+hardware-approximation forms (<= 2e-5); spins and scores from the form's own
+phases are bit-exact.
+"""
+import numpy as np
+import pytest
+
+from gpu_common import circ, gpu_run, oracle_phases, rad_dist, require_gpu
+from workloads import csr_from_edges, erdos_renyi, linear_ramp, constant, make_workload
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    require_gpu()
+
+
+@pytest.mark.parametrize("n,p,R", [(800, 0.06, 64), (300, 0.2, 8), (1100, 0.03, 72)])
+def test_dense_coupling_within_1e2_per_row(orc, n, p, R):
+    g = erdos_renyi(n, p, n, "pm1")
+    dt, K = 1e-3, 1.0
+    run = gpu_run(g, 2, K, 0.0, 0.0, dt, 1, R, 13, form="gemm", precision="bf16")
+    assert run.info()["form"] == 3
+    th0 = orc.init_phases(g.n, R, 13)
+    D = circ(run.phases()[0].astype(np.float64) - th0) / (np.float32(dt) * K)
+    rows = np.repeat(np.arange(g.n), g.degrees())
+    A = np.zeros((R, g.n))
+    B = np.zeros((R, g.n))
+    for r in range(R):
+        np.add.at(A[r], rows, g.w * np.cos(2 * np.pi * th0[r, g.col]))
+        np.add.at(B[r], rows, g.w * np.sin(2 * np.pi * th0[r, g.col]))
+    D64 = np.stack([orc.coupling(g, th0[r]) for r in range(R)])
+    err = np.linalg.norm(D - D64, axis=0)
+    ref = np.sqrt(np.sum(A**2 + B**2, axis=0))
+    assert np.max(err / ref) <= 1e-2
+
+
+def test_dense_noise_draws(orc):
+    n, R, kick = 500, 64, 0.05
+    g = csr_from_edges(n, np.zeros(0, int), np.zeros(0, int))
+    run = gpu_run(g, 2, 0.0, 0.0, kick, 1.0, 1, R, 6, form="gemm", precision="bf16")
+    th1 = run.phases()[0].astype(np.float64)
+    th0 = orc.init_phases(n, R, 6)
+    err = np.abs(circ(th1 - th0) / kick - orc.noise_block(n, R, 6, 0))
+    assert err.max() <= 2e-5
+
+
+@pytest.mark.parametrize("R", [8, 70])
+def test_dense_readout_bitexact_and_short_run_parity(orc, R):
+    w = make_workload("er800")
+    g = w.graphs[0]
+    T = 100
+    run = gpu_run(g, 2, w.K[0][:T], w.Ks[0][:T], w.Kn[0][:T], w.dt, T, R, 5, form="gemm",
+                  precision="bf16", readout_every=25)
+    th = run.phases()[0]
+    out = run.readout()
+    spins = orc.readout_f32(2, th)
+    assert np.array_equal(out["spins"][0], spins)
+    assert np.array_equal(out["score"][0], orc.scores(g, 2, spins))
+    assert np.array_equal(out["trace"][0, -1], out["score"][0])
+    # BF16 coupling: short horizon phase agreement with the FP64 oracle, loose
+    ref = oracle_phases(orc, g, 2, w.K[0][:20], w.Ks[0][:20], w.Kn[0][:20], w.dt, 20, R, 5)
+    run20 = gpu_run(g, 2, w.K[0][:20], w.Ks[0][:20], w.Kn[0][:20], w.dt, 20, R, 5, form="gemm",
+                    precision="bf16")
+    assert np.median(rad_dist(run20.phases()[0], ref)) <= 1e-3
+
+
+def test_dense_graph_capture_matches_direct():
+    g = erdos_renyi(400, 0.1, 2, "+1")
+    T, R = 40, 64
+    args = (g, 2, constant(T, 0.3), linear_ramp(T, 0, 1), constant(T, 0.1), 0.01, T, R, 3)
+    a = gpu_run(*args, form="gemm", precision="bf16", use_graph=True).phases()[0]
+    b = gpu_run(*args, form="gemm", precision="bf16", use_graph=False).phases()[0]
+    assert np.array_equal(a, b)
