@@ -419,11 +419,20 @@ __global__ void __launch_bounds__(1024, 1) resident_quad_kernel(ResidentArgs a) 
         const float K = __ldg(P.K + sbase + t), Ks = __ldg(P.Ks + sbase + t);
         const float Kn = __ldg(P.Kn + sbase + t);
         const float dtK = P.dt * K, dtKs = P.dt * Ks, kick = Kn * sdt;
+        // nodes in order of degree, so the lanes of a warp run rows of equal length;
+        // the next node's phases are loaded while the current one is processed
+        int i_cur = i_begin < n ? (kSmemCSR ? (int)s_order[i_begin] : a.csr.order[noff + i_begin]) : 0;
+        float4 th_cur = i_begin < n ? *reinterpret_cast<const float4*>(theta + (size_t)(noff + i_cur) * R_pad)
+                                    : make_float4(0.f, 0.f, 0.f, 0.f);
         for (int slot_i = i_begin; slot_i < n; slot_i += NS) {
-            // nodes in order of degree, so the lanes of a warp run rows of equal length
-            const int i = kSmemCSR ? (int)s_order[slot_i] : a.csr.order[noff + slot_i];
+            const int i = i_cur;
+            const float4 th = th_cur;
+            const int slot_n = slot_i + NS;
+            if (slot_n < n) {
+                i_cur = kSmemCSR ? (int)s_order[slot_n] : a.csr.order[noff + slot_n];
+                th_cur = *reinterpret_cast<const float4*>(theta + (size_t)(noff + i_cur) * R_pad);
+            }
             const int node = noff + i;
-            const float4 th = *reinterpret_cast<const float4*>(theta + (size_t)node * R_pad);
             float2 own[4];
             Quad::unpack(cache[i * units + u], own);
             float2 acc[4];
@@ -480,10 +489,15 @@ __global__ void __launch_bounds__(1024, 1) resident_quad_kernel(ResidentArgs a) 
             *reinterpret_cast<float4*>(theta + (size_t)node * R_pad) = make_float4(tn[0], tn[1], tn[2], tn[3]);
         }
         __syncthreads();
-        for (int i = i_begin; i < n; i += NS) {
-            const float4 th = *reinterpret_cast<const float4*>(theta + (size_t)(noff + i) * R_pad);
-            const float2 cs[4] = {M::cs(th.x), M::cs(th.y), M::cs(th.z), M::cs(th.w)};
-            cache[i * units + u] = Quad::pack(cs);
+        {
+            float4 th_n = i_begin < n ? *reinterpret_cast<const float4*>(theta + (size_t)(noff + i_begin) * R_pad)
+                                      : make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int i = i_begin; i < n; i += NS) {
+                const float4 th = th_n;
+                if (i + NS < n) th_n = *reinterpret_cast<const float4*>(theta + (size_t)(noff + i + NS) * R_pad);
+                const float2 cs[4] = {M::cs(th.x), M::cs(th.y), M::cs(th.z), M::cs(th.w)};
+                cache[i * units + u] = Quad::pack(cs);
+            }
         }
         __syncthreads();
 
