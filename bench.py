@@ -77,6 +77,22 @@ def profiled_traffic(kernel, workload):
     return None
 
 
+def rank_seed(rank: int) -> int:
+    """Seed of a rank's replica set: ranks simulate independent replicas (weak scaling)."""
+    return 1000 * (rank + 1)
+
+
+def reduce_max(value: float, world: int, device="cpu") -> float:
+    """Max over ranks of a per-rank scalar (the step time), on the initialised process group."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -285,7 +301,7 @@ def main():
     problems = [Problem.from_graph(g, w.q) for g in w.graphs]
     prob = Problem.batch(problems) if len(problems) > 1 else problems[0]
     stream = torch.cuda.current_stream()
-    seed_base = 1000 * (rank + 1)
+    seed_base = rank_seed(rank)
     run = Run(prob, dK, dKs, dKn, w.dt, w.steps, w.replicas, seed_base, form=args.form,
               precision=args.precision, readout_every=args.readout_every, stream=stream)
     info = run.info()
@@ -315,10 +331,7 @@ def main():
     clocks = sampler.stop()
     ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     ms_step = float(np.mean(ms))
-    if world > 1:
-        t = torch.tensor([ms_step], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = reduce_max(ms_step, world, device="cuda")
     edge_updates = w.edge_updates() * world
     value = edge_updates / (ms_step / 1e3)
 

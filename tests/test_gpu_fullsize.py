@@ -1,0 +1,129 @@
+"""Full-size checks of every workload, in the launch configuration the benchmark uses.
+
+The oracle cannot follow thousands of replicas for thousands of steps, so these
+compare what it can compute one by one: sampled replicas after a short horizon
+(phases), the exact recount of every replica's score from the GPU's own spins,
+and properties that hold at any size.  The statistical best-cut criterion runs
+on the 800-node workload over ten seeds.
+"""
+import numpy as np
+import pytest
+
+from gpu_common import circ, oracle_phases, rad_dist, require_gpu
+from workloads import make_workload
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    require_gpu()
+
+
+def run_workload(w, steps=None, form="auto", precision="auto", readout_every=0, seed=1):
+    from paper_2505_22631_gb300 import Problem, Run
+    probs = [Problem.from_graph(g, w.q) for g in w.graphs]
+    prob = probs[0] if len(probs) == 1 else Problem.batch(probs)
+    T = steps or w.steps
+    K = np.stack(w.K)[:, :T].copy()
+    Ks = np.stack(w.Ks)[:, :T].copy()
+    Kn = np.stack(w.Kn)[:, :T].copy()
+    return Run(prob, K, Ks, Kn, w.dt, T, w.replicas, seed, form=form, precision=precision,
+               readout_every=readout_every)
+
+
+def test_batched_maxcut_sampled_replicas_fp32(orc):
+    # horizon: at these couplings (K = 4 per torus edge) the FP64 dynamics alone amplify an
+    # FP32-ulp perturbation of the start to 6.9e-5 rad in 10 steps, 1.8e-4 in 20, 3.3e-2 in 50
+    w = make_workload("torus_er2000")
+    T = 15
+    run = run_workload(w, steps=T, form="resident", precision="fp32", seed=3)
+    ph = run.phases()
+    for gi, g in enumerate(w.graphs):
+        for r0 in (0, 517, 1020):
+            ref = oracle_phases(orc, g, 2, w.K[gi], w.Ks[gi], w.Kn[gi], w.dt, T, 4, 3, graph=gi,
+                                replica_offset=r0, nthreads=8)
+            assert rad_dist(ph[gi][r0:r0 + 4], ref).max() <= 1e-3
+
+
+def test_batched_maxcut_full_run_scores_exact(orc):
+    # the benchmark's form (AUTO: resident, FP16 cache), full 5000 steps, every replica
+    w = make_workload("torus_er2000")
+    run = run_workload(w, readout_every=50, seed=5)
+    out = run.readout()
+    ph = run.phases()
+    for gi, g in enumerate(w.graphs):
+        spins = orc.readout_f32(2, ph[gi])
+        assert np.array_equal(out["spins"][gi], spins)
+        assert np.array_equal(out["score"][gi], orc.scores(g, 2, spins))
+        assert np.array_equal(out["trace"][gi, -1], out["score"][gi])
+        # the annealed machine ends far above random assignments
+        rnd = orc.scores(g, 2, np.random.default_rng(gi).integers(0, 2, (64, g.n)).astype(np.int8))
+        assert out["score"][gi].mean() > rnd.max() + 0.1 * g.num_edges
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+def test_planted_colouring_conflicts_exact(orc, precision):
+    w = make_workload("planted600")
+    run = run_workload(w, form="resident", precision=precision, readout_every=500, seed=7)
+    out = run.readout()
+    th = run.phases()[0]
+    spins = orc.readout_f32(3, th)
+    assert np.array_equal(out["spins"][0], spins)
+    conf = orc.scores(w.graphs[0], 3, spins)
+    assert np.array_equal(out["score"][0], conf)
+    assert conf.min() <= 0.05 * w.graphs[0].num_edges   # near-proper colourings are found
+
+
+def test_uneven_batch_runs_and_scores_exact(orc):
+    w = make_workload("uneven16", steps=400)
+    run = run_workload(w, readout_every=100, seed=9)
+    out = run.readout()
+    ph = run.phases()
+    for gi in (0, 7, 8, 15):
+        g = w.graphs[gi]
+        spins = orc.readout_f32(2, ph[gi][:16])
+        assert np.array_equal(out["spins"][gi][:16], spins)
+        assert np.array_equal(out["score"][gi][:16], orc.scores(g, 2, spins))
+
+
+def test_schedule_batch_adjoint_consistent_with_forward_energy():
+    from paper_2505_22631_gb300 import Problem, capi
+    w = make_workload("er64", steps=300)
+    probs = [Problem.from_graph(g, 2) for g in w.graphs]
+    prob = Problem.batch(probs)
+    T = w.steps
+    K, Ks, Kn = (np.stack(x).astype(np.float32) for x in (w.K, w.Ks, w.Kn))
+    o = capi.oim_default_opts()
+    o.form = capi.OIM_FORM_STREAM
+    o.precision = capi.OIM_PREC_FP32
+    o.checkpoint_every = 100
+    r = capi.oim_run(prob.handle, K, Ks, Kn, w.dt, T, w.replicas, 11, o)
+    G = len(w.graphs)
+    E = np.zeros(G * w.replicas)
+    capi.oim_readout(r, None, None, None, None, E)
+    dK, dKs, dKn, L = np.zeros((G, T)), np.zeros((G, T)), np.zeros((G, T)), np.zeros(G)
+    capi.oim_backward(r, dK, dKs, dKn, L)
+    capi.oim_destroy_run(r)
+    # the adjoint's loss is the mean final energy the readout reports
+    assert np.allclose(L, E.reshape(G, w.replicas).mean(1), rtol=1e-5, atol=1e-3)
+    assert np.all(np.isfinite(dK)) and np.all(np.isfinite(dKs)) and np.all(np.isfinite(dKn))
+
+
+def test_best_cut_statistically_matches_oracle(orc):
+    w = make_workload("er800")
+    g = w.graphs[0]
+    seeds = range(1, 11)
+    gpu, ref = [], []
+    for s in seeds:
+        run = run_workload(w, form="resident", precision="fp32", seed=s)
+        gpu.append(run.readout(spins=False)["score"][0].max())
+        th, _ = orc.run(g, 2, w.K[0].astype(np.float64), w.Ks[0].astype(np.float64),
+                        w.Kn[0].astype(np.float64), float(np.float32(w.dt)), w.steps, w.replicas,
+                        s, nthreads=16)
+        ref.append(orc.scores(g, 2, orc.readout_f64(2, th)).max())
+    gpu, ref = np.array(gpu), np.array(ref)
+    diff = gpu.mean() - ref.mean()
+    ci = 1.96 * np.sqrt(gpu.var(ddof=1) / len(gpu) + ref.var(ddof=1) / len(ref))
+    print(f"best cut: GPU {gpu.mean():.1f} oracle {ref.mean():.1f} diff {diff:.1f} (95% CI +-{ci:.1f})")
+    assert abs(diff) <= 0.005 * ref.mean()
