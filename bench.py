@@ -302,8 +302,18 @@ def main():
     prob = Problem.batch(problems) if len(problems) > 1 else problems[0]
     stream = torch.cuda.current_stream()
     seed_base = rank_seed(rank)
-    run = Run(prob, dK, dKs, dKn, w.dt, w.steps, w.replicas, seed_base, form=args.form,
-              precision=args.precision, readout_every=args.readout_every, stream=stream)
+    form, precision, rpb, threads = args.form, args.precision, 0, 0
+    tuned = None
+    if args.form == "auto":
+        # the library's autotuner times candidate forms / block shapes on short probes
+        policy = capi.OIM_PREC_FP32 if args.precision == "fp32" else capi.OIM_PREC_AUTO
+        o, us = capi.oim_autotune(prob.handle, w.replicas, policy, 200)
+        form, precision, rpb, threads = o.form, o.precision, o.replicas_per_block, o.threads_per_block
+        tuned = {"form": o.form, "precision": o.precision, "replicas_per_block": rpb,
+                 "threads_per_block": threads, "probe_us_per_step": us}
+    run = Run(prob, dK, dKs, dKn, w.dt, w.steps, w.replicas, seed_base, form=form,
+              precision=precision, readout_every=args.readout_every, stream=stream,
+              replicas_per_block=rpb, threads_per_block=threads)
     info = run.info()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
@@ -346,7 +356,8 @@ def main():
     alg_bytes = node_replica_steps * bytes_per_unit + csr_bytes
     achieved = alg_bytes / (ms_step / 1e3) / 1e9
     prec_name = {1: "fp32", 2: "bf16", 3: "fp16"}.get(info["precision"])
-    kname = (f"resident_quad_kernel<{prec_name}>" if info["form"] == 2 else "step_stream_kernel")
+    kname = {2: f"resident_quad_kernel<{prec_name}>", 1: "step_stream_kernel",
+             3: "gemm_step_kernel"}.get(info["form"], "?")
     traffic = profiled_traffic(kname, w.name)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "kernel": kname,
@@ -374,6 +385,8 @@ def main():
         o = C.oim_default_opts()
         o.form = run.opts.form
         o.precision = run.opts.precision
+        o.replicas_per_block = run.opts.replicas_per_block
+        o.threads_per_block = run.opts.threads_per_block
         o.readout_every = args.readout_every
         o.stream = int(stream.cuda_stream)
         hr = C.oim_run(hb, pin["K"], pin["Ks"], pin["Kn"], w.dt, w.steps, w.replicas, seed, o)
@@ -410,6 +423,7 @@ def main():
                    "form": {0: "auto", 1: "stream", 2: "resident", 3: "gemm"}[info["form"]],
                    "precision": {1: "fp32", 2: "bf16", 3: "fp16"}.get(info["precision"]),
                    "l2": "256 MB buffer written between timed steps (outside the events)",
+                   "autotuned": tuned,
                    "parallelism": f"replicas x{world} (weak)"},
         "roofline": roofline,
         "clocks": clocks,
@@ -421,7 +435,8 @@ def main():
     }
 
     if rank == 0 and not args.no_quality:
-        line["quality"] = quality(w, prob, problems, args, stream, ms_step)
+        line["quality"] = quality(w, prob, problems, args, stream, ms_step,
+                                  (form, precision, rpb, threads))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_oracle_sample(w)
     if rank == 0:
@@ -431,22 +446,24 @@ def main():
         torch.distributed.destroy_process_group()
 
 
-def quality(w, prob, problems, args, stream, ms_step_chosen):
+def quality(w, prob, problems, args, stream, ms_step_chosen, chosen_cfg):
     """Time to 99% of the best known cut: chosen form vs the plain FP32 CSR form."""
     import torch
     from paper_2505_22631_gb300 import Run
     re = args.readout_every
     q2 = w.q == 2
     # best known: best score of a 4x longer run of the chosen form
+    form, precision, rpb, threads = chosen_cfg
     K4, Ks4, Kn4, T4 = stretched(w, 4)
-    long = Run(prob, K4, Ks4, Kn4, w.dt, T4, w.replicas, 4242, form=args.form,
-               precision=args.precision, readout_every=re * 4, stream=stream)
+    long = Run(prob, K4, Ks4, Kn4, w.dt, T4, w.replicas, 4242, form=form, precision=precision,
+               readout_every=re * 4, stream=stream, replicas_per_block=rpb, threads_per_block=threads)
     tr = long.readout(spins=False)["trace"]
     long.close()
     best_known = tr.max(axis=(1, 2)) if q2 else tr.min(axis=(1, 2))
     K, Ks, Kn = schedules(w)
-    chosen = Run(prob, K, Ks, Kn, w.dt, w.steps, w.replicas, 777, form=args.form,
-                 precision=args.precision, readout_every=re, stream=stream).readout(spins=False)
+    chosen = Run(prob, K, Ks, Kn, w.dt, w.steps, w.replicas, 777, form=form, precision=precision,
+                 readout_every=re, stream=stream, replicas_per_block=rpb,
+                 threads_per_block=threads).readout(spins=False)
     per_step_chosen = ms_step_chosen / 1e3 / w.steps
     res = {"best_known": best_known.tolist(), "graphs": []}
     for gi, g in enumerate(w.graphs):

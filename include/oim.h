@@ -206,6 +206,24 @@ int oim_debug_derivative(oim_problem_t p, const float* theta, int32_t replicas, 
                          float* f_out);
 
 /*
+ * oim_autotune -- pick the launch configuration of p for `replicas` replicas by
+ * measurement: candidate forms (resident with a 16-bit or FP32 (cos, sin) cache,
+ * several replicas-per-block and thread counts; the FP32 stream form; the dense
+ * tensor-core form for a single graph) each run `probe_steps` steps twice on a
+ * private stream, and the fastest is returned in *best (stream set to `stream`)
+ * with its time per step in *best_us_per_step (may be NULL).  The paper leaves the
+ * per-GPU batch size to the user (Sec. III-C); this chooses it, and the form,
+ * per problem shape.
+ *   precision_policy  OIM_PREC_AUTO (16-bit caches and BF16 allowed) or
+ *                     OIM_PREC_FP32 (FP32 forms only)
+ * Decisions are cached for the process, keyed by graph sizes, nonzeros, q,
+ * replicas and policy.  Synchronous.  Errors: OIM_EINVAL, OIM_EUNSUPPORTED (no
+ * candidate ran), OIM_ECUDA.
+ */
+int oim_autotune(oim_problem_t p, int32_t replicas, int32_t precision_policy, int64_t probe_steps,
+                 void* stream, oim_run_opts* best, double* best_us_per_step);
+
+/*
  * oim_backward -- gradients of the relaxed loss L_g = (1/R) sum_r E_g(theta_T^r)
  * (Eq. 6 energy of the final phases, before thresholding) with respect to the
  * per-step schedules K_t, Ks_t, Kn_t of each graph, by the adjoint of the

@@ -86,6 +86,8 @@ SIGNATURES = {
     "oim_get_phases": (ctypes.c_int, [_vp, _vp]),
     "oim_debug_derivative": (ctypes.c_int, [_vp, _vp, _i32, _f32, _f32, _vp]),
     "oim_backward": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "oim_autotune": (ctypes.c_int, [_vp, _i32, _i32, _i64, _vp, ctypes.POINTER(oim_run_opts),
+                                    ctypes.POINTER(ctypes.c_double)]),
     "oim_debug_tc_gemm": (ctypes.c_int, [_vp, _vp, _vp, _i32, _i32, _i32]),
     "oim_destroy_run": (None, [_vp]),
     "oim_score_phases_noalloc": (ctypes.c_int, [_vp, _vp, _i32, _i32, _vp, _vp]),
@@ -238,6 +240,15 @@ def oim_backward(r, dK=None, dKs=None, dKn=None, loss=None):
 def oim_debug_tc_gemm(A, B, D, M, N, K):
     """D = A B^T on the tensor cores (A bf16 [M,K], B bf16 [N,K], D float32 [M,N]; device)."""
     _check(load().oim_debug_tc_gemm(A.data_ptr(), B.data_ptr(), ptr(D, np.float32), int(M), int(N), int(K)))
+
+
+def oim_autotune(p, replicas, precision_policy=OIM_PREC_AUTO, probe_steps=100, stream=None):
+    """Fastest launch configuration for p (by short probe runs); returns (opts, us_per_step)."""
+    o = oim_run_opts()
+    us = ctypes.c_double()
+    _check(load().oim_autotune(p, int(replicas), int(precision_policy), int(probe_steps), stream,
+                               ctypes.byref(o), ctypes.byref(us)))
+    return o, us.value
 
 
 def oim_destroy_run(r):

@@ -1,0 +1,153 @@
+// autotune.cu -- choose the launch configuration of a problem by measurement.
+//
+// Candidates (filtered by the precision policy and by what the problem allows):
+// the resident form with a 16-bit or FP32 cache, at the planner's replicas per
+// block and at half / double that, with 1024 or 512 threads; the FP32 stream
+// form; the dense tensor-core form (one graph).  Each candidate runs a short
+// probe (same graph, replicas and coupling scale as the real run, a neutral
+// schedule) twice and is timed with CUDA events on a private stream; the fastest
+// wins.  Decisions are cached for the life of the process, keyed by the graphs'
+// sizes and nonzeros, q, replicas and the policy.
+#include <cmath>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "oim_internal.h"
+
+namespace oim {
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+}  // namespace oim
+
+using namespace oim;
+
+namespace {
+
+struct TuneResult {
+    oim_run_opts opts;
+    double us_per_step;
+};
+
+std::mutex g_tune_mutex;
+std::map<std::string, TuneResult> g_tune_cache;
+
+std::string tune_key(const oim_problem_s* p, int32_t replicas, int32_t policy) {
+    std::string k = "q" + std::to_string(p->q) + "R" + std::to_string(replicas) + "P" + std::to_string(policy);
+    for (int g = 0; g < p->G; ++g) {
+        const int64_t end = (g + 1 < p->G) ? p->graphs[g + 1].edge_off : p->nnz;
+        k += ":" + std::to_string(p->graphs[g].n) + "/" + std::to_string(end - p->graphs[g].edge_off);
+    }
+    return k;
+}
+
+}  // namespace
+
+extern "C" int oim_autotune(oim_problem_t p, int32_t replicas, int32_t precision_policy,
+                            int64_t probe_steps, void* stream, oim_run_opts* best,
+                            double* best_us_per_step) {
+    if (!p || !best) return fail(OIM_EINVAL, "NULL argument");
+    if (replicas < 1) return fail(OIM_EINVAL, "replicas must be >= 1");
+    if (precision_policy != OIM_PREC_AUTO && precision_policy != OIM_PREC_FP32)
+        return fail(OIM_EINVAL, "precision policy must be OIM_PREC_AUTO or OIM_PREC_FP32");
+    if (probe_steps < 4) probe_steps = 4;
+    const std::string key = tune_key(p, replicas, precision_policy);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            *best = it->second.opts;
+            best->stream = stream;
+            if (best_us_per_step) *best_us_per_step = it->second.us_per_step;
+            return OIM_OK;
+        }
+    }
+    // neutral probe schedule: coupling ~ 1 / mean degree per graph, ramp, noise 0.1
+    const int G = p->G;
+    const int64_t T = probe_steps;
+    std::vector<float> K((size_t)G * T), Ks((size_t)G * T), Kn((size_t)G * T, 0.1f);
+    for (int g = 0; g < G; ++g) {
+        const int64_t end = (g + 1 < G) ? p->graphs[g + 1].edge_off : p->nnz;
+        const double deg = std::max(1.0, (double)(end - p->graphs[g].edge_off) / p->graphs[g].n);
+        for (int64_t t = 0; t < T; ++t) {
+            K[(size_t)g * T + t] = (float)(1.0 / deg);
+            Ks[(size_t)g * T + t] = (float)(2.0 * t / std::max<int64_t>(T - 1, 1));
+        }
+    }
+    std::vector<oim_run_opts> cands;
+    auto add = [&](int form, int prec, int rpb, int threads) {
+        oim_run_opts o;
+        oim_default_opts(&o);
+        o.form = form;
+        o.precision = prec;
+        o.replicas_per_block = rpb;
+        o.threads_per_block = threads;
+        o.use_graph = 1;
+        cands.push_back(o);
+    };
+    std::vector<int> caches;
+    if (precision_policy == OIM_PREC_AUTO) caches.push_back(OIM_PREC_FP16);
+    caches.push_back(OIM_PREC_FP32);
+    for (int prec : caches) {
+        ResidentPlan plan;
+        const int32_t R_pad = (replicas + 3) & ~3;
+        if (plan_resident(*p, R_pad, prec, 0, 0, &plan) != cudaSuccess) continue;
+        int kmax = 0;
+        for (int k : plan.k_of_graph) kmax = std::max(kmax, k);
+        const int unit = plan.unit;
+        add(OIM_FORM_RESIDENT, prec, 0, 0);
+        add(OIM_FORM_RESIDENT, prec, 0, 512);
+        for (int k : {kmax / 2, kmax * 2}) {
+            k = (k / unit) * unit;
+            if (k < unit || k == kmax) continue;
+            ResidentPlan tmp;
+            if (plan_resident(*p, R_pad, prec, k, 0, &tmp) == cudaSuccess) add(OIM_FORM_RESIDENT, prec, k, 0);
+        }
+    }
+    add(OIM_FORM_STREAM, OIM_PREC_FP32, 0, 0);
+    if (precision_policy == OIM_PREC_AUTO && G == 1) add(OIM_FORM_GEMM, OIM_PREC_BF16, 0, 0);
+
+    cudaStream_t s = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(e, "autotune stream");
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    TuneResult bestr{};
+    bestr.us_per_step = INFINITY;
+    for (auto& o : cands) {
+        o.stream = s;
+        oim_run_t r = nullptr;
+        if (oim_run(p, K.data(), Ks.data(), Kn.data(), 0.01f, T, replicas, 12345, &o, &r) != OIM_OK) continue;
+        double best_ms = INFINITY;
+        bool ok = oim_run_sync(r) == OIM_OK;
+        for (int rep = 0; rep < 2 && ok; ++rep) {
+            cudaEventRecord(e0, s);
+            ok = oim_rerun(r, K.data(), Ks.data(), Kn.data(), 0.01f, T, 777 + rep) == OIM_OK;
+            cudaEventRecord(e1, s);
+            if (ok) ok = cudaEventSynchronize(e1) == cudaSuccess;
+            float ms = 0.f;
+            if (ok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) best_ms = std::min(best_ms, (double)ms);
+        }
+        oim_destroy_run(r);
+        const double us = best_ms * 1e3 / (double)T;
+        if (ok && us < bestr.us_per_step) {
+            bestr.us_per_step = us;
+            bestr.opts = o;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamDestroy(s);
+    if (!std::isfinite(bestr.us_per_step)) return fail(OIM_EUNSUPPORTED, "no candidate configuration ran");
+    bestr.opts.stream = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        g_tune_cache[key] = bestr;
+    }
+    *best = bestr.opts;
+    best->stream = stream;
+    if (best_us_per_step) *best_us_per_step = bestr.us_per_step;
+    return OIM_OK;
+}

@@ -274,3 +274,23 @@ def test_invalid_form_requests():
     assert ei.value.code == -5
     with pytest.raises(OimError):
         gpu_run(torus(4, 4, 1), 2, 1.0, 1.0, 0.1, 0.01, 2, 4, 1, form="stream", precision="bf16")
+
+
+def test_autotune_picks_a_valid_cached_configuration(c1):
+    import time
+    from paper_2505_22631_gb300 import Problem, capi
+    from workloads import torus
+    p = Problem.batch([Problem.from_graph(c1.graphs[0], 2), Problem.from_graph(torus(20, 20, 3), 2)])
+    o, us = capi.oim_autotune(p.handle, 64, capi.OIM_PREC_AUTO, 50)
+    assert o.form in (capi.OIM_FORM_RESIDENT, capi.OIM_FORM_STREAM) and us > 0
+    t0 = time.perf_counter()
+    o2, us2 = capi.oim_autotune(p.handle, 64, capi.OIM_PREC_AUTO, 50)
+    assert time.perf_counter() - t0 < 0.05 and us2 == us and o2.form == o.form   # cached
+    o3, _ = capi.oim_autotune(p.handle, 64, capi.OIM_PREC_FP32, 50)
+    assert o3.precision == capi.OIM_PREC_FP32
+    # the chosen configuration runs
+    T = 20
+    K = np.full((2, T), 0.1, np.float32)
+    r = capi.oim_run(p.handle, K, K, K, 0.01, T, 64, 1, o)
+    capi.oim_run_sync(r)
+    capi.oim_destroy_run(r)
