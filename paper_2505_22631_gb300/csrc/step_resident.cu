@@ -71,7 +71,29 @@ struct ResidentArgs {
     double* agree;          // [G][row_stride][R_pad]
     int64_t row_stride;
     int64_t readout_every;
+    int32_t integer_weights;   // scores accumulate exactly in 32-bit integers
 };
+
+// Block-level accumulation of the agreeing weight of each replica at a readout:
+// native 32-bit shared-memory atomics (integers when every weight is an integer,
+// exact; FP32 otherwise), written out as FP64.
+struct ReadoutAcc {
+    int32_t i[64];
+    float f[64];
+};
+__device__ __forceinline__ void acc_clear(ReadoutAcc& r, int slot) {
+    r.i[slot] = 0;
+    r.f[slot] = 0.f;
+}
+__device__ __forceinline__ void acc_add(ReadoutAcc& r, int slot, float v, bool integer) {
+    if (integer)
+        atomicAdd(&r.i[slot], __float2int_rn(v));
+    else
+        atomicAdd(&r.f[slot], v);
+}
+__device__ __forceinline__ double acc_get(const ReadoutAcc& r, int slot, bool integer) {
+    return integer ? (double)r.i[slot] : (double)r.f[slot];
+}
 
 template <int U>
 __device__ __forceinline__ void load_theta(const float* p, float (&th)[U]) {
@@ -120,7 +142,7 @@ __global__ void __launch_bounds__(1024, 1) resident_kernel(ResidentArgs a) {
     using T = typename Cache::T;
     using UT = Unit<U, T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double red[64];
+    __shared__ ReadoutAcc red;
     UT* cache = reinterpret_cast<UT*>(smem_raw);   // [n][units]
 
     const int4 item = a.items[blockIdx.x];
@@ -205,7 +227,7 @@ __global__ void __launch_bounds__(1024, 1) resident_kernel(ResidentArgs a) {
         if (t + 1 == next_readout) {
             const int64_t k = next_readout / a.readout_every - 1;
             next_readout += a.readout_every;
-            if (threadIdx.x < kk) red[threadIdx.x] = 0.0;
+            if (threadIdx.x < kk) acc_clear(red, threadIdx.x);
             for (int i = i_begin; i < n; i += NS) {
                 float th[U];
                 load_theta<U>(theta + (size_t)(noff + i) * R_pad, th);
@@ -236,11 +258,11 @@ __global__ void __launch_bounds__(1024, 1) resident_kernel(ResidentArgs a) {
             if (slot < NS) {
 #pragma unroll
                 for (int v = 0; v < U; ++v)
-                    if (f[v] != 0.f) atomicAdd(&red[U * u + v], (double)f[v]);
+                    if (f[v] != 0.f) acc_add(red, U * u + v, f[v], a.integer_weights);
             }
             __syncthreads();
             if (threadIdx.x < kk)
-                a.agree[((int64_t)g * a.row_stride + k) * R_pad + r0 + threadIdx.x] = red[threadIdx.x];
+                a.agree[((int64_t)g * a.row_stride + k) * R_pad + r0 + threadIdx.x] = acc_get(red, threadIdx.x, a.integer_weights);
         }
     }
 }
@@ -367,7 +389,7 @@ __global__ void __launch_bounds__(1024, 1) resident_quad_kernel(ResidentArgs a) 
     using T = typename Quad::T;
     using M = typename Quad::Math;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double red[64];
+    __shared__ ReadoutAcc red;
 
     const int4 item = a.items[blockIdx.x];
     const int g = item.x, r0 = item.y, kk = item.z;
@@ -504,7 +526,7 @@ __global__ void __launch_bounds__(1024, 1) resident_quad_kernel(ResidentArgs a) 
         if (t + 1 == next_readout) {
             const int64_t k = next_readout / a.readout_every - 1;
             next_readout += a.readout_every;
-            if (threadIdx.x < kk) red[threadIdx.x] = 0.0;
+            if (threadIdx.x < kk) acc_clear(red, threadIdx.x);
             for (int i = i_begin; i < n; i += NS) {
                 const float4 th = *reinterpret_cast<const float4*>(theta + (size_t)(noff + i) * R_pad);
                 char4 sp;
@@ -552,16 +574,16 @@ __global__ void __launch_bounds__(1024, 1) resident_quad_kernel(ResidentArgs a) 
                 if ((threadIdx.x & 31) < units && slot < NS) {
 #pragma unroll
                     for (int v = 0; v < 4; ++v)
-                        if (f[v] != 0.f) atomicAdd(&red[4 * u + v], (double)f[v]);
+                        if (f[v] != 0.f) acc_add(red, 4 * u + v, f[v], a.integer_weights);
                 }
             } else if (slot < NS) {
 #pragma unroll
                 for (int v = 0; v < 4; ++v)
-                    if (f[v] != 0.f) atomicAdd(&red[4 * u + v], (double)f[v]);
+                    if (f[v] != 0.f) acc_add(red, 4 * u + v, f[v], a.integer_weights);
             }
             __syncthreads();
             if (threadIdx.x < kk)
-                a.agree[((int64_t)g * a.row_stride + k) * R_pad + r0 + threadIdx.x] = red[threadIdx.x];
+                a.agree[((int64_t)g * a.row_stride + k) * R_pad + r0 + threadIdx.x] = acc_get(red, threadIdx.x, a.integer_weights);
         }
     }
 }
@@ -721,6 +743,7 @@ cudaError_t launch_resident_impl(const oim_run_s& r, const int4* d_items, cudaSt
     a.agree = r.d_trace;
     a.row_stride = r.readouts_cap;
     a.readout_every = r.readout_every;
+    a.integer_weights = r.p->integer_weights ? 1 : 0;
     const ResidentPlan& pl = r.plan;
     const int blocks = (int)pl.items.size();
     const bool unit = r.p->unit_weights;
