@@ -238,6 +238,15 @@ int oim_autotune(oim_problem_t p, int32_t replicas, int32_t precision_policy, in
  */
 int oim_backward(oim_run_t r, double* dK, double* dKs, double* dKn, double* loss);
 
+/*
+ * oim_schedule_triangular -- Algorithm 1's injection-strength waveform (Sec. III-D:
+ * Ks ramped up to Ks_max and back to zero, periodically): with
+ * x = periods * t / steps, out[t] = ks_max * (1 - |2 frac(x) - 1|), t = 0..steps-1,
+ * computed in double and rounded to float.  `out` is host memory.
+ * Errors: OIM_EINVAL (NULL out, steps < 0, periods < 1, non-finite ks_max).
+ */
+int oim_schedule_triangular(float* out, int64_t steps, float ks_max, int32_t periods);
+
 void oim_destroy_run(oim_run_t r);
 
 /*

@@ -83,6 +83,7 @@ def _load():
                                _u64, _u32, _i32, _vp, _i64, _vp, _i32]),
             "orc_bruteforce_maxcut": (_dbl, [_i32, _vp, _vp, _vp, _vp]),
             "orc_bruteforce_min_conflicts": (_dbl, [_i32, _i32, _vp, _vp, _vp, _vp]),
+            "orc_triangular": (None, [_i64, _dbl, _i32, _vp]),
             "orc_adjoint": (_i32, [_i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _dbl, _i64, _i32,
                                    _u64, _u32, _i32, _vp, _vp, _vp, _vp, _vp, _i32]),
         }
@@ -264,6 +265,12 @@ def adjoint(g, q: int, K, Ks, Kn, dt: float, T: int, R: int, seed: int, graph: i
     if rc != 0:
         raise RuntimeError(f"orc_adjoint failed with {rc}")
     return float(loss[0]), dK[:T], dKs[:T], dKn[:T]
+
+
+def triangular(steps: int, ks_max: float, periods: int) -> np.ndarray:
+    out = np.zeros(max(steps, 1))
+    _load().orc_triangular(int(steps), float(ks_max), int(periods), _p(out))
+    return out[:steps]
 
 
 def accuracy_percent(cut: float, best_known: float) -> float:

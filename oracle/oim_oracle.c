@@ -459,3 +459,15 @@ int orc_adjoint(int32_t n, int32_t q, const int64_t* row_ptr, const int32_t* col
     free(gK); free(gS); free(gN); free(Er);
     return failed ? -2 : 0;
 }
+
+/* Algorithm 1's annealing waveform for the injection strength (Sec. III-D): Ks
+ * ramps linearly from 0 up to Ks_max and back to 0, `periods` times over `steps`
+ * steps.  With x = periods * t / steps, Ks_t = Ks_max * (1 - |2 frac(x) - 1|). */
+void orc_triangular(int64_t steps, double ks_max, int32_t periods, double* out)
+{
+    for (int64_t t = 0; t < steps; ++t) {
+        double x = (double)periods * (double)t / (double)steps;
+        double f = x - floor(x);
+        out[t] = ks_max * (1.0 - fabs(2.0 * f - 1.0));
+    }
+}

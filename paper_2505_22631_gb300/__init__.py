@@ -9,13 +9,14 @@ from __future__ import annotations
 import numpy as np
 
 from . import capi
-from .capi import (FORMS, PRECISIONS, OimError, oim_create_batch, oim_create_problem,
+from .capi import (FORMS, PRECISIONS, OimError, oim_schedule_triangular, oim_create_batch,
+                   oim_create_problem,
                    oim_debug_derivative, oim_default_opts, oim_destroy_problem, oim_destroy_run,
                    oim_get_phases, oim_last_error, oim_problem_info, oim_readout, oim_rerun,
                    oim_run, oim_run_info, oim_run_sync, oim_version)
 
 __all__ = [
-    "Problem", "Run", "simulate", "OimError", "FORMS", "PRECISIONS", "oim_create_problem",
+    "Problem", "Run", "simulate", "sweep", "oim_schedule_triangular", "OimError", "FORMS", "PRECISIONS", "oim_create_problem",
     "oim_create_batch", "oim_problem_info", "oim_destroy_problem", "oim_run", "oim_rerun",
     "oim_run_sync", "oim_readout", "oim_run_info", "oim_get_phases", "oim_debug_derivative",
     "oim_destroy_run", "oim_default_opts", "oim_version", "oim_last_error",
@@ -168,3 +169,27 @@ class Run:
 
 def simulate(problem: Problem, K, Ks, Kn, dt, steps, replicas, seed, **kw) -> Run:
     return Run(problem, K, Ks, Kn, dt, steps, replicas, seed, **kw)
+
+
+def sweep(problem: Problem, K_values, Ks_max_values, Kn, dt, steps, replicas, seed, periods=0, **kw):
+    """Parameter sweep (the paper's K x Ks_max study, Sec. IV-B) as one batched launch.
+
+    Every (K, Ks_max) pair becomes one graph of a batch of copies of `problem` (one
+    graph) with its own schedules: constant K, and Ks a linear ramp to Ks_max
+    (periods == 0) or the triangular waveform with `periods` periods.  Returns the
+    Run; graph g of the batch is pair g in row-major (K, Ks_max) order.
+    """
+    if problem.graphs != 1:
+        raise ValueError("sweep takes a single-graph problem")
+    pairs = [(k, s) for k in K_values for s in Ks_max_values]
+    batch = Problem.batch([problem] * len(pairs))
+    K = np.stack([np.full(steps, k, np.float32) for k, _ in pairs])
+    if periods > 0:
+        Ks = np.stack([oim_schedule_triangular(steps, s, periods) for _, s in pairs])
+    else:
+        ramp = np.arange(steps, dtype=np.float64) / max(steps - 1, 1)
+        Ks = np.stack([(s * ramp).astype(np.float32) for _, s in pairs])
+    Kn_ = np.broadcast_to(np.asarray(Kn, np.float32), (len(pairs), steps)).copy()
+    run = Run(batch, K, Ks, Kn_, dt, steps, replicas, seed, **kw)
+    run.pairs = pairs
+    return run

@@ -89,6 +89,7 @@ SIGNATURES = {
     "oim_autotune": (ctypes.c_int, [_vp, _i32, _i32, _i64, _vp, ctypes.POINTER(oim_run_opts),
                                     ctypes.POINTER(ctypes.c_double)]),
     "oim_debug_tc_gemm": (ctypes.c_int, [_vp, _vp, _vp, _i32, _i32, _i32]),
+    "oim_schedule_triangular": (ctypes.c_int, [_vp, _i64, _f32, _i32]),
     "oim_destroy_run": (None, [_vp]),
     "oim_score_phases_noalloc": (ctypes.c_int, [_vp, _vp, _i32, _i32, _vp, _vp]),
 }
@@ -249,6 +250,12 @@ def oim_autotune(p, replicas, precision_policy=OIM_PREC_AUTO, probe_steps=100, s
     _check(load().oim_autotune(p, int(replicas), int(precision_policy), int(probe_steps), stream,
                                ctypes.byref(o), ctypes.byref(us)))
     return o, us.value
+
+
+def oim_schedule_triangular(steps, ks_max, periods):
+    out = np.zeros(max(int(steps), 1), dtype=np.float32)
+    _check(load().oim_schedule_triangular(ptr(out, np.float32), int(steps), float(ks_max), int(periods)))
+    return out[:int(steps)]
 
 
 def oim_destroy_run(r):

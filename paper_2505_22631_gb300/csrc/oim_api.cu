@@ -886,6 +886,17 @@ int oim_backward(oim_run_t r, double* dK, double* dKs, double* dKn, double* loss
     return OIM_OK;
 }
 
+int oim_schedule_triangular(float* out, int64_t steps, float ks_max, int32_t periods) {
+    if (!out && steps > 0) return fail(OIM_EINVAL, "NULL output");
+    if (steps < 0 || periods < 1 || !std::isfinite(ks_max)) return fail(OIM_EINVAL, "bad waveform arguments");
+    for (int64_t t = 0; t < steps; ++t) {
+        const double x = (double)periods * (double)t / (double)steps;
+        const double frac = x - std::floor(x);
+        out[t] = (float)((double)ks_max * (1.0 - std::fabs(2.0 * frac - 1.0)));
+    }
+    return OIM_OK;
+}
+
 void oim_destroy_run(oim_run_t r) {
     if (!r) return;
     cudaStreamSynchronize(r->stream);

@@ -294,3 +294,18 @@ def test_autotune_picks_a_valid_cached_configuration(c1):
     r = capi.oim_run(p.handle, K, K, K, 0.01, T, 64, 1, o)
     capi.oim_run_sync(r)
     capi.oim_destroy_run(r)
+
+
+@pytest.mark.parametrize("periods", [0, 2])
+def test_parameter_sweep_is_one_batched_launch(orc, c1, periods):
+    from paper_2505_22631_gb300 import Problem, oim_schedule_triangular, sweep
+    g = c1.graphs[0]
+    T, R = 40, 8
+    run = sweep(Problem.from_graph(g, 2), [0.2, 0.4], [1.0, 2.0], 0.1, 0.01, T, R, 3, periods=periods,
+                form="resident", precision="fp32")
+    ph = run.phases()
+    for gi, (k, smax) in enumerate(run.pairs):
+        Ks = (oim_schedule_triangular(T, smax, periods) if periods else
+              (smax * np.arange(T) / (T - 1)).astype(np.float32))
+        ref = oracle_phases(orc, g, 2, np.full(T, k, np.float32), Ks, 0.1, 0.01, T, R, 3, graph=gi)
+        assert rad_dist(ph[gi], ref).max() <= 1e-3

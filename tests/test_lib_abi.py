@@ -129,3 +129,11 @@ def test_library_package_does_not_touch_the_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "oim_oracle" not in text and "orc_" not in text, f
+
+
+def test_triangular_schedule_matches_oracle(capi, orc):
+    got = capi.oim_schedule_triangular(1000, 2.0, 4)
+    ref = orc.triangular(1000, 2.0, 4).astype(np.float32)
+    assert np.array_equal(got, ref)
+    with pytest.raises(capi.OimError):
+        capi.oim_schedule_triangular(10, 1.0, 0)

@@ -133,3 +133,16 @@ def test_single_step_is_synchronous_euler(orc):
     th, _ = orc.run(g, 3, K, Ks, 0.0, dt, 1, 1, seed=1, theta0=th0)
     expect = (th0[0] + dt * orc.derivative(g, 3, th0[0], K, Ks)) % 1.0
     assert np.max(np.abs(circ(th[0] - expect))) < 1e-15
+
+
+def test_triangular_waveform_shape(orc):
+    # Algorithm 1's Ks waveform: 0 at each period start, Ks_max at mid-period, linear between
+    T, kmax, P = 1200, 1.7, 3
+    ks = orc.triangular(T, kmax, P)
+    period = T // P
+    assert np.allclose(ks[::period], 0.0, atol=1e-12)
+    assert np.allclose(ks[period // 2::period], kmax, atol=1e-12)
+    assert ks.min() >= 0 and ks.max() <= kmax + 1e-12
+    d = np.diff(ks[:period // 2])
+    assert np.allclose(d, d[0]) and d[0] > 0              # linear rise
+    assert np.allclose(ks[:period], ks[period:2 * period])  # periodic
