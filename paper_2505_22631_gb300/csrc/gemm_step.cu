@@ -44,12 +44,6 @@ struct GemmArgs {
     int32_t* err;
 };
 
-__device__ __forceinline__ float noise_of(uint64_t seed, uint32_t g, uint32_t i, uint32_t t, uint32_t r) {
-    const uint4 x = draw_block(seed, g, kStreamNoise, i, t, r >> 2);
-    const float2 z = (r & 2) ? box_muller_fast(x.z, x.w) : box_muller_fast(x.x, x.y);
-    return (r & 1) ? z.y : z.x;
-}
-
 template <int BN, int S>
 __global__ void __launch_bounds__(256, 1)
     gemm_step_kernel(const __grid_constant__ CUtensorMap mX, const __grid_constant__ CUtensorMap mW,
@@ -64,10 +58,15 @@ __global__ void __launch_bounds__(256, 1)
     unsigned char* sB = base + S * kABytes;
     __shared__ __align__(8) uint64_t full[S], empty[S], done;
     __shared__ uint32_t tmem_slot;
+    __shared__ int issued, consumed;   // K blocks loaded / multiplied (error-path drain)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * BN;
     const int KB = a.n_pad / kBK;
+    if (threadIdx.x == 0) {
+        issued = 0;
+        consumed = 0;
+    }
     if (threadIdx.x == 0) {
         prefetch_map(&mX);
         prefetch_map(&mW);
@@ -84,20 +83,24 @@ __global__ void __launch_bounds__(256, 1)
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
 
-    if (threadIdx.x == 0) {
-        const uint32_t idesc = idesc_bf16_f32(kBM, BN);
-        bool ok = true;
-        for (int kb = 0; kb < KB && kb < S; ++kb) {
-            mbar_arrive_expect_tx(&full[kb], kABytes + kBBytes);
-            tma_load_2d(sA + kb * kABytes, &mX, kb * kBK, m0, &full[kb]);
-            tma_load_2d(sB + kb * kBBytes, &mW, kb * kBK, n0, &full[kb]);
-        }
-        for (int kb = 0; kb < KB && ok; ++kb) {
+    // warp 1 lane 0: TMA producer; warp 0 lane 0: MMA issuer.  The producer refills a
+    // stage as soon as the MMAs reading it have completed; the issuer never waits on
+    // anything but data, so the tensor pipe runs the K loop back to back.
+    if (warp == 1 && lane == 0) {
+        for (int kb = 0; kb < KB; ++kb) {
             const int s = kb % S;
-            if (!mbar_wait(&full[s], (kb / S) & 1, a.err, kErrFullWait)) {
-                ok = false;
-                break;
-            }
+            if (kb >= S && !mbar_wait(&empty[s], ((kb / S) - 1) & 1, a.err, kErrEmptyWait)) break;
+            mbar_arrive_expect_tx(&full[s], kABytes + kBBytes);
+            tma_load_2d(sA + s * kABytes, &mX, kb * kBK, m0, &full[s]);
+            tma_load_2d(sB + s * kBBytes, &mW, kb * kBK, n0, &full[s]);
+            issued = kb + 1;
+        }
+    }
+    if (warp == 0 && lane == 0) {
+        const uint32_t idesc = idesc_bf16_f32(kBM, BN);
+        for (int kb = 0; kb < KB; ++kb) {
+            const int s = kb % S;
+            if (!mbar_wait(&full[s], (kb / S) & 1, a.err, kErrFullWait)) break;
             tc_fence_after();
             const uint32_t a0 = smem_u32(sA + s * kABytes), b0 = smem_u32(sB + s * kBBytes);
 #pragma unroll
@@ -105,16 +108,9 @@ __global__ void __launch_bounds__(256, 1)
                 umma_bf16(tmem, sdesc_kmajor_sw128(a0 + 32 * k), sdesc_kmajor_sw128(b0 + 32 * k), idesc,
                           (kb | k) != 0);
             umma_commit(&empty[s]);
-            if (kb + S < KB) {
-                if (!mbar_wait(&empty[s], (kb / S) & 1, a.err, kErrEmptyWait)) {
-                    ok = false;
-                    break;
-                }
-                mbar_arrive_expect_tx(&full[s], kABytes + kBBytes);
-                tma_load_2d(sA + s * kABytes, &mX, (kb + S) * kBK, m0, &full[s]);
-                tma_load_2d(sB + s * kBBytes, &mW, (kb + S) * kBK, n0, &full[s]);
-            }
+            consumed = kb + 1;
         }
+        // completes when every MMA issued above has finished (also after an early exit)
         umma_commit(&done);
     }
     __syncwarp();
@@ -153,13 +149,27 @@ __global__ void __launch_bounds__(256, 1)
             th[0] = t0.x; th[1] = t0.y; th[2] = t0.z; th[3] = t0.w;
             th[4] = t1.x; th[5] = t1.y; th[6] = t1.z; th[7] = t1.w;
             __align__(16) __nv_bfloat16 oc[8], os[8];
+            // Philox blocks of this chunk: the four replica lanes of a quad that share a
+            // half (same comp) need the same block per node; lane rho computes the blocks of
+            // nodes rho and rho + 4 of its half and the group exchanges them by shuffles
+            const int rho = (lane >> 1) & 3;
+            const uint32_t rq = (uint32_t)(r >> 2);
+            const uint4 blk0 = draw_block(a.seed, (uint32_t)a.graph, kStreamNoise, (uint32_t)(i0 + rho),
+                                          (uint32_t)a.t, rq);
+            const uint4 blk1 = draw_block(a.seed, (uint32_t)a.graph, kStreamNoise, (uint32_t)(i0 + rho + 4),
+                                          (uint32_t)a.t, rq);
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
+                const int src = (lane & ~7) | ((j & 3) << 1) | comp;
+                const uint4 b = (j < 4) ? blk0 : blk1;
+                const uint32_t w0 = __shfl_sync(full_mask, b.x, src), w1 = __shfl_sync(full_mask, b.y, src);
+                const uint32_t w2 = __shfl_sync(full_mask, b.z, src), w3 = __shfl_sync(full_mask, b.w, src);
                 const int i = i0 + j;
                 if (i < a.n) {
                     const float2 cs = cos_sin_2pi_fast(th[j]);
                     const float d = cs.y * A[j] - cs.x * B[j];
-                    const float z = noise_of(a.seed, (uint32_t)a.graph, (uint32_t)i, (uint32_t)a.t, (uint32_t)r);
+                    const float2 zz = (r & 2) ? box_muller_fast(w2, w3) : box_muller_fast(w0, w1);
+                    const float z = (r & 1) ? zz.y : zz.x;
                     const float tn = wrap01(th[j] + (dtK * d - dtKs * sin_q(a.q, cs.x, cs.y)) + kick * z);
                     const float2 ncs = cos_sin_2pi_fast(tn);
                     th[j] = tn;
@@ -178,6 +188,10 @@ __global__ void __launch_bounds__(256, 1)
         }
     }
     tc_fence_before();
+    __syncthreads();
+    // after a timed-out wait, let copies still in flight land before the block exits
+    if (threadIdx.x == 0)
+        for (int kb = consumed; kb < issued; ++kb) mbar_wait(&full[kb % S], (kb / S) & 1, a.err, kErrFullWait);
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, kCols);
 }

@@ -129,12 +129,21 @@ def _c5(steps=None, replicas=None, count=64):
                     "64 Erdos-Renyi graphs for schedule learning")
 
 
+def _dense(steps=None, replicas=None):
+    g = erdos_renyi(2000, 0.05, BASE_SEED + 4, "+1")
+    T = steps or 1000
+    K, Ks, Kn = _schedules([g], T)
+    return Workload("maxcut_er2000_p0.05_R1024", [g], 2, replicas or 1024, T, 0.01, K, Ks, Kn,
+                    BASE_SEED, "denser max-cut graph (mean degree 100), the tensor-core form's case")
+
+
 WORKLOADS = {
     "er800": _c1,
     "torus_er2000": _c2,
     "planted600": _c3,
     "uneven16": _c4,
     "er64": _c5,
+    "dense2000": _dense,
 }
 
 
