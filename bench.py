@@ -47,15 +47,20 @@ def load_peaks():
         return p
 
 
-KERNEL_SOURCES = ["paper_2505_22631_gb300/csrc/step_resident.cu",
-                  "paper_2505_22631_gb300/csrc/oim_device.cuh",
-                  "paper_2505_22631_gb300/csrc/step_stream.cu"]
+CSRC = "paper_2505_22631_gb300/csrc/"
+KERNEL_SOURCES = {
+    "resident": [CSRC + "step_resident.cu", CSRC + "oim_device.cuh"],
+    "stream": [CSRC + "step_stream.cu", CSRC + "oim_device.cuh"],
+    "gemm": [CSRC + "gemm_step.cu", CSRC + "tc_common.cuh", CSRC + "oim_device.cuh"],
+}
 
 
-def kernel_source_hash():
+def kernel_source_hash(kernel):
+    """sha1 prefix of the source files that define `kernel`."""
     import hashlib
+    fam = "resident" if kernel.startswith("resident") else ("gemm" if kernel.startswith("gemm") else "stream")
     h = hashlib.sha1()
-    for f in KERNEL_SOURCES:
+    for f in KERNEL_SOURCES[fam]:
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -67,7 +72,7 @@ def profiled_traffic(kernel, workload):
     path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     if not os.path.exists(path):
         return None
-    want = kernel_source_hash()
+    want = kernel_source_hash(kernel)
     for line in open(path):
         if line.startswith("#") or not line.strip():
             continue
@@ -260,6 +265,16 @@ def first_hit(trace_best, target):
     return int(hit[0]) if hit.size else None
 
 
+def kernels_per_run(form, steps, readout_every):
+    """Kernels of this library that one run enqueues (memsets and copies excluded)."""
+    readouts = steps // readout_every if readout_every > 0 else 0
+    if form == 2:          # resident: one launch covers every step and readout
+        return 1
+    if form == 3:          # dense: init, a step kernel per step, relayout + score per readout, final relayout
+        return 1 + steps + 2 * readouts + 1
+    return 1 + steps + readouts   # stream: init, a step kernel per step, a score pass per readout
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -345,26 +360,47 @@ def main():
     edge_updates = w.edge_updates() * world
     value = edge_updates / (ms_step / 1e3)
 
-    # roofline of the dominant kernel.  Algorithmic bytes per node-replica-step
-    # are the state a step must move if nothing stays on chip: read and write the
-    # phase (4 + 4 B), write and read the (cos, sin) cache (8 + 8 B in FP32, 4 + 4 B
-    # in 16 bits), plus the CSR structure once per graph and step.
+    # roofline of the dominant kernel.  CSR forms: algorithmic bytes per
+    # node-replica-step are the state a step must move if nothing stays on chip:
+    # read and write the phase (4 + 4 B), write and read the (cos, sin) cache (8 + 8 B
+    # in FP32, 4 + 4 B in 16 bits), plus the CSR structure once per graph and step.
+    # Dense form: a tensor-core contraction of 2 * (2R) * n * n FLOPs per step.
     peaks = load_peaks()
-    node_replica_steps = w.nodes * w.replicas * w.steps
-    csr_bytes = sum(4 * g.nnz + 8 * (g.n + 1) for g in w.graphs) * w.steps
-    bytes_per_unit = 24 if info["precision"] == 1 else 16
-    alg_bytes = node_replica_steps * bytes_per_unit + csr_bytes
-    achieved = alg_bytes / (ms_step / 1e3) / 1e9
     prec_name = {1: "fp32", 2: "bf16", 3: "fp16"}.get(info["precision"])
     kname = {2: f"resident_quad_kernel<{prec_name}>", 1: "step_stream_kernel",
              3: "gemm_step_kernel"}.get(info["form"], "?")
     traffic = profiled_traffic(kname, w.name)
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "kernel": kname,
-                "peak_source": peaks["source"], "algorithmic_bytes_per_launch": alg_bytes,
-                "bytes_per_node_replica_step": bytes_per_unit,
-                "kernel_time": "CUDA events around each run (one launch of the resident "
-                               "kernel plus a 1.6 MB memset and schedule copies)"}
+    if info["form"] == 3:
+        n = w.graphs[0].n
+        flops_per_step = 2.0 * (2 * w.replicas) * n * n
+        alg_flops = flops_per_step * w.steps
+        achieved = alg_flops / (ms_step / 1e3) / 1e12
+        peak = peaks["bf16_tflops"]
+        roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": traffic, "kernel": kname,
+                    "peak_source": peaks["source"] + " bf16 burst",
+                    "algorithmic_flops_per_launch": flops_per_step,
+                    "flops_per_node_replica_step": 4.0 * n,
+                    "kernel_time": "CUDA events around each run divided by its steps (one "
+                                   "launch per step, plus an init kernel and a score pass "
+                                   "per readout, counted against the step kernel)"}
+    else:
+        node_replica_steps = w.nodes * w.replicas * w.steps
+        csr_bytes = sum(4 * g.nnz + 8 * (g.n + 1) for g in w.graphs) * w.steps
+        bytes_per_unit = 24 if info["precision"] == 1 else 16
+        alg_bytes = node_replica_steps * bytes_per_unit + csr_bytes
+        achieved = alg_bytes / (ms_step / 1e3) / 1e9
+        resident = info["form"] == 2
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "kernel": kname,
+                    "peak_source": peaks["source"],
+                    "algorithmic_bytes_per_launch": alg_bytes if resident else alg_bytes / w.steps,
+                    "bytes_per_node_replica_step": bytes_per_unit,
+                    "kernel_time": ("CUDA events around each run (one launch of the resident "
+                                    "kernel plus a memset of the trace and schedule copies)"
+                                    if resident else
+                                    "CUDA events around each run (one launch per step plus an "
+                                    "init kernel and a score pass per readout)")}
 
     # end to end through the C ABI with host buffers: upload graphs and schedules,
     # simulate, read spins and scores back, free everything
@@ -428,8 +464,7 @@ def main():
         "roofline": roofline,
         "clocks": clocks,
         "e2e": e2e,
-        "gpu_launches": args.steps * (1 if info["form"] == 2 else
-                                      w.steps + 1 + (w.steps // args.readout_every if args.readout_every else 0)),
+        "gpu_launches": args.steps * kernels_per_run(info["form"], w.steps, args.readout_every),
         "wall_s_timed_region": wall,
         "step_ms_all": ms,
     }

@@ -45,7 +45,7 @@ struct GemmArgs {
 };
 
 template <int BN, int S>
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(256, (BN <= 128 ? 2 : 1))
     gemm_step_kernel(const __grid_constant__ CUtensorMap mX, const __grid_constant__ CUtensorMap mW,
                      GemmArgs a) {
     using namespace tc;
@@ -241,7 +241,10 @@ __global__ void gemm_to_common_kernel(int n, int n_pad, int R_pad, int node_off,
 
 }  // namespace
 
-int gemm_bn_for(int n) { return n >= 1024 ? 256 : 128; }
+// 128-wide tiles with three stages use 97 KB of shared memory and 128 TMEM columns,
+// so two blocks share an SM and one block's epilogue overlaps the other's MMAs.
+int gemm_bn_for(int) { return 128; }
+constexpr int kStages128 = 3, kStages256 = 4;
 int gemm_n_pad(int n) {
     const int bn = gemm_bn_for(n);
     return ((n + bn - 1) / bn) * bn;
@@ -272,12 +275,12 @@ int gemm_setup(oim_run_s& r) {
         rc = make_map_bf16(&st.map_x[b], st.x[b], st.n_pad, 2 * (uint64_t)r.R_pad, (uint64_t)st.n_pad * 2, 128);
     if (rc != OIM_OK) return rc;
     // opt in to the large shared-memory footprint once, outside any stream capture
-    constexpr int S = 4;
-    e = cudaFuncSetAttribute(gemm_step_kernel<256, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)((size_t)S * (kABytes + 256 * 128) + 1024));
+    e = cudaFuncSetAttribute(gemm_step_kernel<256, kStages256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)((size_t)kStages256 * (kABytes + 256 * 128) + 1024));
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(gemm_step_kernel<128, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)((size_t)S * (kABytes + 128 * 128) + 1024));
+        e = cudaFuncSetAttribute(gemm_step_kernel<128, kStages128>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)((size_t)kStages128 * (kABytes + 128 * 128) + 1024));
     if (e != cudaSuccess) return cuda_fail(e, "dense form shared memory");
     return OIM_OK;
 }
@@ -319,14 +322,13 @@ cudaError_t launch_gemm_step(const oim_run_s& r, int64_t t, cudaStream_t s) {
     a.n = st.n;
     a.n_pad = st.n_pad;
     a.err = r.d_err;
-    constexpr int S = 4;
     dim3 grid(st.n_pad / st.bn, (2 * r.R_pad) / kBM);
     if (st.bn == 256) {
-        const size_t smem = (size_t)S * (kABytes + 256 * 128) + 1024;
-        gemm_step_kernel<256, S><<<grid, 256, smem, s>>>(st.map_x[t & 1], st.map_w, a);
+        const size_t smem = (size_t)kStages256 * (kABytes + 256 * 128) + 1024;
+        gemm_step_kernel<256, kStages256><<<grid, 256, smem, s>>>(st.map_x[t & 1], st.map_w, a);
     } else {
-        const size_t smem = (size_t)S * (kABytes + 128 * 128) + 1024;
-        gemm_step_kernel<128, S><<<grid, 256, smem, s>>>(st.map_x[t & 1], st.map_w, a);
+        const size_t smem = (size_t)kStages128 * (kABytes + 128 * 128) + 1024;
+        gemm_step_kernel<128, kStages128><<<grid, 256, smem, s>>>(st.map_x[t & 1], st.map_w, a);
     }
     return cudaGetLastError();
 }
