@@ -469,6 +469,14 @@ def main():
         "step_ms_all": ms,
     }
 
+    # the job's answer: best score per graph over every rank's replicas and the
+    # winning spins (the only cross-rank data; taken after the timed region)
+    from paper_2505_22631_gb300.distributed import best_across_ranks
+    res = run.readout(spins=True, trace=False)
+    best, winner, _ = best_across_ranks(res["score"], res["spins"], w.q)
+    line["best_score"] = {"per_graph": best.tolist(), "winning_rank": winner.tolist(),
+                          "kind": "cut" if w.q == 2 else "conflicts"}
+
     if rank == 0 and not args.no_quality:
         line["quality"] = quality(w, prob, problems, args, stream, ms_step,
                                   (form, precision, rpb, threads))
