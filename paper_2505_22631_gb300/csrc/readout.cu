@@ -7,6 +7,8 @@
 // sum_{i<j} w_ij [s_i == s_j], in FP64; the cut is wtot - agree.  With integer
 // weights every partial sum is an integer below 2^53, so the result is exact
 // whatever the order of the additions.
+#include <algorithm>
+
 #include "oim_device.cuh"
 #include "oim_internal.h"
 
@@ -14,21 +16,19 @@ namespace oim {
 
 namespace {
 
-constexpr int kNodesPerThread = 16;
-
-// Thread = (replica quad, chunk of kNodesPerThread consecutive nodes).  Each
+// Thread = (replica quad, chunk of `npt` consecutive nodes).  Each
 // thread sums the agreeing weight of the upper-triangle edges of its nodes for
 // its four replicas, and flushes with one FP64 atomic per replica whenever the
 // graph changes or the chunk ends.
 __global__ void __launch_bounds__(256) score_kernel(CSRDev csr, const float* __restrict__ theta,
                                                     int R_pad, int q,
                                                     double* __restrict__ agree,
-                                                    int64_t row_stride, int64_t k) {
+                                                    int64_t row_stride, int64_t k, int npt) {
     const int quads = R_pad >> 2;
     const int quad = blockIdx.x * blockDim.x + threadIdx.x;
     if (quad >= quads) return;
-    const int first = blockIdx.y * kNodesPerThread;
-    const int last = min(first + kNodesPerThread, csr.nodes);
+    const int first = blockIdx.y * npt;
+    const int last = min(first + npt, csr.nodes);
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
     int g_cur = -1;
     auto flush = [&]() {
@@ -74,12 +74,12 @@ __global__ void __launch_bounds__(256) score_kernel(CSRDev csr, const float* __r
 
 // E_r = sum_{i<j} w_ij cos(2 pi (theta_i - theta_j)) with FP32 terms, FP64 sum.
 __global__ void __launch_bounds__(256) energy_kernel(CSRDev csr, const float* __restrict__ theta,
-                                                     int R_pad, double* __restrict__ energy) {
+                                                     int R_pad, double* __restrict__ energy, int npt) {
     const int quads = R_pad >> 2;
     const int quad = blockIdx.x * blockDim.x + threadIdx.x;
     if (quad >= quads) return;
-    const int first = blockIdx.y * kNodesPerThread;
-    const int last = min(first + kNodesPerThread, csr.nodes);
+    const int first = blockIdx.y * npt;
+    const int last = min(first + npt, csr.nodes);
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
     int g_cur = -1;
     auto flush = [&]() {
@@ -148,15 +148,34 @@ __global__ void gather_kernel(CSRDev csr, const float* __restrict__ theta, int R
     if (th_out) th_out[gid] = th;
 }
 
+// Nodes per thread of the edge passes: few enough that the grid holds about
+// 2048 threads per SM (the passes are latency bound: one dependent gather per
+// edge), at most 16 so that the FP64 atomics stay few when the grid is large.
+int nodes_per_thread(const oim_run_s& r) {
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+            sms = v;
+        else
+            sms = 152;
+    }
+    const int64_t quads = r.R_pad / 4;
+    const int64_t want = (int64_t)sms * 2048;
+    const int64_t npt = (int64_t)r.p->nodes * quads / want;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(16, npt));
+}
+
 }  // namespace
 
 cudaError_t launch_score(const oim_run_s& r, const float* theta, int64_t k, cudaStream_t s) {
     const int quads = r.R_pad / 4;
+    const int npt = nodes_per_thread(r);
     dim3 block(min(256, ((quads + 31) / 32) * 32));
-    dim3 grid((quads + block.x - 1) / block.x,
-              (unsigned)((r.p->nodes + kNodesPerThread - 1) / kNodesPerThread));
+    dim3 grid((quads + block.x - 1) / block.x, (unsigned)((r.p->nodes + npt - 1) / npt));
     score_kernel<<<grid, block, 0, s>>>(r.p->csr(), theta, r.R_pad, r.p->q, r.d_trace,
-                                        r.readouts_cap, k);
+                                        r.readouts_cap, k, npt);
     return cudaGetLastError();
 }
 
@@ -171,9 +190,9 @@ cudaError_t launch_finalize(const oim_run_s& r, int64_t k, double* score, cudaSt
 cudaError_t launch_energy_of(const oim_run_s& r, const float* theta, double* energy, cudaStream_t s) {
     const int quads = r.R_pad / 4;
     dim3 block(min(256, ((quads + 31) / 32) * 32));
-    dim3 grid((quads + block.x - 1) / block.x,
-              (unsigned)((r.p->nodes + kNodesPerThread - 1) / kNodesPerThread));
-    energy_kernel<<<grid, block, 0, s>>>(r.p->csr(), theta, r.R_pad, energy);
+    const int npt = nodes_per_thread(r);
+    dim3 grid((quads + block.x - 1) / block.x, (unsigned)((r.p->nodes + npt - 1) / npt));
+    energy_kernel<<<grid, block, 0, s>>>(r.p->csr(), theta, r.R_pad, energy, npt);
     return cudaGetLastError();
 }
 

@@ -9,7 +9,8 @@ import numpy as np
 import pytest
 
 from gpu_common import circ, gpu_run, oracle_phases, rad_dist, require_gpu
-from workloads import csr_from_edges, erdos_renyi, linear_ramp, constant, make_workload
+from workloads import (constant, csr_from_edges, erdos_renyi, linear_ramp, make_workload,
+                       sherrington_kirkpatrick)
 
 pytestmark = pytest.mark.gpu
 
@@ -76,3 +77,41 @@ def test_dense_graph_capture_matches_direct():
     a = gpu_run(*args, form="gemm", precision="bf16", use_graph=True).phases()[0]
     b = gpu_run(*args, form="gemm", precision="bf16", use_graph=False).phases()[0]
     assert np.array_equal(a, b)
+
+
+def test_dense_real_valued_all_to_all_coupling_within_1e2_per_row(orc):
+    # Gaussian couplings on every pair: the BF16 operands still meet the per-row bound
+    g = sherrington_kirkpatrick(384, 11)
+    R, dt, K = 64, 1e-3, 1.0
+    run = gpu_run(g, 2, K, 0.0, 0.0, dt, 1, R, 21, form="gemm", precision="bf16")
+    assert run.info()["form"] == 3
+    th0 = orc.init_phases(g.n, R, 21)
+    D = circ(run.phases()[0].astype(np.float64) - th0) / (np.float32(dt) * K)
+    rows = np.repeat(np.arange(g.n), g.degrees())
+    A = np.zeros((R, g.n))
+    B = np.zeros((R, g.n))
+    for r in range(R):
+        np.add.at(A[r], rows, g.w * np.cos(2 * np.pi * th0[r, g.col]))
+        np.add.at(B[r], rows, g.w * np.sin(2 * np.pi * th0[r, g.col]))
+    D64 = np.stack([orc.coupling(g, th0[r]) for r in range(R)])
+    err = np.linalg.norm(D - D64, axis=0)
+    ref = np.sqrt(np.sum(A**2 + B**2, axis=0))
+    assert np.max(err / ref) <= 1e-2
+
+
+@pytest.mark.parametrize("q", [4, 5])
+def test_dense_potts_readout_and_short_run_parity(orc, q):
+    g = sherrington_kirkpatrick(200, 3 + q)
+    T, R = 20, 64
+    K, Ks, Kn = constant(T, 0.05), linear_ramp(T, 0, 1), constant(T, 0.1)
+    run = gpu_run(g, q, K, Ks, Kn, 0.01, T, R, 9, form="gemm", precision="bf16", readout_every=10)
+    th = run.phases()[0]
+    out = run.readout()
+    spins = orc.readout_f32(q, th)
+    assert np.array_equal(out["spins"][0], spins)
+    # real weights: each node's agreeing weight is an FP32 sum of at most n - 1 terms
+    # (then FP64 across nodes), so it is off by at most (n - 1) 2^-24 sum |w| in total
+    bound = (g.n - 1) * 2.0**-24 * np.abs(g.w).sum() / 2
+    assert np.max(np.abs(out["score"][0] - orc.scores(g, q, spins))) <= bound
+    ref = oracle_phases(orc, g, q, K, Ks, Kn, 0.01, T, R, 9)
+    assert np.median(rad_dist(th, ref)) <= 1e-3

@@ -9,11 +9,13 @@ shapes (sizes, densities, +1 / +-1 weights, toroidal grids, planted
 3-colourable graphs), not their items.
 """
 from .graphs import (CSRGraph, csr_from_edges, erdos_renyi, gnm, planted_partition, torus,
-                     cycle, complete, complete_bipartite, petersen, from_dense)
+                     cycle, complete, complete_bipartite, petersen, from_dense,
+                     sherrington_kirkpatrick)
 from .configs import WORKLOADS, Workload, linear_ramp, constant, make_workload
 
 __all__ = [
     "CSRGraph", "csr_from_edges", "erdos_renyi", "gnm", "planted_partition", "torus", "cycle",
-    "complete", "complete_bipartite", "petersen", "from_dense", "WORKLOADS", "Workload",
+    "complete", "complete_bipartite", "petersen", "from_dense", "sherrington_kirkpatrick",
+    "WORKLOADS", "Workload",
     "linear_ramp", "constant", "make_workload",
 ]

@@ -165,6 +165,14 @@ def complete(n: int) -> CSRGraph:
     return csr_from_edges(n, i, j, None, f"K{n}")
 
 
+def sherrington_kirkpatrick(n: int, seed: int) -> CSRGraph:
+    """All-to-all couplings w_ij ~ N(0, 1), i.i.d. per pair (real-valued, dense)."""
+    rng = np.random.default_rng(seed)
+    i, j = np.triu_indices(n, 1)
+    w = rng.standard_normal(i.shape[0]).astype(np.float32)
+    return csr_from_edges(n, i, j, w, f"sk{n}")
+
+
 def complete_bipartite(a: int, b: int) -> CSRGraph:
     i, j = np.meshgrid(np.arange(a), a + np.arange(b), indexing="ij")
     return csr_from_edges(a + b, i.ravel(), j.ravel(), None, f"K{a},{b}")
