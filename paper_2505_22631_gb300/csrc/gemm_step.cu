@@ -5,14 +5,15 @@
 // columns = nodes, BF16) and W the dense coupling matrix (BF16; +-1 weights are
 // exact), one step needs D^T = X^T W, i.e. D^T[2r][i] = A_{i,r} = sum_j w_ij c_j,r and
 // D^T[2r+1][i] = B_{i,r}; W is symmetric, so W itself is the K-major B operand.
-// A CTA computes a 128 x BN tile of D^T with tcgen05.mma (FP32 accumulator in
-// TMEM) from TMA-loaded 128-byte-swizzled tiles, then its eight warps finish the
-// step for the tile's (node, replica) pairs: coupling s A - c B, injection,
-// Philox noise, Euler update and wrap (Eq. 5, Algorithm 1), and write the new
-// FP32 phases ([R_pad][n_pad], replica-major) and the next step's BF16 X^T.
+// A CTA computes a 128 x 128 tile of D^T with tcgen05.mma (FP32 accumulator in
+// TMEM) from TMA-loaded 128-byte-swizzled tiles, and its eight epilogue warps finish
+// the step for the tile's (node, replica) pairs: coupling s A - c B, injection,
+// Philox noise, Euler update and wrap (Eq. 5, Algorithm 1), writing the new FP32
+// phases ([R_pad][n_pad], replica-major) and the next step's BF16 X^T.
 // The trigonometry and Box-Muller use the hardware approximations (the BF16
 // operands round at 2^-9, far above their ~1e-6 error).
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <string>
 
@@ -44,13 +45,30 @@ struct GemmArgs {
     int32_t* err;
 };
 
-template <int BN, int S>
-__global__ void __launch_bounds__(256, (BN <= 128 ? 2 : 1))
+// Block layout: warp 0 lane 0 streams the K blocks with TMA, warp 1 lane 0 issues the
+// MMAs, warps 2..9 are the epilogue.  TMEM lanes are split by warp index mod 4, so
+// the epilogue warps cover the four 32-lane quadrants twice: warp w takes quadrant
+// w & 3 and column half (w - 2) >> 2.  While the K loop runs, the epilogue warps
+// already do everything that does not need the coupling sums (load theta, its cos
+// and sin, the injection term, the Philox draws and Box-Muller noise) and park the
+// results in TMEM columns beside the accumulator; once the product is complete
+// only the coupling, the update, the new cos / sin and the stores remain.  The two
+// warps of a quadrant share its TMEM lanes, so each column half has its own stash:
+// per 16-column chunk 8 FP32 bases and 8 (cos, sin) pairs packed as FP16
+// (2^-11 relative, far below the BF16 operands' 2^-9).
+constexpr int kBN = 128;                   // tile columns (nodes)
+constexpr int kStages = 3;                 // shared-memory ring depth
+constexpr int kThreads = 320;              // 10 warps
+constexpr uint32_t kCols = 256;            // TMEM: accumulator [0, 128), stashes [128, 256)
+constexpr uint32_t kStash = 128;           // half h, chunk k: columns 128 + 64 h + 16 k
+constexpr size_t kSmemBytes = (size_t)kStages * (kABytes + kBN * 128) + 1024;
+
+template <int S>
+__global__ void __launch_bounds__(kThreads, 2)
     gemm_step_kernel(const __grid_constant__ CUtensorMap mX, const __grid_constant__ CUtensorMap mW,
                      GemmArgs a) {
     using namespace tc;
-    constexpr int kBBytes = BN * 128;
-    constexpr uint32_t kCols = BN <= 64 ? 64 : (BN <= 128 ? 128 : 256);
+    constexpr int kBBytes = kBN * 128;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base =
         reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -61,13 +79,11 @@ __global__ void __launch_bounds__(256, (BN <= 128 ? 2 : 1))
     __shared__ int issued, consumed;   // K blocks loaded / multiplied (error-path drain)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * BN;
+    const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * kBN;
     const int KB = a.n_pad / kBK;
     if (threadIdx.x == 0) {
         issued = 0;
         consumed = 0;
-    }
-    if (threadIdx.x == 0) {
         prefetch_map(&mX);
         prefetch_map(&mW);
         for (int s = 0; s < S; ++s) {
@@ -83,108 +99,138 @@ __global__ void __launch_bounds__(256, (BN <= 128 ? 2 : 1))
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
 
-    // warp 1 lane 0: TMA producer; warp 0 lane 0: MMA issuer.  The producer refills a
-    // stage as soon as the MMAs reading it have completed; the issuer never waits on
-    // anything but data, so the tensor pipe runs the K loop back to back.
-    if (warp == 1 && lane == 0) {
-        for (int kb = 0; kb < KB; ++kb) {
-            const int s = kb % S;
-            if (kb >= S && !mbar_wait(&empty[s], ((kb / S) - 1) & 1, a.err, kErrEmptyWait)) break;
-            mbar_arrive_expect_tx(&full[s], kABytes + kBBytes);
-            tma_load_2d(sA + s * kABytes, &mX, kb * kBK, m0, &full[s]);
-            tma_load_2d(sB + s * kBBytes, &mW, kb * kBK, n0, &full[s]);
-            issued = kb + 1;
+    if (warp == 0) {
+        // TMA producer: refill a stage as soon as the MMAs reading it have completed
+        if (lane == 0) {
+            for (int kb = 0; kb < KB; ++kb) {
+                const int s = kb % S;
+                if (kb >= S && !mbar_wait(&empty[s], ((kb / S) - 1) & 1, a.err, kErrEmptyWait)) break;
+                mbar_arrive_expect_tx(&full[s], kABytes + kBBytes);
+                tma_load_2d(sA + s * kABytes, &mX, kb * kBK, m0, &full[s]);
+                tma_load_2d(sB + s * kBBytes, &mW, kb * kBK, n0, &full[s]);
+                issued = kb + 1;
+            }
         }
-    }
-    if (warp == 0 && lane == 0) {
-        const uint32_t idesc = idesc_bf16_f32(kBM, BN);
-        for (int kb = 0; kb < KB; ++kb) {
-            const int s = kb % S;
-            if (!mbar_wait(&full[s], (kb / S) & 1, a.err, kErrFullWait)) break;
-            tc_fence_after();
-            const uint32_t a0 = smem_u32(sA + s * kABytes), b0 = smem_u32(sB + s * kBBytes);
+        __syncwarp();
+    } else if (warp == 1) {
+        // MMA issuer: waits on data only, so the tensor pipe runs the K loop back to back
+        if (lane == 0) {
+            const uint32_t idesc = idesc_bf16_f32(kBM, kBN);
+            for (int kb = 0; kb < KB; ++kb) {
+                const int s = kb % S;
+                if (!mbar_wait(&full[s], (kb / S) & 1, a.err, kErrFullWait)) break;
+                tc_fence_after();
+                const uint32_t a0 = smem_u32(sA + s * kABytes), b0 = smem_u32(sB + s * kBBytes);
 #pragma unroll
-            for (int k = 0; k < kBK / 16; ++k)
-                umma_bf16(tmem, sdesc_kmajor_sw128(a0 + 32 * k), sdesc_kmajor_sw128(b0 + 32 * k), idesc,
-                          (kb | k) != 0);
-            umma_commit(&empty[s]);
-            consumed = kb + 1;
+                for (int k = 0; k < kBK / 16; ++k)
+                    umma_bf16(tmem, sdesc_kmajor_sw128(a0 + 32 * k), sdesc_kmajor_sw128(b0 + 32 * k), idesc,
+                              (kb | k) != 0);
+                umma_commit(&empty[s]);
+                consumed = kb + 1;
+            }
+            // completes when every MMA issued above has finished (also after an early exit)
+            umma_commit(&done);
         }
-        // completes when every MMA issued above has finished (also after an early exit)
-        umma_commit(&done);
-    }
-    __syncwarp();
-    const bool have = mbar_wait(&done, 0, a.err, kErrDoneWait);
-    tc_fence_after();
-
-    if (have) {
-        // warp -> TMEM lane quadrant (rows) and half of the tile's columns
-        const int quad = warp & 3, half = warp >> 2;
+        __syncwarp();
+    } else {
+        const int quad = warp & 3, half = (warp - 2) >> 2;
+        const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16);
         const int row = m0 + quad * 32 + lane;            // row of X^T: 2 r + comp
         const int r = row >> 1, comp = row & 1;
         const float K = __ldg(a.K + a.t), Ks = __ldg(a.Ks + a.t), Kn = __ldg(a.Kn + a.t);
         const float dtK = a.dt * K, dtKs = a.dt * Ks, kick = Kn * a.sqrt_dt;
         float* th_row = a.theta + (size_t)r * a.n_pad;
-        __nv_bfloat16* xc = a.x_out + (size_t)(2 * r) * a.n_pad;        // cos row of replica r
-        __nv_bfloat16* xs = xc + a.n_pad;                                  // sin row
         const unsigned full_mask = 0xffffffffu;
+        constexpr int kChunks = kBN / 2 / 16;              // 16-column chunks per half
+
+        // ---- before the product: per node-replica base = theta - dt Ks sin(2 pi q theta)
+        //      + Kn sqrt(dt) xi, and (cos, sin) of theta, parked in TMEM
+        // lane pair (cos row, sin row) of replica r: the cos lane finishes nodes 0..7 of
+        // each chunk, the sin lane nodes 8..15
 #pragma unroll 1
-        for (int c0 = half * (BN / 2); c0 < (half + 1) * (BN / 2); c0 += 16) {
-            uint32_t v[16];
-            tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0, v);
-            // lane pair (cos row, sin row) of replica r: the cos lane finishes nodes 0..7
-            // of the chunk, the sin lane nodes 8..15; each needs the other's sums
-            float A[8], B[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const float send = __uint_as_float(comp ? v[j] : v[j + 8]);
-                const float recv = __shfl_xor_sync(full_mask, send, 1);
-                A[j] = comp ? recv : __uint_as_float(v[j]);
-                B[j] = comp ? __uint_as_float(v[j + 8]) : recv;
-            }
-            const int i0 = n0 + c0 + 8 * comp;                 // first node of this lane's eight
+        for (int k = 0; k < kChunks; ++k) {
+            const int c0 = half * (kBN / 2) + 16 * k;
+            const int i0 = n0 + c0 + 8 * comp;             // first node of this lane's eight
             float th[8];
             const float4 t0 = *reinterpret_cast<const float4*>(th_row + i0);
             const float4 t1 = *reinterpret_cast<const float4*>(th_row + i0 + 4);
             th[0] = t0.x; th[1] = t0.y; th[2] = t0.z; th[3] = t0.w;
             th[4] = t1.x; th[5] = t1.y; th[6] = t1.z; th[7] = t1.w;
-            __align__(16) __nv_bfloat16 oc[8], os[8];
-            // Philox blocks of this chunk: the four replica lanes of a quad that share a
-            // half (same comp) need the same block per node; lane rho computes the blocks of
-            // nodes rho and rho + 4 of its half and the group exchanges them by shuffles
+            // Philox blocks: the four replica lanes of a quad that share a half (same comp)
+            // need the same block per node; lane rho computes the blocks of nodes rho and
+            // rho + 4 of its eight and the group exchanges them by shuffles
             const int rho = (lane >> 1) & 3;
             const uint32_t rq = (uint32_t)(r >> 2);
             const uint4 blk0 = draw_block(a.seed, (uint32_t)a.graph, kStreamNoise, (uint32_t)(i0 + rho),
                                           (uint32_t)a.t, rq);
             const uint4 blk1 = draw_block(a.seed, (uint32_t)a.graph, kStreamNoise, (uint32_t)(i0 + rho + 4),
                                           (uint32_t)a.t, rq);
+            uint32_t vb[8], vcs[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 const int src = (lane & ~7) | ((j & 3) << 1) | comp;
                 const uint4 b = (j < 4) ? blk0 : blk1;
                 const uint32_t w0 = __shfl_sync(full_mask, b.x, src), w1 = __shfl_sync(full_mask, b.y, src);
                 const uint32_t w2 = __shfl_sync(full_mask, b.z, src), w3 = __shfl_sync(full_mask, b.w, src);
-                const int i = i0 + j;
-                if (i < a.n) {
-                    const float2 cs = cos_sin_2pi_fast(th[j]);
-                    const float d = cs.y * A[j] - cs.x * B[j];
+                float bj = 0.0f;
+                float2 cs = make_float2(0.0f, 0.0f);
+                if (i0 + j < a.n) {
+                    cs = cos_sin_2pi_fast(th[j]);
                     const float2 zz = (r & 2) ? box_muller_fast(w2, w3) : box_muller_fast(w0, w1);
                     const float z = (r & 1) ? zz.y : zz.x;
-                    const float tn = wrap01(th[j] + (dtK * d - dtKs * sin_q(a.q, cs.x, cs.y)) + kick * z);
-                    const float2 ncs = cos_sin_2pi_fast(tn);
+                    bj = (th[j] - dtKs * sin_q(a.q, cs.x, cs.y)) + kick * z;
+                }
+                vb[j] = __float_as_uint(bj);
+                const __half2 h = __floats2half2_rn(cs.x, cs.y);
+                vcs[j] = *reinterpret_cast<const uint32_t*>(&h);
+            }
+            const uint32_t col = kStash + 64u * (uint32_t)half + 16u * (uint32_t)k;
+            tmem_st8(lane_base + col, vb);
+            tmem_st8(lane_base + col + 8, vcs);
+        }
+        tmem_wait_st();
+
+        // ---- after the product: coupling s A - c B, update, wrap, new (cos, sin)
+        // the TMEM loads below are warp-collective: the whole warp goes on, or none of it
+        const bool have = __all_sync(full_mask, mbar_wait(&done, 0, a.err, kErrDoneWait));
+        tc_fence_after();
+        if (have) {
+            __nv_bfloat16* xc = a.x_out + (size_t)(2 * r) * a.n_pad;    // cos row of replica r
+            __nv_bfloat16* xs = xc + a.n_pad;                              // sin row
+#pragma unroll 1
+            for (int k = 0; k < kChunks; ++k) {
+                const int c0 = half * (kBN / 2) + 16 * k;
+                const int i0 = n0 + c0 + 8 * comp;
+                uint32_t v[16], st[16];
+                tmem_ld16x2(lane_base + (uint32_t)c0,
+                            lane_base + kStash + 64u * (uint32_t)half + 16u * (uint32_t)k, v, st);
+                // each lane of the pair needs the other's sums for its eight nodes
+                float A[8], B[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const float send = __uint_as_float(comp ? v[j] : v[j + 8]);
+                    const float recv = __shfl_xor_sync(full_mask, send, 1);
+                    A[j] = comp ? recv : __uint_as_float(v[j]);
+                    B[j] = comp ? __uint_as_float(v[j + 8]) : recv;
+                }
+                float th[8];
+                __align__(16) __nv_bfloat16 oc[8], os[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const uint32_t hw = st[8 + j];
+                    const float2 cs = __half22float2(*reinterpret_cast<const __half2*>(&hw));
+                    const float d = cs.y * A[j] - cs.x * B[j];
+                    const float tn = (i0 + j < a.n) ? wrap01(__uint_as_float(st[j]) + dtK * d) : 0.0f;
+                    const float2 ncs = (i0 + j < a.n) ? cos_sin_2pi_fast(tn) : make_float2(0.0f, 0.0f);
                     th[j] = tn;
                     oc[j] = __float2bfloat16_rn(ncs.x);
                     os[j] = __float2bfloat16_rn(ncs.y);
-                } else {
-                    th[j] = 0.0f;
-                    oc[j] = __float2bfloat16_rn(0.0f);
-                    os[j] = __float2bfloat16_rn(0.0f);
                 }
+                *reinterpret_cast<float4*>(th_row + i0) = make_float4(th[0], th[1], th[2], th[3]);
+                *reinterpret_cast<float4*>(th_row + i0 + 4) = make_float4(th[4], th[5], th[6], th[7]);
+                *reinterpret_cast<uint4*>(xc + i0) = *reinterpret_cast<const uint4*>(oc);
+                *reinterpret_cast<uint4*>(xs + i0) = *reinterpret_cast<const uint4*>(os);
             }
-            *reinterpret_cast<float4*>(th_row + i0) = make_float4(th[0], th[1], th[2], th[3]);
-            *reinterpret_cast<float4*>(th_row + i0 + 4) = make_float4(th[4], th[5], th[6], th[7]);
-            *reinterpret_cast<uint4*>(xc + i0) = *reinterpret_cast<const uint4*>(oc);
-            *reinterpret_cast<uint4*>(xs + i0) = *reinterpret_cast<const uint4*>(os);
         }
     }
     tc_fence_before();
@@ -241,10 +287,9 @@ __global__ void gemm_to_common_kernel(int n, int n_pad, int R_pad, int node_off,
 
 }  // namespace
 
-// 128-wide tiles with three stages use 97 KB of shared memory and 128 TMEM columns,
-// so two blocks share an SM and one block's epilogue overlaps the other's MMAs.
-int gemm_bn_for(int) { return 128; }
-constexpr int kStages128 = 3, kStages256 = 4;
+// 128-wide tiles with three stages use 97 KB of shared memory and 256 TMEM columns,
+// so two blocks share an SM (and its 512 TMEM columns).
+int gemm_bn_for(int) { return kBN; }
 int gemm_n_pad(int n) {
     const int bn = gemm_bn_for(n);
     return ((n + bn - 1) / bn) * bn;
@@ -275,12 +320,8 @@ int gemm_setup(oim_run_s& r) {
         rc = make_map_bf16(&st.map_x[b], st.x[b], st.n_pad, 2 * (uint64_t)r.R_pad, (uint64_t)st.n_pad * 2, 128);
     if (rc != OIM_OK) return rc;
     // opt in to the large shared-memory footprint once, outside any stream capture
-    e = cudaFuncSetAttribute(gemm_step_kernel<256, kStages256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)((size_t)kStages256 * (kABytes + 256 * 128) + 1024));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(gemm_step_kernel<128, kStages128>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)((size_t)kStages128 * (kABytes + 128 * 128) + 1024));
+    e = cudaFuncSetAttribute(gemm_step_kernel<kStages>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kSmemBytes);
     if (e != cudaSuccess) return cuda_fail(e, "dense form shared memory");
     return OIM_OK;
 }
@@ -322,14 +363,8 @@ cudaError_t launch_gemm_step(const oim_run_s& r, int64_t t, cudaStream_t s) {
     a.n = st.n;
     a.n_pad = st.n_pad;
     a.err = r.d_err;
-    dim3 grid(st.n_pad / st.bn, (2 * r.R_pad) / kBM);
-    if (st.bn == 256) {
-        const size_t smem = (size_t)kStages256 * (kABytes + 256 * 128) + 1024;
-        gemm_step_kernel<256, kStages256><<<grid, 256, smem, s>>>(st.map_x[t & 1], st.map_w, a);
-    } else {
-        const size_t smem = (size_t)kStages128 * (kABytes + 128 * 128) + 1024;
-        gemm_step_kernel<128, kStages128><<<grid, 256, smem, s>>>(st.map_x[t & 1], st.map_w, a);
-    }
+    dim3 grid(st.n_pad / kBN, (2 * r.R_pad) / kBM);
+    gemm_step_kernel<kStages><<<grid, kThreads, kSmemBytes, s>>>(st.map_x[t & 1], st.map_w, a);
     return cudaGetLastError();
 }
 
