@@ -201,9 +201,20 @@ def cpu_oracle_sample(w, seconds_hint=15.0):
                    graph=gi, nthreads=cores)
     el = time.perf_counter() - t0
     edge_updates = sum(g.nnz for g in w.graphs) * R_s * T_s
+    # the same oracle on one core: one replica, a tenth of the steps
+    T_1 = max(1, T_s // 10)
+    t0 = time.perf_counter()
+    for gi, g in enumerate(w.graphs):
+        oracle.run(g, w.q, K[gi, :T_1].astype(np.float64), Ks[gi, :T_1].astype(np.float64),
+                   Kn[gi, :T_1].astype(np.float64), float(np.float32(w.dt)), T_1, 1, 1,
+                   graph=gi, nthreads=1)
+    el_1 = time.perf_counter() - t0
+    one_core = sum(g.nnz for g in w.graphs) * T_1 / el_1
     return {"value": edge_updates / el, "unit": "edge-updates/s", "cores": cores, "kind": "oracle",
             "sample": f"all {len(w.graphs)} graphs, {R_s} replicas, first {T_s} of {w.steps} steps "
-                      f"(FP64 C oracle, OpenMP over replicas), {el:.1f} s"}
+                      f"(FP64 C oracle, OpenMP over replicas), {el:.1f} s",
+            "single_core": {"value": one_core, "unit": "edge-updates/s",
+                            "sample": f"all graphs, 1 replica, first {T_1} steps, {el_1:.1f} s"}}
 
 
 def run_reference(args):
@@ -359,6 +370,7 @@ def main():
     ms_step = reduce_max(ms_step, world, device="cuda")
     edge_updates = w.edge_updates() * world
     value = edge_updates / (ms_step / 1e3)
+    node_updates_per_s = w.nodes * w.replicas * w.steps * world / (ms_step / 1e3)
 
     # roofline of the dominant kernel.  CSR forms: algorithmic bytes per
     # node-replica-step are the state a step must move if nothing stays on chip:
@@ -464,6 +476,7 @@ def main():
         "roofline": roofline,
         "clocks": clocks,
         "e2e": e2e,
+        "node_updates_per_s": node_updates_per_s,
         "gpu_launches": args.steps * kernels_per_run(info["form"], w.steps, args.readout_every),
         "wall_s_timed_region": wall,
         "step_ms_all": ms,
