@@ -20,7 +20,7 @@ def _gpu():
     require_gpu()
 
 
-@pytest.mark.parametrize("n,p,R", [(800, 0.06, 64), (300, 0.2, 8), (1100, 0.03, 72)])
+@pytest.mark.parametrize("n,p,R", [(800, 0.06, 64), (300, 0.2, 8), (1100, 0.03, 72), (900, 0.05, 256)])
 def test_dense_coupling_within_1e2_per_row(orc, n, p, R):
     g = erdos_renyi(n, p, n, "pm1")
     dt, K = 1e-3, 1.0
@@ -70,9 +70,10 @@ def test_dense_readout_bitexact_and_short_run_parity(orc, R):
     assert np.median(rad_dist(run20.phases()[0], ref)) <= 1e-3
 
 
-def test_dense_graph_capture_matches_direct():
+@pytest.mark.parametrize("R", [64, 128])
+def test_dense_graph_capture_matches_direct(R):
     g = erdos_renyi(400, 0.1, 2, "+1")
-    T, R = 40, 64
+    T = 40
     args = (g, 2, constant(T, 0.3), linear_ramp(T, 0, 1), constant(T, 0.1), 0.01, T, R, 3)
     a = gpu_run(*args, form="gemm", precision="bf16", use_graph=True).phases()[0]
     b = gpu_run(*args, form="gemm", precision="bf16", use_graph=False).phases()[0]
