@@ -62,6 +62,31 @@ def test_batched_maxcut_full_run_scores_exact(orc):
         assert out["score"][gi].mean() > rnd.max() + 0.1 * g.num_edges
 
 
+def test_dense_workload_in_the_tensor_core_form(orc):
+    # the dense benchmark workload at full size in the form the autotuner picks for it
+    # (BF16 tensor cores): sampled replicas against the oracle over a short horizon (the
+    # BF16 coupling is within 1e-2 of the row norm, so a median bound), then the full
+    # 1000-step run with every replica's score recounted from its own spins
+    w = make_workload("dense2000")
+    g = w.graphs[0]
+    T = 10
+    run = run_workload(w, steps=T, form="gemm", precision="bf16", seed=4)
+    assert run.info()["form"] == 3
+    ph = run.phases()[0]
+    for r0 in (0, 640, 1020):
+        ref = oracle_phases(orc, g, 2, w.K[0], w.Ks[0], w.Kn[0], w.dt, T, 4, 4, replica_offset=r0,
+                            nthreads=8)
+        assert np.median(rad_dist(ph[r0:r0 + 4], ref)) <= 1e-3
+    run = run_workload(w, form="gemm", precision="bf16", readout_every=50, seed=6)
+    out = run.readout()
+    spins = orc.readout_f32(2, run.phases()[0])
+    assert np.array_equal(out["spins"][0], spins)
+    assert np.array_equal(out["score"][0], orc.scores(g, 2, spins))
+    assert np.array_equal(out["trace"][0, -1], out["score"][0])
+    rnd = orc.scores(g, 2, np.random.default_rng(9).integers(0, 2, (64, g.n)).astype(np.int8))
+    assert out["score"][0].mean() > rnd.max() + 0.01 * g.num_edges
+
+
 @pytest.mark.parametrize("precision", ["fp32", "fp16"])
 def test_planted_colouring_conflicts_exact(orc, precision):
     w = make_workload("planted600")
