@@ -556,17 +556,18 @@ def quality(w, prob, problems, args, stream, ms_step_chosen, chosen_cfg):
     G = len(w.graphs)
     hits = [[r[name]["steps_to_99pct"] for r in res["graphs"]] for name in ("chosen", "plain_fp32_csr")]
     per = [[r[name]["s_per_euler_step"] for r in res["graphs"]] for name in ("chosen", "plain_fp32_csr")]
-    if any(h is None for h in hits[0]):
-        t_chosen = float("inf")
-    else:
-        t_chosen = max(hits[0]) * per[0][0]
-    t_plain = float("inf")
+    # null when some graph never reaches its target within the schedule
+    t_chosen = None if any(h is None for h in hits[0]) else max(hits[0]) * per[0][0]
+    t_plain = None
     if not any(h is None for h in hits[1]):
         full = sum(w.steps * per[1][g] for g in range(G))
         for last in range(G):   # the graph run last stops at its hit; the others run fully
             t = full - w.steps * per[1][last] + hits[1][last] * per[1][last]
-            t_plain = min(t_plain, t)
+            t_plain = t if t_plain is None else min(t_plain, t)
     res["time_to_99pct_best_cut_s"] = {"chosen": t_chosen, "plain_fp32_csr": t_plain}
+    res["graphs_reaching_99pct"] = {"chosen": sum(h is not None for h in hits[0]),
+                                    "plain_fp32_csr": sum(h is not None for h in hits[1]),
+                                    "of": G}
     return res
 
 
