@@ -53,7 +53,8 @@ extern "C" {
 
 /* ---- integration forms ---------------------------------------------------- */
 #define OIM_FORM_AUTO      0  /* chosen per graph by the autotuner               */
-#define OIM_FORM_STREAM    1  /* plain FP32 CSR: one launch per step, state in HBM */
+#define OIM_FORM_STREAM    1  /* CSR, one launch per step, state in HBM: FP32     */
+                              /* cache (the plain form, AUTO) or FP16 / BF16      */
 #define OIM_FORM_RESIDENT  2  /* one launch for all steps; each block keeps whole  */
                               /* replicas of one graph in shared memory           */
 #define OIM_FORM_GEMM      3  /* dense coupling on the tensor cores (BF16 W x     */
@@ -208,8 +209,9 @@ int oim_debug_derivative(oim_problem_t p, const float* theta, int32_t replicas, 
 /*
  * oim_autotune -- pick the launch configuration of p for `replicas` replicas by
  * measurement: candidate forms (resident with a 16-bit or FP32 (cos, sin) cache,
- * several replicas-per-block and thread counts; the FP32 stream form; the dense
- * tensor-core form for a single graph) each run `probe_steps` steps twice on a
+ * several replicas-per-block and thread counts; the stream form with an FP32 or
+ * FP16 cache; the dense tensor-core form for a single graph) each run
+ * `probe_steps` steps twice on a
  * private stream, and the fastest is returned in *best (stream set to `stream`)
  * with its time per step in *best_us_per_step (may be NULL).  The paper leaves the
  * per-GPU batch size to the user (Sec. III-C); this chooses it, and the form,

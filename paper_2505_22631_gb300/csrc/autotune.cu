@@ -106,6 +106,7 @@ extern "C" int oim_autotune(oim_problem_t p, int32_t replicas, int32_t precision
         }
     }
     add(OIM_FORM_STREAM, OIM_PREC_FP32, 0, 0);
+    if (precision_policy == OIM_PREC_AUTO) add(OIM_FORM_STREAM, OIM_PREC_FP16, 0, 0);
     if (precision_policy == OIM_PREC_AUTO && G == 1) add(OIM_FORM_GEMM, OIM_PREC_BF16, 0, 0);
 
     cudaStream_t s = nullptr;

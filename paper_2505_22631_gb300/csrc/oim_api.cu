@@ -240,7 +240,7 @@ int choose_form(oim_run_s* r) {
     }
     // AUTO precision: the resident form keeps its (cos, sin) cache in FP16 (twice
     // the replicas per block of FP32, coupling error ~1e-4 relative); the stream
-    // form is FP32 only.
+    // form defaults to FP32 (the plain form) and takes FP16 / BF16 when asked.
     if (prec == OIM_PREC_AUTO) prec = (form == OIM_FORM_STREAM) ? OIM_PREC_FP32 : OIM_PREC_FP16;
     if (form == OIM_FORM_AUTO) {
         ResidentPlan tmp;
@@ -250,8 +250,6 @@ int choose_form(oim_run_s* r) {
                    : OIM_FORM_STREAM;
         if (form == OIM_FORM_STREAM && r->opts.precision == OIM_PREC_AUTO) prec = OIM_PREC_FP32;
     }
-    if (form == OIM_FORM_STREAM && prec != OIM_PREC_FP32)
-        return fail(OIM_EUNSUPPORTED, "the stream form stores its cache in FP32 only");
     r->form = form;
     r->prec = prec;
     if (form == OIM_FORM_RESIDENT) {
@@ -276,8 +274,10 @@ int allocate_run(oim_run_s* r) {
     OIM_CUDA(dev_alloc(&r->d_t0, 1), "cudaMalloc(t0)");
     if (r->form == OIM_FORM_STREAM) {
         OIM_CUDA(dev_alloc(&r->d_theta[1], state), "cudaMalloc(theta)");
-        OIM_CUDA(cudaMalloc(&r->d_cs[0], state * sizeof(float2)), "cudaMalloc(cs)");
-        OIM_CUDA(cudaMalloc(&r->d_cs[1], state * sizeof(float2)), "cudaMalloc(cs)");
+        // (cos, sin) pairs: float2, or two 16-bit values in the FP16 / BF16 variant
+        const size_t pair = r->prec == OIM_PREC_FP32 ? sizeof(float2) : sizeof(uint32_t);
+        OIM_CUDA(cudaMalloc(&r->d_cs[0], state * pair), "cudaMalloc(cs)");
+        OIM_CUDA(cudaMalloc(&r->d_cs[1], state * pair), "cudaMalloc(cs)");
     }
     if (r->form == OIM_FORM_GEMM) {
         int rc = gemm_setup(*r);

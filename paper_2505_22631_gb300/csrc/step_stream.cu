@@ -1,5 +1,9 @@
-// step_stream.cu -- the plain FP32 CSR form: one launch per Euler-Maruyama step,
-// all state in device memory.
+// step_stream.cu -- the CSR stream form: one launch per Euler-Maruyama step, all
+// state in device memory.  The plain form keeps the (cos, sin) cache in FP32 and
+// uses correctly rounded math; the 16-bit variant stores the cache as FP16 or BF16
+// pairs (half the cache bytes per step), recomputes each node's own (cos, sin) in
+// FP32 from its phase, and uses the hardware approximations for the trigonometry
+// and Box-Muller (errors ~1e-6, far below the 16-bit storage's 2^-11 / 2^-8).
 //
 // Layout: theta[node][R_pad] (FP32) and cs[node][R_pad] = (cos 2 pi theta,
 // sin 2 pi theta) as float2, replicas contiguous.  One thread owns one node and
@@ -13,6 +17,9 @@
 //   D_i      = sin(2 pi theta_i) A - cos(2 pi theta_i) B = sum_j w_ij sin 2 pi (theta_i - theta_j)
 //   theta_i' = wrap(theta_i + dt (K D_i - Ks sin 2 pi q theta_i) + Kn sqrt(dt) xi)
 //   cs_i'    = (cos 2 pi theta_i', sin 2 pi theta_i')
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "oim_device.cuh"
 #include "oim_internal.h"
 
@@ -20,31 +27,92 @@ namespace oim {
 
 namespace {
 
+// Storage of the (cos, sin) cache: four replicas' pairs per thread.
+struct CacheF32 {
+    using T = float2;
+    static constexpr bool kOwnFromCache = true;   // the plain form reads its own pairs back
+    static constexpr bool kFastMath = false;      // correctly rounded sincospi, logf, sqrtf
+    __device__ static void load4(const T* p, float2 (&v)[4]) {
+        const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+        const float4 b = __ldg(reinterpret_cast<const float4*>(p) + 1);
+        v[0] = make_float2(a.x, a.y);
+        v[1] = make_float2(a.z, a.w);
+        v[2] = make_float2(b.x, b.y);
+        v[3] = make_float2(b.z, b.w);
+    }
+    __device__ static void store4(T* p, const float2 (&v)[4]) {
+        reinterpret_cast<float4*>(p)[0] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+        reinterpret_cast<float4*>(p)[1] = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
+    }
+};
+
+template <typename H2>
+struct Cache16 {
+    using T = H2;
+    static constexpr bool kOwnFromCache = false;  // own pairs recomputed in FP32
+    // hardware sin / cos / log2 / sqrt (errors ~1e-6, far below the 16-bit storage's)
+    static constexpr bool kFastMath = true;
+    __device__ static float2 to_f2(H2 h);
+    __device__ static H2 from_f2(float2 f);
+    __device__ static void load4(const T* p, float2 (&v)[4]) {
+        const uint4 a = __ldg(reinterpret_cast<const uint4*>(p));
+        const uint32_t w[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] = to_f2(*reinterpret_cast<const H2*>(&w[k]));
+    }
+    __device__ static void store4(T* p, const float2 (&v)[4]) {
+        uint32_t w[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const H2 h = from_f2(v[k]);
+            w[k] = *reinterpret_cast<const uint32_t*>(&h);
+        }
+        *reinterpret_cast<uint4*>(p) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+};
+template <>
+__device__ float2 Cache16<__half2>::to_f2(__half2 h) { return __half22float2(h); }
+template <>
+__device__ __half2 Cache16<__half2>::from_f2(float2 f) { return __floats2half2_rn(f.x, f.y); }
+template <>
+__device__ float2 Cache16<__nv_bfloat162>::to_f2(__nv_bfloat162 h) { return __bfloat1622float2(h); }
+template <>
+__device__ __nv_bfloat162 Cache16<__nv_bfloat162>::from_f2(float2 f) { return __floats2bfloat162_rn(f.x, f.y); }
+
+// Thread = node x quad of replicas: initial phases and their (cos, sin).
+template <typename C>
 __global__ void __launch_bounds__(256) init_stream_kernel(CSRDev csr, StepParams P,
                                                           float* __restrict__ theta,
-                                                          float2* __restrict__ cs) {
-    const int pairs = P.R_pad >> 1;
+                                                          typename C::T* __restrict__ cs) {
+    const int quads = P.R_pad >> 2;
     const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (gid >= (int64_t)csr.nodes * pairs) return;
-    const int node = (int)(gid / pairs);
-    const int r = 2 * (int)(gid - (int64_t)node * pairs);
+    if (gid >= (int64_t)csr.nodes * quads) return;
+    const int node = (int)(gid / quads);
+    const int r = 4 * (int)(gid - (int64_t)node * quads);
     const int g = csr.node_graph[node];
     const int i = node - csr.graphs[g].node_off;
-    const float2 th = init_pair(P.seed, (uint32_t)g, (uint32_t)i, (uint32_t)r);
+    const float2 t01 = init_pair(P.seed, (uint32_t)g, (uint32_t)i, (uint32_t)r);
+    const float2 t23 = init_pair(P.seed, (uint32_t)g, (uint32_t)i, (uint32_t)(r + 2));
     const size_t at = (size_t)node * P.R_pad + r;
-    *reinterpret_cast<float2*>(theta + at) = th;
-    float s0, c0, s1, c1;
-    sincospif(2.0f * th.x, &s0, &c0);
-    sincospif(2.0f * th.y, &s1, &c1);
-    *reinterpret_cast<float4*>(cs + at) = make_float4(c0, s0, c1, s1);
+    *reinterpret_cast<float4*>(theta + at) = make_float4(t01.x, t01.y, t23.x, t23.y);
+    const float th[4] = {t01.x, t01.y, t23.x, t23.y};
+    float2 v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (C::kFastMath)
+            v[k] = cos_sin_2pi_fast(th[k]);
+        else
+            sincospif(2.0f * th[k], &v[k].y, &v[k].x);
+    }
+    C::store4(cs + at, v);
 }
 
-template <bool kUnit>
+template <bool kUnit, typename C>
 __global__ void __launch_bounds__(256) step_stream_kernel(CSRDev csr, StepParams P,
                                                           const float* __restrict__ th_in,
-                                                          const float2* __restrict__ cs_in,
+                                                          const typename C::T* __restrict__ cs_in,
                                                           float* __restrict__ th_out,
-                                                          float2* __restrict__ cs_out,
+                                                          typename C::T* __restrict__ cs_out,
                                                           int64_t t_fixed,
                                                           const int32_t* __restrict__ d_t0,
                                                           int32_t t_add) {
@@ -61,10 +129,18 @@ __global__ void __launch_bounds__(256) step_stream_kernel(CSRDev csr, StepParams
 
     const size_t at = (size_t)node * P.R_pad + 4 * quad;
     const float4 th = *reinterpret_cast<const float4*>(th_in + at);
-    const float4 o01 = *reinterpret_cast<const float4*>(cs_in + at);
-    const float4 o23 = *reinterpret_cast<const float4*>(cs_in + at + 2);
+    const float t0[4] = {th.x, th.y, th.z, th.w};
+    float2 own[4];
+    if (C::kOwnFromCache) {
+        C::load4(cs_in + at, own);
+    } else {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) own[v] = cos_sin_2pi_fast(t0[v]);
+    }
 
-    float2 a0 = make_float2(0.f, 0.f), a1 = a0, a2 = a0, a3 = a0;
+    float2 acc[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[v] = make_float2(0.f, 0.f);
     const int e_end = __ldg(csr.rowp + node + 1);
     for (int e = __ldg(csr.rowp + node); e < e_end; ++e) {
         const uint32_t cw = __ldg(csr.col + e);
@@ -77,41 +153,34 @@ __global__ void __launch_bounds__(256) step_stream_kernel(CSRDev csr, StepParams
             j = cw;
             w = __ldg(csr.w + e);
         }
-        const float4* nb = reinterpret_cast<const float4*>(cs_in + (size_t)j * P.R_pad + 4 * quad);
-        const float4 v01 = __ldg(nb);
-        const float4 v23 = __ldg(nb + 1);
+        float2 nb[4];
+        C::load4(cs_in + (size_t)j * P.R_pad + 4 * quad, nb);
         const float2 ww = make_float2(w, w);
-        a0 = ffma2(make_float2(v01.x, v01.y), ww, a0);
-        a1 = ffma2(make_float2(v01.z, v01.w), ww, a1);
-        a2 = ffma2(make_float2(v23.x, v23.y), ww, a2);
-        a3 = ffma2(make_float2(v23.z, v23.w), ww, a3);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[v] = ffma2(nb[v], ww, acc[v]);
     }
 
     const uint4 x = draw_block(P.seed, (uint32_t)g, kStreamNoise, (uint32_t)i, (uint32_t)t,
                                (uint32_t)quad);
-    const float2 z01 = box_muller(x.x, x.y);
-    const float2 z23 = box_muller(x.z, x.w);
+    const float2 z01 = C::kFastMath ? box_muller_fast(x.x, x.y) : box_muller(x.x, x.y);
+    const float2 z23 = C::kFastMath ? box_muller_fast(x.z, x.w) : box_muller(x.z, x.w);
+    const float z[4] = {z01.x, z01.y, z23.x, z23.y};
     const float kick = Kn * P.sqrt_dt;
     const float dtK = P.dt * K, dtKs = P.dt * Ks;
-
-    auto update = [&](float th0, float c, float s, float2 a, float z) {
-        const float coup = s * a.x - c * a.y;
-        const float shil = sin_q(P.q, c, s);
-        return wrap01(th0 + (dtK * coup - dtKs * shil) + kick * z);
-    };
-    float4 tn;
-    tn.x = update(th.x, o01.x, o01.y, a0, z01.x);
-    tn.y = update(th.y, o01.z, o01.w, a1, z01.y);
-    tn.z = update(th.z, o23.x, o23.y, a2, z23.x);
-    tn.w = update(th.w, o23.z, o23.w, a3, z23.y);
-    *reinterpret_cast<float4*>(th_out + at) = tn;
-    float4 n01, n23;
-    sincospif(2.0f * tn.x, &n01.y, &n01.x);
-    sincospif(2.0f * tn.y, &n01.w, &n01.z);
-    sincospif(2.0f * tn.z, &n23.y, &n23.x);
-    sincospif(2.0f * tn.w, &n23.w, &n23.z);
-    *reinterpret_cast<float4*>(cs_out + at) = n01;
-    *reinterpret_cast<float4*>(cs_out + at + 2) = n23;
+    float tn[4];
+    float2 ncs[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        const float coup = own[v].y * acc[v].x - own[v].x * acc[v].y;
+        const float shil = sin_q(P.q, own[v].x, own[v].y);
+        tn[v] = wrap01(t0[v] + (dtK * coup - dtKs * shil) + kick * z[v]);
+        if (C::kFastMath)
+            ncs[v] = cos_sin_2pi_fast(tn[v]);
+        else
+            sincospif(2.0f * tn[v], &ncs[v].y, &ncs[v].x);
+    }
+    *reinterpret_cast<float4*>(th_out + at) = make_float4(tn[0], tn[1], tn[2], tn[3]);
+    C::store4(cs_out + at, ncs);
 }
 
 // f = K sum_j w_ij (s_i c_j - c_i s_j) - Ks sin(2 pi q theta_i) for theta[r][n] of
@@ -164,14 +233,21 @@ static StepParams params_of(const oim_run_s& r) {
 
 StepParams make_params(const oim_run_s& r) { return params_of(r); }
 
-cudaError_t launch_init_stream(const oim_run_s& r, cudaStream_t s) {
+template <typename C>
+static cudaError_t init_stream_as(const oim_run_s& r, cudaStream_t s) {
     const StepParams P = params_of(r);
-    const int64_t total = r.p->nodes * (r.R_pad / 2);
+    const int64_t total = r.p->nodes * (r.R_pad / 4);
     const int threads = 256;
     const int64_t blocks = (total + threads - 1) / threads;
-    init_stream_kernel<<<(unsigned)blocks, threads, 0, s>>>(
-        r.p->csr(), P, r.d_theta[0], reinterpret_cast<float2*>(r.d_cs[0]));
+    init_stream_kernel<C><<<(unsigned)blocks, threads, 0, s>>>(
+        r.p->csr(), P, r.d_theta[0], reinterpret_cast<typename C::T*>(r.d_cs[0]));
     return cudaGetLastError();
+}
+
+cudaError_t launch_init_stream(const oim_run_s& r, cudaStream_t s) {
+    if (r.prec == OIM_PREC_FP16) return init_stream_as<Cache16<__half2>>(r, s);
+    if (r.prec == OIM_PREC_BF16) return init_stream_as<Cache16<__nv_bfloat162>>(r, s);
+    return init_stream_as<CacheF32>(r, s);
 }
 
 // (cos, sin) of every phase, for restarting the stream form from stored phases.
@@ -190,7 +266,7 @@ cudaError_t launch_cs_from_theta(const oim_run_s& r, const float* theta, float2*
     return cudaGetLastError();
 }
 
-// One step t of the stream form between explicit buffers.
+// One step t of the stream form between explicit buffers (FP32 cache: the adjoint).
 cudaError_t launch_step_stream_buffers(const oim_run_s& r, int64_t t, const float* th_in,
                                        const float2* cs_in, float* th_out, float2* cs_out,
                                        cudaStream_t s) {
@@ -199,15 +275,16 @@ cudaError_t launch_step_stream_buffers(const oim_run_s& r, int64_t t, const floa
     const int threads = 256;
     const int64_t blocks = (total + threads - 1) / threads;
     if (r.p->unit_weights)
-        step_stream_kernel<true><<<(unsigned)blocks, threads, 0, s>>>(
+        step_stream_kernel<true, CacheF32><<<(unsigned)blocks, threads, 0, s>>>(
             r.p->csr(), P, th_in, cs_in, th_out, cs_out, t, nullptr, 0);
     else
-        step_stream_kernel<false><<<(unsigned)blocks, threads, 0, s>>>(
+        step_stream_kernel<false, CacheF32><<<(unsigned)blocks, threads, 0, s>>>(
             r.p->csr(), P, th_in, cs_in, th_out, cs_out, t, nullptr, 0);
     return cudaGetLastError();
 }
 
-cudaError_t launch_step_stream(const oim_run_s& r, int64_t t, const int32_t* d_t0, cudaStream_t s) {
+template <typename C>
+static cudaError_t step_stream_as(const oim_run_s& r, int64_t t, const int32_t* d_t0, cudaStream_t s) {
     // with d_t0 the step is *d_t0 + t (graph replay); otherwise t itself.
     const StepParams P = params_of(r);
     const int64_t total = r.p->nodes * (r.R_pad / 4);
@@ -215,17 +292,24 @@ cudaError_t launch_step_stream(const oim_run_s& r, int64_t t, const int32_t* d_t
     const int64_t blocks = (total + threads - 1) / threads;
     const int in = (int)(t & 1);   // buffer parity follows the step index
     const int out = in ^ 1;
+    using T = typename C::T;
     const float* th_in = r.d_theta[in];
-    const float2* cs_in = reinterpret_cast<const float2*>(r.d_cs[in]);
+    const T* cs_in = reinterpret_cast<const T*>(r.d_cs[in]);
     float* th_out = r.d_theta[out];
-    float2* cs_out = reinterpret_cast<float2*>(r.d_cs[out]);
+    T* cs_out = reinterpret_cast<T*>(r.d_cs[out]);
     if (r.p->unit_weights)
-        step_stream_kernel<true><<<(unsigned)blocks, threads, 0, s>>>(
+        step_stream_kernel<true, C><<<(unsigned)blocks, threads, 0, s>>>(
             r.p->csr(), P, th_in, cs_in, th_out, cs_out, t, d_t0, (int32_t)t);
     else
-        step_stream_kernel<false><<<(unsigned)blocks, threads, 0, s>>>(
+        step_stream_kernel<false, C><<<(unsigned)blocks, threads, 0, s>>>(
             r.p->csr(), P, th_in, cs_in, th_out, cs_out, t, d_t0, (int32_t)t);
     return cudaGetLastError();
+}
+
+cudaError_t launch_step_stream(const oim_run_s& r, int64_t t, const int32_t* d_t0, cudaStream_t s) {
+    if (r.prec == OIM_PREC_FP16) return step_stream_as<Cache16<__half2>>(r, t, d_t0, s);
+    if (r.prec == OIM_PREC_BF16) return step_stream_as<Cache16<__nv_bfloat162>>(r, t, d_t0, s);
+    return step_stream_as<CacheF32>(r, t, d_t0, s);
 }
 
 }  // namespace oim

@@ -69,6 +69,34 @@ def test_fast_noise_draws_of_16bit_forms(orc, precision):
     assert err.max() <= 2e-5
 
 
+@pytest.mark.parametrize("precision", ["fp16", "bf16"])
+def test_stream_16bit_cache_start_noise_readout(orc, c1, precision):
+    # the 16-bit stream form: FP32 phases, the stored neighbour (cos, sin) pairs rounded
+    # to 16 bits, hardware Box-Muller (the 16-bit forms' noise bound)
+    g = c1.graphs[0]
+    R = 8
+    run = gpu_run(g, 2, 0.0, 0.0, 0.0, 0.01, 0, R, seed=77, form="stream", precision=precision)
+    assert np.array_equal(run.phases()[0], orc.init_phases(g.n, R, 77).astype(np.float32))
+    n, kick = 1000, 0.05
+    e = csr_from_edges(n, np.zeros(0, int), np.zeros(0, int))
+    run = gpu_run(e, 2, 0.0, 0.0, kick, 1.0, 1, 12, seed=5, form="stream", precision=precision)
+    xi = circ(run.phases()[0].astype(np.float64) - orc.init_phases(n, 12, 5)) / kick
+    assert np.max(np.abs(xi - orc.noise_block(n, 12, 5, 0))) <= 2e-5
+    T = 100
+    run = gpu_run(g, 2, c1.K[0][:T], c1.Ks[0][:T], c1.Kn[0][:T], c1.dt, T, R, 5, form="stream",
+                  precision=precision, readout_every=25)
+    th = run.phases()[0]
+    out = run.readout()
+    spins = orc.readout_f32(2, th)
+    assert np.array_equal(out["spins"][0], spins)
+    assert np.array_equal(out["score"][0], orc.scores(g, 2, spins))
+    assert np.array_equal(out["trace"][0, -1], out["score"][0])
+    ref = oracle_phases(orc, g, 2, c1.K[0][:20], c1.Ks[0][:20], c1.Kn[0][:20], c1.dt, 20, R, 5)
+    th20 = gpu_run(g, 2, c1.K[0][:20], c1.Ks[0][:20], c1.Kn[0][:20], c1.dt, 20, R, 5, form="stream",
+                   precision=precision).phases()[0]
+    assert np.median(rad_dist(th20, ref)) <= 1e-3
+
+
 def test_drift_matches_fp64(orc, c1):
     from paper_2505_22631_gb300 import Problem, oim_debug_derivative
     g = c1.graphs[0]
@@ -226,11 +254,13 @@ def test_potts_orders(orc, form, q):
     assert np.array_equal(run.readout()["score"][0], orc.scores(g, q, orc.readout_f32(q, th)))
 
 
+@pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("precision", ["fp16", "bf16"])
-def test_half_cache_coupling_within_1e2_per_row(orc, c1, precision):
+def test_half_cache_coupling_within_1e2_per_row(orc, c1, form, precision):
     g = c1.graphs[0]
     R, dt, K = 16, 1e-3, 1.0
-    run = gpu_run(g, 2, K, 0.0, 0.0, dt, 1, R, 13, form="resident", precision=precision)
+    run = gpu_run(g, 2, K, 0.0, 0.0, dt, 1, R, 13, form=form, precision=precision)
+    assert run.info()["precision"] == {"fp16": 3, "bf16": 2}[precision]
     th0 = orc.init_phases(g.n, R, 13)
     D = circ(run.phases()[0].astype(np.float64) - th0) / (np.float32(dt) * K)
     A = np.zeros((R, g.n))
@@ -272,8 +302,12 @@ def test_invalid_form_requests():
     with pytest.raises(OimError) as ei:
         gpu_run(g, 2, 1.0, 1.0, 0.1, 0.01, 2, 4, 1, form="resident")
     assert ei.value.code == -5
-    with pytest.raises(OimError):
-        gpu_run(torus(4, 4, 1), 2, 1.0, 1.0, 0.1, 0.01, 2, 4, 1, form="stream", precision="bf16")
+    with pytest.raises(OimError) as ei:
+        gpu_run(torus(4, 4, 1), 2, 1.0, 1.0, 0.1, 0.01, 2, 64, 1, form="gemm", precision="fp16")
+    assert ei.value.code == -5
+    with pytest.raises(OimError) as ei:
+        gpu_run([torus(4, 4, 1), torus(4, 4, 2)], 2, 1.0, 1.0, 0.1, 0.01, 2, 64, 1, form="gemm")
+    assert ei.value.code == -5
 
 
 def test_autotune_picks_a_valid_cached_configuration(c1):
