@@ -301,6 +301,9 @@ def main():
     ap.add_argument("--no-quality", action="store_true")
     ap.add_argument("--euler-steps", type=int, default=0, help="override the workload's steps")
     ap.add_argument("--replicas", type=int, default=0, help="override the workload's replicas")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="time the checkpointed forward run plus oim_backward (schedule gradients)")
+    ap.add_argument("--checkpoint-every", type=int, default=100)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -319,6 +322,10 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     build.build()
     capi.load()
+
+    if args.adjoint:
+        run_adjoint(args, rank, world)
+        return
 
     w = make_workload(args.workload, steps=args.euler_steps or None,
                       replicas=args.replicas or None)
@@ -500,6 +507,66 @@ def main():
     run.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def run_adjoint(args, rank, world):
+    """Schedule-gradient pass: FP32 stream forward with a checkpoint every C steps,
+    then oim_backward (recompute each segment, reverse sweep).  Reported as edge-updates
+    of the forward trajectory per second of forward + backward."""
+    import torch
+    from paper_2505_22631_gb300 import Problem, build, capi  # noqa: F401
+    name = args.workload if args.workload != "torus_er2000" else "er64"
+    w = make_workload(name, steps=args.euler_steps or None, replicas=args.replicas or None)
+    K, Ks, Kn = schedules(w)
+    problems = [Problem.from_graph(g, w.q) for g in w.graphs]
+    prob = Problem.batch(problems) if len(problems) > 1 else problems[0]
+    stream = torch.cuda.current_stream()
+    G, T = len(w.graphs), w.steps
+    dK, dKs, dKn = (np.zeros((G, T)) for _ in range(3))
+    loss = np.zeros(G)
+
+    def step(seed):
+        o = capi.oim_default_opts()
+        o.form = capi.OIM_FORM_STREAM
+        o.precision = capi.OIM_PREC_FP32
+        o.checkpoint_every = args.checkpoint_every
+        o.use_graph = 1
+        o.stream = int(stream.cuda_stream)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        r = capi.oim_run(prob.handle, K, Ks, Kn, w.dt, T, w.replicas, seed, o)
+        e1.record(stream)
+        capi.oim_backward(r, dK, dKs, dKn, loss)   # synchronous
+        e2.record(stream)
+        torch.cuda.synchronize()
+        capi.oim_destroy_run(r)
+        return e0.elapsed_time(e1), e1.elapsed_time(e2)
+
+    for k in range(args.warmup):
+        step(seed=11 + k)
+    fw, bw = [], []
+    for k in range(args.steps):
+        a, b = step(seed=101 + k)
+        fw.append(a)
+        bw.append(b)
+    ms = float(np.mean(fw) + np.mean(bw))
+    ms = reduce_max(ms, world, device="cuda")
+    edge_updates = w.edge_updates() * world
+    line = {"metric": "edge-updates/s (forward + schedule adjoint)", "value": edge_updates / (ms / 1e3),
+            "unit": "edge-updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "ms_forward": float(np.mean(fw)), "ms_backward": float(np.mean(bw)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (f64 gradient sums)",
+            "data": "synthetic",
+            "config": {"workload": w.name, "graphs": len(w.graphs), "nodes": w.nodes, "replicas": w.replicas,
+                       "euler_steps": T, "checkpoint_every": args.checkpoint_every,
+                       "form": "stream", "precision": "fp32",
+                       "timing": "CUDA events around the forward launch sequence and around oim_backward "
+                                 "(which includes its scratch allocation and the gradient copies)"},
+            "mean_loss": float(loss.mean()),
+            "gradient_norms": {"dK": float(np.linalg.norm(dK)), "dKs": float(np.linalg.norm(dKs)),
+                               "dKn": float(np.linalg.norm(dKn))}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
 
 
 def quality(w, prob, problems, args, stream, ms_step_chosen, chosen_cfg):
