@@ -15,6 +15,8 @@
 //   dL/dK_t = dt sum lambda_{t+1} D(theta_t),  dL/dKs_t = -dt sum lambda_{t+1} sin 2 pi q theta_t,
 //   dL/dKn_t = sqrt(dt) sum lambda_{t+1} xi_t  (pathwise: the same Philox draws as the forward).
 // Layout as the stream form: [node][R_pad], replicas contiguous, a thread per (node, quad).
+// Y holds four planes c, s, lambda c, lambda s of [node][R_pad] floats each, so a
+// neighbour gather is four 16-byte loads that a warp turns into whole 512-byte rows.
 #include "oim_device.cuh"
 #include "oim_internal.h"
 
@@ -24,21 +26,24 @@ namespace {
 
 constexpr float kTwoPi = 6.28318530717958647f;
 
-// (c, s, lambda c, lambda s) of every node-replica at theta_t.
-__global__ void __launch_bounds__(256) adj_prep_kernel(int nodes, int R_pad, const float* __restrict__ theta,
-                                                       const float* __restrict__ lam, float4* __restrict__ Y) {
+// (c, s, lambda c, lambda s) of every node-replica at theta_t, as four planes.
+__global__ void __launch_bounds__(256) adj_prep_kernel(int64_t state, const float* __restrict__ theta,
+                                                       const float* __restrict__ lam, float* __restrict__ Y) {
     const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (gid >= (int64_t)nodes * R_pad) return;
+    if (gid >= state) return;
     float s, c;
     sincospif(2.0f * theta[gid], &s, &c);
     const float l = lam[gid];
-    Y[gid] = make_float4(c, s, l * c, l * s);
+    Y[gid] = c;
+    Y[state + gid] = s;
+    Y[2 * state + gid] = l * c;
+    Y[3 * state + gid] = l * s;
 }
 
 // D(theta) * scale into lam (the terminal adjoint, scale = -2 pi / R), and the
 // per-graph FP64 sum of E = 1/2 sum_i (c_i A_i + s_i B_i) over the real replicas.
 __global__ void __launch_bounds__(256) adj_terminal_kernel(CSRDev csr, int R, int R_pad, float scale,
-                                                           const float4* __restrict__ Y,
+                                                           const float* __restrict__ Y,
                                                            float* __restrict__ lam,
                                                            double* __restrict__ loss) {
     const int quads = R_pad >> 2;
@@ -50,23 +55,29 @@ __global__ void __launch_bounds__(256) adj_terminal_kernel(CSRDev csr, int R, in
         const int quad = (int)(gid - (int64_t)node * quads);
         g = csr.node_graph[node];
         const size_t at = (size_t)node * R_pad + 4 * quad;
+        const size_t state = (size_t)csr.nodes * R_pad;
+        const float* Yc = Y;
+        const float* Ys = Y + state;
         float A[4] = {0, 0, 0, 0}, B[4] = {0, 0, 0, 0};
         for (int ei = csr.rowp[node]; ei < csr.rowp[node + 1]; ++ei) {
             const uint32_t cw = csr.col[ei];
             const uint32_t j = csr.w ? cw : (cw & ~kSignBit);
             const float w = csr.w ? csr.w[ei] : ((cw & kSignBit) ? -1.0f : 1.0f);
+            const size_t jat = (size_t)j * R_pad + 4 * quad;
+            const float4 c4 = *reinterpret_cast<const float4*>(Yc + jat);
+            const float4 s4 = *reinterpret_cast<const float4*>(Ys + jat);
+            const float cj[4] = {c4.x, c4.y, c4.z, c4.w}, sj[4] = {s4.x, s4.y, s4.z, s4.w};
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
-                const float4 y = Y[(size_t)j * R_pad + 4 * quad + v];
-                A[v] = fmaf(w, y.x, A[v]);
-                B[v] = fmaf(w, y.y, B[v]);
+                A[v] = fmaf(w, cj[v], A[v]);
+                B[v] = fmaf(w, sj[v], B[v]);
             }
         }
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-            const float4 y = Y[at + v];
-            lam[at + v] = scale * (y.y * A[v] - y.x * B[v]);
-            if (4 * quad + v < R) e += 0.5 * (double)(y.x * A[v] + y.y * B[v]);
+            const float c = Yc[at + v], sn = Ys[at + v];
+            lam[at + v] = scale * (sn * A[v] - c * B[v]);
+            if (4 * quad + v < R) e += 0.5 * (double)(c * A[v] + sn * B[v]);
         }
     }
     // block reduce per graph: blocks may straddle graphs, so reduce by atomics per thread group
@@ -77,7 +88,7 @@ __global__ void __launch_bounds__(256) adj_terminal_kernel(CSRDev csr, int R, in
 // and the step's gradient terms added to dK[g][t], dKs[g][t], dKn[g][t].
 __global__ void __launch_bounds__(256) adj_step_kernel(CSRDev csr, StepParams P, int64_t t,
                                                        const float* __restrict__ theta,
-                                                       const float4* __restrict__ Y,
+                                                       const float* __restrict__ Y,
                                                        const float* __restrict__ lam_in,
                                                        float* __restrict__ lam_out,
                                                        double* __restrict__ dK, double* __restrict__ dKs,
@@ -95,18 +106,29 @@ __global__ void __launch_bounds__(256) adj_step_kernel(CSRDev csr, StepParams P,
         const size_t sidx = (size_t)g * P.steps + t;
         const float K = P.K[sidx], Ks = P.Ks[sidx];
         const size_t at = (size_t)node * P.R_pad + 4 * quad;
+        const size_t state = (size_t)csr.nodes * P.R_pad;
+        const float* Yc = Y;
+        const float* Ys = Y + state;
+        const float* Ylc = Y + 2 * state;
+        const float* Yls = Y + 3 * state;
         float A[4] = {0, 0, 0, 0}, B[4] = {0, 0, 0, 0}, Pp[4] = {0, 0, 0, 0}, Q[4] = {0, 0, 0, 0};
         for (int ei = csr.rowp[node]; ei < csr.rowp[node + 1]; ++ei) {
             const uint32_t cw = csr.col[ei];
             const uint32_t j = csr.w ? cw : (cw & ~kSignBit);
             const float w = csr.w ? csr.w[ei] : ((cw & kSignBit) ? -1.0f : 1.0f);
+            const size_t jat = (size_t)j * P.R_pad + 4 * quad;
+            const float4 c4 = *reinterpret_cast<const float4*>(Yc + jat);
+            const float4 s4 = *reinterpret_cast<const float4*>(Ys + jat);
+            const float4 lc4 = *reinterpret_cast<const float4*>(Ylc + jat);
+            const float4 ls4 = *reinterpret_cast<const float4*>(Yls + jat);
+            const float cj[4] = {c4.x, c4.y, c4.z, c4.w}, sj[4] = {s4.x, s4.y, s4.z, s4.w};
+            const float lcj[4] = {lc4.x, lc4.y, lc4.z, lc4.w}, lsj[4] = {ls4.x, ls4.y, ls4.z, ls4.w};
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
-                const float4 y = Y[(size_t)j * P.R_pad + 4 * quad + v];
-                A[v] = fmaf(w, y.x, A[v]);
-                B[v] = fmaf(w, y.y, B[v]);
-                Pp[v] = fmaf(w, y.z, Pp[v]);
-                Q[v] = fmaf(w, y.w, Q[v]);
+                A[v] = fmaf(w, cj[v], A[v]);
+                B[v] = fmaf(w, sj[v], B[v]);
+                Pp[v] = fmaf(w, lcj[v], Pp[v]);
+                Q[v] = fmaf(w, lsj[v], Q[v]);
             }
         }
         const uint4 x = draw_block(P.seed, (uint32_t)g, kStreamNoise, (uint32_t)i, (uint32_t)t,
@@ -116,8 +138,7 @@ __global__ void __launch_bounds__(256) adj_step_kernel(CSRDev csr, StepParams P,
         const float z[4] = {z01.x, z01.y, z23.x, z23.y};
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-            const float4 y = Y[at + v];
-            const float c = y.x, s = y.y;
+            const float c = Yc[at + v], s = Ys[at + v];
             const float l = lam_in[at + v];
             const float S = c * A[v] + s * B[v];
             const float Cc = c * Pp[v] + s * Q[v];
@@ -156,11 +177,13 @@ __global__ void __launch_bounds__(256) adj_step_kernel(CSRDev csr, StepParams P,
 
 StepParams make_params(const oim_run_s& r);
 
-// Y from (theta, lambda).
+// Y (four planes of [node][R_pad] floats, in a buffer of node-replica float4s) from
+// (theta, lambda).
 cudaError_t launch_adj_prep(const oim_run_s& r, const float* theta, const float* lam, float4* Y,
                             cudaStream_t s) {
     const int64_t total = r.p->nodes * r.R_pad;
-    adj_prep_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>((int)r.p->nodes, r.R_pad, theta, lam, Y);
+    adj_prep_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(total, theta, lam,
+                                                                   reinterpret_cast<float*>(Y));
     return cudaGetLastError();
 }
 
@@ -169,8 +192,8 @@ cudaError_t launch_adj_terminal(const oim_run_s& r, const float4* Y, float* lam,
                                 cudaStream_t s) {
     const int64_t total = r.p->nodes * (r.R_pad / 4);
     const float scale = -6.28318530717958647f / (float)r.R;
-    adj_terminal_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(r.p->csr(), r.R, r.R_pad, scale, Y,
-                                                                       lam, loss);
+    adj_terminal_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
+        r.p->csr(), r.R, r.R_pad, scale, reinterpret_cast<const float*>(Y), lam, loss);
     return cudaGetLastError();
 }
 
@@ -179,8 +202,8 @@ cudaError_t launch_adj_step(const oim_run_s& r, int64_t t, const float* theta, c
                             cudaStream_t s) {
     const StepParams P = make_params(r);
     const int64_t total = r.p->nodes * (r.R_pad / 4);
-    adj_step_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(r.p->csr(), P, t, theta, Y, lam_in,
-                                                                   lam_out, dK, dKs, dKn, r.steps);
+    adj_step_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
+        r.p->csr(), P, t, theta, reinterpret_cast<const float*>(Y), lam_in, lam_out, dK, dKs, dKn, r.steps);
     return cudaGetLastError();
 }
 
