@@ -100,3 +100,81 @@ def learn_schedules(problem, graphs, steps: int, replicas: int, dt: float = 0.01
             raise FloatingPointError("schedule loss is not finite")
         history.append(v)
     return model, history
+
+
+def evaluate(problem, graphs, K, Ks, Kn, dt, replicas, seed, readout_every=50):
+    """Run the given [graphs, steps] schedules on `problem` (autotuned form) and return,
+    per graph, the best score over replicas at each readout ([graphs, readouts])."""
+    from . import Run
+    K, Ks, Kn = (np.ascontiguousarray(np.asarray(x.detach() if hasattr(x, "detach") else x,
+                                                 np.float32)) for x in (K, Ks, Kn))
+    steps = K.shape[1]
+    run = Run(problem, K, Ks, Kn, dt, steps, replicas, seed, readout_every=readout_every)
+    tr = run.readout(spins=False)["trace"]
+    run.close()
+    return tr.max(axis=2) if problem.q == 2 else tr.min(axis=2)
+
+
+def _first_hit(best_per_readout, target, readout_every):
+    hit = np.nonzero(best_per_readout >= target)[0]
+    return None if hit.size == 0 else int(hit[0] + 1) * readout_every
+
+
+def demo(count: int = 64, steps: int = 2000, replicas: int = 32, iters: int = 15, lr: float = 0.05,
+         knots: int = 8, eval_replicas: int = 128, seed: int = 1):
+    """Learn schedules on the even-indexed graphs of the 64-graph Erdos-Renyi family
+    (n = 800-3000, p = 0.06-0.01, weights +-1) and compare them with the hand schedules
+    (K = 16 / mean degree, Ks ramped 0 -> 2, Kn = 0.1) on the odd-indexed, held-out
+    graphs with unseen noise: final best cut and steps to 99 % of the better final
+    best cut of the two, per graph.  Returns a dict (printed as JSON by __main__)."""
+    import time
+
+    from . import Problem
+    from workloads import make_workload
+    w = make_workload("er64", steps=steps, replicas=replicas)
+    graphs = w.graphs[:count]
+    train = [g for k, g in enumerate(graphs) if k % 2 == 0]
+    held = [g for k, g in enumerate(graphs) if k % 2 == 1]
+    ptrain = Problem.batch([Problem.from_graph(g, 2) for g in train])
+    pheld = Problem.batch([Problem.from_graph(g, 2) for g in held])
+    t0 = time.perf_counter()
+    model, hist = learn_schedules(ptrain, train, steps, replicas, w.dt, iters=iters, lr=lr, knots=knots,
+                                  seed=seed)
+    t_train = time.perf_counter() - t0
+    init = ScheduleModel(steps, knots, [1.0], 16.0, 2.0, 0.1)
+    re = 50
+    with torch.no_grad():
+        b0 = evaluate(pheld, held, *init.schedules_for(held), w.dt, eval_replicas, 9001, re)
+        b1 = evaluate(pheld, held, *model.schedules_for(held), w.dt, eval_replicas, 9001, re)
+    rows = []
+    for gi in range(len(held)):
+        target = 0.99 * max(b0[gi, -1], b1[gi, -1])
+        rows.append({"hand": {"final_best": float(b0[gi, -1]), "steps_to_99pct": _first_hit(b0[gi], target, re)},
+                     "learned": {"final_best": float(b1[gi, -1]),
+                                 "steps_to_99pct": _first_hit(b1[gi], target, re)}})
+
+    def mean_steps(key):
+        v = [r[key]["steps_to_99pct"] for r in rows]
+        return None if any(x is None for x in v) else float(np.mean(v))
+
+    with torch.no_grad():
+        K, Ks, Kn = model(np.ones(1))
+    return {"train_graphs": len(train), "held_out_graphs": len(held), "steps": steps,
+            "train_replicas": replicas, "eval_replicas": eval_replicas, "iters": iters,
+            "train_seconds": t_train, "loss_history": hist,
+            "held_out": {"hand_mean_final_best": float(b0[:, -1].mean()),
+                         "learned_mean_final_best": float(b1[:, -1].mean()),
+                         "learned_better_or_equal": int(np.sum(b1[:, -1] >= b0[:, -1])),
+                         "hand_mean_steps_to_99pct": mean_steps("hand"),
+                         "learned_mean_steps_to_99pct": mean_steps("learned")},
+            "learned_knots": {"K_times_mean_degree": K[0, ::max(1, steps // (knots - 1))].tolist(),
+                              "Ks": Ks[0, ::max(1, steps // (knots - 1))].tolist(),
+                              "Kn": Kn[0, ::max(1, steps // (knots - 1))].tolist()}}
+
+
+if __name__ == "__main__":
+    import json
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    print(json.dumps(demo()), flush=True)
