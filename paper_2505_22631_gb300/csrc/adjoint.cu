@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(256) adj_step_kernel(CSRDev csr, StepParams P,
                 Q[v] = fmaf(w, lsj[v], Q[v]);
             }
         }
-        const uint4 x = draw_block(P.seed, (uint32_t)g, kStreamNoise, (uint32_t)i, (uint32_t)t,
+        const uint4 x = draw_block(P.seed_dev ? *P.seed_dev : P.seed, (uint32_t)g, kStreamNoise, (uint32_t)i, (uint32_t)t,
                                    (uint32_t)quad);
         const float2 z01 = box_muller(x.x, x.y);
         const float2 z23 = box_muller(x.z, x.w);

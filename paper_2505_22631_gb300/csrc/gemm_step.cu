@@ -40,7 +40,7 @@ struct GemmArgs {
     const float* Kn;
     int64_t t;
     float dt, sqrt_dt;
-    uint64_t seed;
+    const uint64_t* seed;       // device copy of the run's seed (graph replays serve any seed)
     int32_t graph, q, n, n_pad;
     int32_t* err;
 };
@@ -161,9 +161,10 @@ __global__ void __launch_bounds__(kThreads, 2)
             // rho + 4 of its eight and the group exchanges them by shuffles
             const int rho = (lane >> 1) & 3;
             const uint32_t rq = (uint32_t)(r >> 2);
-            const uint4 blk0 = draw_block(a.seed, (uint32_t)a.graph, kStreamNoise, (uint32_t)(i0 + rho),
+            const uint64_t seed = *a.seed;
+            const uint4 blk0 = draw_block(seed, (uint32_t)a.graph, kStreamNoise, (uint32_t)(i0 + rho),
                                           (uint32_t)a.t, rq);
-            const uint4 blk1 = draw_block(a.seed, (uint32_t)a.graph, kStreamNoise, (uint32_t)(i0 + rho + 4),
+            const uint4 blk1 = draw_block(seed, (uint32_t)a.graph, kStreamNoise, (uint32_t)(i0 + rho + 4),
                                           (uint32_t)a.t, rq);
             uint32_t vb[8], vcs[8];
 #pragma unroll
@@ -243,14 +244,14 @@ __global__ void __launch_bounds__(kThreads, 2)
 }
 
 // ----------------------------------------------------------------------------- set-up
-__global__ void gemm_init_kernel(int n, int n_pad, int R_pad, uint64_t seed, int graph, float* theta,
+__global__ void gemm_init_kernel(int n, int n_pad, int R_pad, const uint64_t* seed_dev, int graph, float* theta,
                                  __nv_bfloat16* x) {
     const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= (int64_t)R_pad * n_pad) return;
     const int r = (int)(gid / n_pad), i = (int)(gid - (int64_t)r * n_pad);
     float th = 0.0f, c = 0.0f, s = 0.0f;
     if (i < n) {
-        const uint4 w = draw_block(seed, (uint32_t)graph, kStreamInit, (uint32_t)i, 0, (uint32_t)(r >> 2));
+        const uint4 w = draw_block(*seed_dev, (uint32_t)graph, kStreamInit, (uint32_t)i, 0, (uint32_t)(r >> 2));
         const uint32_t words[4] = {w.x, w.y, w.z, w.w};
         th = u01(words[r & 3]);
         const float2 cs = cos_sin_2pi_fast(th);
@@ -341,7 +342,7 @@ cudaError_t launch_gemm_init(const oim_run_s& r, cudaStream_t s) {
     const GemmState& st = r.gemm;
     const int64_t total = (int64_t)r.R_pad * st.n_pad;
     gemm_init_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
-        st.n, st.n_pad, r.R_pad, r.seed, 0, st.theta, reinterpret_cast<__nv_bfloat16*>(st.x[0]));
+        st.n, st.n_pad, r.R_pad, r.d_seed, 0, st.theta, reinterpret_cast<__nv_bfloat16*>(st.x[0]));
     return cudaGetLastError();
 }
 
@@ -357,7 +358,7 @@ cudaError_t launch_gemm_step(const oim_run_s& r, int64_t t, cudaStream_t s) {
     a.t = t;
     a.dt = P.dt;
     a.sqrt_dt = P.sqrt_dt;
-    a.seed = P.seed;
+    a.seed = r.d_seed;
     a.graph = 0;
     a.q = P.q;
     a.n = st.n;

@@ -41,6 +41,7 @@ cudaError_t launch_step_stream_buffers(const oim_run_s& r, int64_t t, const floa
 int gemm_setup(oim_run_s& r);
 void gemm_free(oim_run_s& r);
 cudaError_t launch_gemm_init(const oim_run_s& r, cudaStream_t s);
+cudaError_t launch_set_seed(uint64_t* d_seed, uint64_t seed, cudaStream_t s);
 cudaError_t launch_gemm_step(const oim_run_s& r, int64_t t, cudaStream_t s);
 cudaError_t launch_gemm_to_common(const oim_run_s& r, float* out, cudaStream_t s);
 cudaError_t launch_adj_prep(const oim_run_s& r, const float* theta, const float* lam, float4* Y,
@@ -174,6 +175,7 @@ void free_run_buffers(oim_run_s* r) {
     dev_free(r->d_score);
     dev_free(r->d_energy);
     dev_free(r->d_err);
+    dev_free(r->d_seed);
     dev_free(r->d_t0);
     dev_free(r->d_items);
     dev_free(r->d_ckpt);
@@ -271,6 +273,7 @@ int allocate_run(oim_run_s* r) {
     OIM_CUDA(dev_alloc(&r->d_score, (size_t)G * r->R_pad), "cudaMalloc(score)");
     OIM_CUDA(dev_alloc(&r->d_energy, (size_t)G * r->R_pad), "cudaMalloc(energy)");
     OIM_CUDA(dev_alloc(&r->d_err, 1), "cudaMalloc(err)");
+    OIM_CUDA(dev_alloc(&r->d_seed, 1), "cudaMalloc(seed)");
     OIM_CUDA(dev_alloc(&r->d_t0, 1), "cudaMalloc(t0)");
     if (r->form == OIM_FORM_STREAM) {
         OIM_CUDA(dev_alloc(&r->d_theta[1], state), "cudaMalloc(theta)");
@@ -333,8 +336,8 @@ int enqueue_stream_form(oim_run_s* r) {
         if (e != cudaSuccess) return cuda_fail(e, "stream-form launch");
         return OIM_OK;
     }
-    const bool same = r->chunk_exec && r->graph_steps == r->steps && r->graph_seed == r->seed &&
-                      r->graph_dt == r->dt;
+    // the seed is read from device memory, so one graph serves every seed
+    const bool same = r->chunk_exec && r->graph_steps == r->steps && r->graph_dt == r->dt;
     if (!same) {
         if (r->chunk_exec) cudaGraphExecDestroy(r->chunk_exec);
         r->chunk_exec = nullptr;
@@ -358,7 +361,6 @@ int enqueue_stream_form(oim_run_s* r) {
         cudaGraphDestroy(graph);
         if (e != cudaSuccess) return cuda_fail(e, "instantiate graph");
         r->graph_steps = r->steps;
-        r->graph_seed = r->seed;
         r->graph_dt = r->dt;
     }
     OIM_CUDA(cudaGraphLaunch(r->chunk_exec, r->stream), "graph launch");
@@ -386,6 +388,9 @@ int execute(oim_run_s* r, const float* K, const float* Ks, const float* Kn) {
     }
     OIM_CUDA(cudaMemsetAsync(r->d_trace, 0, (size_t)G * r->readouts_cap * r->R_pad * sizeof(double), s),
              "clear trace");
+    // the per-step forms read the seed from device memory (their captured graphs are
+    // replayed for any seed)
+    if (r->form != OIM_FORM_RESIDENT) OIM_CUDA(launch_set_seed(r->d_seed, r->seed, s), "store seed");
     if (r->form == OIM_FORM_RESIDENT) {
         cudaError_t e = launch_resident_impl(*r, r->d_items, s);
         if (e != cudaSuccess) return cuda_fail(e, "resident launch");

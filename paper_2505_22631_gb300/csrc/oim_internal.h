@@ -33,6 +33,8 @@ struct StepParams {
     float dt;
     float sqrt_dt;
     uint64_t seed;
+    const uint64_t* seed_dev;   // when set, kernels read the seed here (CUDA-graph replays
+                                // of the per-step forms then serve any seed)
     int32_t q;
     int32_t R;          // replicas
     int32_t R_pad;      // leading dimension of the replica axis
@@ -125,6 +127,7 @@ struct oim_run_s {
     double* d_score = nullptr;                // [G][R_pad] scratch for scores
     double* d_energy = nullptr;               // [G][R_pad]
     int32_t* d_err = nullptr;                 // device error word
+    uint64_t* d_seed = nullptr;               // the run's seed, read by the per-step forms
     // resident-form launch plan
     oim::ResidentPlan plan;
     // dense-form state
@@ -133,7 +136,6 @@ struct oim_run_s {
     // stream-form CUDA graph of a whole run, reused while its shape is unchanged
     cudaGraphExec_t chunk_exec = nullptr;
     int64_t graph_steps = -1;
-    uint64_t graph_seed = 0;
     float graph_dt = 0.f;
     int32_t* d_t0 = nullptr;                  // device step counter (graph replays)
     // adjoint support: phases every ckpt_every steps ([n_ckpt][nodes][R_pad])

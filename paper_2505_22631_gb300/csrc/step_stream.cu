@@ -95,8 +95,9 @@ __global__ void __launch_bounds__(256) init_stream_kernel(CSRDev csr, StepParams
     const int r = 4 * (int)(gid - (int64_t)node * quads);
     const int g = csr.node_graph[node];
     const int i = node - csr.graphs[g].node_off;
-    const float2 t01 = init_pair(P.seed, (uint32_t)g, (uint32_t)i, (uint32_t)r);
-    const float2 t23 = init_pair(P.seed, (uint32_t)g, (uint32_t)i, (uint32_t)(r + 2));
+    const uint64_t seed = P.seed_dev ? *P.seed_dev : P.seed;
+    const float2 t01 = init_pair(seed, (uint32_t)g, (uint32_t)i, (uint32_t)r);
+    const float2 t23 = init_pair(seed, (uint32_t)g, (uint32_t)i, (uint32_t)(r + 2));
     const size_t at = (size_t)node * P.R_pad + r;
     *reinterpret_cast<float4*>(theta + at) = make_float4(t01.x, t01.y, t23.x, t23.y);
     const float th[4] = {t01.x, t01.y, t23.x, t23.y};
@@ -164,8 +165,8 @@ __global__ void __launch_bounds__(256, C::kMinBlocks) step_stream_kernel(CSRDev 
         for (int v = 0; v < 4; ++v) acc[v] = ffma2(nb[v], ww, acc[v]);
     }
 
-    const uint4 x = draw_block(P.seed, (uint32_t)g, kStreamNoise, (uint32_t)i, (uint32_t)t,
-                               (uint32_t)quad);
+    const uint4 x = draw_block(P.seed_dev ? *P.seed_dev : P.seed, (uint32_t)g, kStreamNoise, (uint32_t)i,
+                               (uint32_t)t, (uint32_t)quad);
     const float2 z01 = C::kFastMath ? box_muller_fast(x.x, x.y) : box_muller(x.x, x.y);
     const float2 z23 = C::kFastMath ? box_muller_fast(x.z, x.w) : box_muller(x.z, x.w);
     const float z[4] = {z01.x, z01.y, z23.x, z23.y};
@@ -219,6 +220,15 @@ cudaError_t launch_derivative(const oim_problem_s& p, const float* theta, int32_
     return cudaGetLastError();
 }
 
+// The run's seed into device memory, ordered on the stream before the run's kernels
+// (a kernel argument is taken by value at launch, so the host needs no staging copy).
+__global__ void set_seed_kernel(uint64_t* d_seed, uint64_t seed) { *d_seed = seed; }
+
+cudaError_t launch_set_seed(uint64_t* d_seed, uint64_t seed, cudaStream_t s) {
+    set_seed_kernel<<<1, 1, 0, s>>>(d_seed, seed);
+    return cudaGetLastError();
+}
+
 static StepParams params_of(const oim_run_s& r) {
     StepParams P;
     const int G = r.p->G;
@@ -229,6 +239,7 @@ static StepParams params_of(const oim_run_s& r) {
     P.dt = r.dt;
     P.sqrt_dt = sqrtf(r.dt);
     P.seed = r.seed;
+    P.seed_dev = r.d_seed;
     P.q = r.p->q;
     P.R = r.R;
     P.R_pad = r.R_pad;

@@ -343,3 +343,24 @@ def test_parameter_sweep_is_one_batched_launch(orc, c1, periods):
               (smax * np.arange(T) / (T - 1)).astype(np.float32))
         ref = oracle_phases(orc, g, 2, np.full(T, k, np.float32), Ks, 0.1, 0.01, T, R, 3, graph=gi)
         assert rad_dist(ph[gi], ref).max() <= 1e-3
+
+
+@pytest.mark.parametrize("form,precision,R", [("stream", "fp32", 8), ("stream", "fp16", 8),
+                                              ("gemm", "bf16", 64)])
+def test_rerun_with_a_new_seed_replays_the_captured_graph(c1, form, precision, R):
+    # the per-step forms keep one captured graph per (steps, dt) and read the seed from
+    # device memory: a rerun under another seed equals a fresh run under that seed
+    from paper_2505_22631_gb300 import Problem, Run
+    g = c1.graphs[0]
+    T = 30
+    sched = (c1.K[0][:T], c1.Ks[0][:T], c1.Kn[0][:T])
+    prob = Problem.from_graph(g, 2)
+    run = Run(prob, *sched, c1.dt, T, R, 5, form=form, precision=precision, readout_every=10)
+    first = run.phases()[0]
+    run.rerun(*sched, c1.dt, T, 9)
+    again = run.phases()[0]
+    trace = run.readout()["trace"]
+    fresh = Run(prob, *sched, c1.dt, T, R, 9, form=form, precision=precision, readout_every=10)
+    assert np.array_equal(again, fresh.phases()[0])
+    assert np.array_equal(trace, fresh.readout()["trace"])
+    assert not np.array_equal(first, again)
