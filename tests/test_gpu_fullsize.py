@@ -135,6 +135,34 @@ def test_schedule_batch_adjoint_consistent_with_forward_energy():
     assert np.all(np.isfinite(dK)) and np.all(np.isfinite(dKs)) and np.all(np.isfinite(dKn))
 
 
+def test_adjoint_at_schedule_workload_sizes_matches_oracle(orc):
+    # the smallest and the largest graph of the 64-graph schedule-learning workload (n = 800
+    # and 3000), its 32 replicas and production schedules, over 50 steps (the horizon over
+    # which FP32 and FP64 trajectories agree at this coupling), checkpoints every 20 steps
+    from paper_2505_22631_gb300 import Problem, capi
+    w = make_workload("er64", steps=50)
+    pick = [0, len(w.graphs) - 1]
+    graphs = [w.graphs[k] for k in pick]
+    prob = Problem.batch([Problem.from_graph(g, 2) for g in graphs])
+    T, R = w.steps, w.replicas
+    K, Ks, Kn = (np.stack([np.asarray(x[k], np.float32) for k in pick]) for x in (w.K, w.Ks, w.Kn))
+    o = capi.oim_default_opts()
+    o.form = capi.OIM_FORM_STREAM
+    o.precision = capi.OIM_PREC_FP32
+    o.checkpoint_every = 20
+    r = capi.oim_run(prob.handle, K, Ks, Kn, w.dt, T, R, 21, o)
+    dK, dKs, dKn, L = np.zeros((2, T)), np.zeros((2, T)), np.zeros((2, T)), np.zeros(2)
+    capi.oim_backward(r, dK, dKs, dKn, L)
+    capi.oim_destroy_run(r)
+    for gi, g in enumerate(graphs):
+        rL, rK, rKs, rKn = orc.adjoint(g, 2, K[gi].astype(np.float64), Ks[gi].astype(np.float64),
+                                       Kn[gi].astype(np.float64), float(np.float32(w.dt)), T, R, 21,
+                                       graph=gi, nthreads=8)
+        assert abs(L[gi] - rL) <= 1e-5 * np.abs(g.w).sum()
+        for got, ref in ((dK[gi], rK), (dKs[gi], rKs), (dKn[gi], rKn)):
+            assert np.max(np.abs(got - ref)) <= 2e-3 * np.max(np.abs(ref)) + 1e-6
+
+
 def test_best_cut_statistically_matches_oracle(orc):
     w = make_workload("er800")
     g = w.graphs[0]
