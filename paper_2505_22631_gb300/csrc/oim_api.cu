@@ -131,6 +131,29 @@ int upload_problem(oim_problem_s* p) {
     OIM_CUDA(cudaMemcpy(p->d_graphs, p->graphs.data(), p->graphs.size() * sizeof(GraphDev),
                         cudaMemcpyHostToDevice),
              "upload graphs");
+    // the upper triangle of every row, in row order, for the score passes
+    std::vector<int32_t> urowp((size_t)p->nodes + 1, 0);
+    std::vector<uint32_t> ucol;
+    std::vector<float> uw;
+    ucol.reserve(p->h_col.size() / 2 + 1);
+    for (int64_t i = 0; i < p->nodes; ++i) {
+        for (int32_t e = p->h_rowp[i]; e < p->h_rowp[i + 1]; ++e) {
+            if (p->h_col_plain[e] <= i) continue;
+            ucol.push_back(p->h_col[e]);
+            if (!p->unit_weights) uw.push_back(p->h_w[e]);
+        }
+        urowp[(size_t)i + 1] = (int32_t)ucol.size();
+    }
+    OIM_CUDA(dev_alloc(&p->d_urowp, urowp.size()), "cudaMalloc(upper row_ptr)");
+    OIM_CUDA(dev_alloc(&p->d_ucol, std::max<size_t>(ucol.size(), 1)), "cudaMalloc(upper col)");
+    OIM_CUDA(dev_alloc(&p->d_uw, std::max<size_t>(uw.size(), 1)), "cudaMalloc(upper w)");
+    OIM_CUDA(cudaMemcpy(p->d_urowp, urowp.data(), urowp.size() * 4, cudaMemcpyHostToDevice),
+             "upload upper row_ptr");
+    if (!ucol.empty())
+        OIM_CUDA(cudaMemcpy(p->d_ucol, ucol.data(), ucol.size() * 4, cudaMemcpyHostToDevice),
+                 "upload upper col");
+    if (!uw.empty())
+        OIM_CUDA(cudaMemcpy(p->d_uw, uw.data(), uw.size() * 4, cudaMemcpyHostToDevice), "upload upper w");
     p->uploaded = true;
     return OIM_OK;
 }
@@ -151,6 +174,9 @@ void free_problem(oim_problem_s* p) {
     dev_free(p->d_split);
     dev_free(p->d_order);
     dev_free(p->d_graphs);
+    dev_free(p->d_urowp);
+    dev_free(p->d_ucol);
+    dev_free(p->d_uw);
 }
 
 // Pack columns: global node index, and for +-1 weights the sign in bit 31.

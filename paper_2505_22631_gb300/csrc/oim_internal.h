@@ -70,6 +70,10 @@ struct CSRDev {
     const GraphDev* graphs;     // [G]
     int32_t G;
     int32_t nodes;
+    // the upper triangle (entries j > i of row i, in row order) for the score passes
+    const int32_t* urowp;       // [nodes + 1]
+    const uint32_t* ucol;       // packed like col
+    const float* uw;            // or nullptr when every |w| == 1
 };
 
 }  // namespace oim
@@ -97,10 +101,14 @@ struct oim_problem_s {
     int32_t* d_split = nullptr;
     int32_t* d_order = nullptr;
     oim::GraphDev* d_graphs = nullptr;
+    int32_t* d_urowp = nullptr;    // upper triangle of the rows (score passes)
+    uint32_t* d_ucol = nullptr;
+    float* d_uw = nullptr;
     int32_t max_n = 0;             // largest graph
     oim::CSRDev csr() const {
         return oim::CSRDev{d_rowp, d_col, unit_weights ? nullptr : d_w, d_node_graph, d_split,
-                           d_order, d_graphs, G, (int32_t)nodes};
+                           d_order, d_graphs, G, (int32_t)nodes, d_urowp, d_ucol,
+                           unit_weights ? nullptr : d_uw};
     }
 };
 

@@ -16,9 +16,10 @@ namespace oim {
 
 namespace {
 
-// Thread = (replica quad, chunk of `npt` consecutive nodes).  Each
-// thread sums the agreeing weight of the upper-triangle edges of its nodes for
-// its four replicas, and flushes with one FP64 atomic per replica whenever the
+// Thread = (replica quad, chunk of `npt` consecutive nodes).  Each thread sums the
+// agreeing weight of its nodes' upper-triangle entries (j > i, kept as a separate
+// CSR in row order) for its four replicas, four entries at a time so that four
+// gathers are in flight, and flushes with one FP64 atomic per replica whenever the
 // graph changes or the chunk ends.
 __global__ void __launch_bounds__(256) score_kernel(CSRDev csr, const float* __restrict__ theta,
                                                     int R_pad, int q,
@@ -49,21 +50,31 @@ __global__ void __launch_bounds__(256) score_kernel(CSRDev csr, const float* __r
         const float4 ti = *reinterpret_cast<const float4*>(theta + (size_t)node * R_pad + 4 * quad);
         const int si0 = spin_of(ti.x, q), si1 = spin_of(ti.y, q), si2 = spin_of(ti.z, q),
                   si3 = spin_of(ti.w, q);
+        // per node the sum has at most max_deg terms; FP32 is exact for integer w
+        // below 2^24 / max_deg and close otherwise, the FP64 sum carries it on
         float f0 = 0.f, f1 = 0.f, f2 = 0.f, f3 = 0.f;
-        const int e_end = csr.rowp[node + 1];
-        for (int e = csr.rowp[node]; e < e_end; ++e) {
-            const uint32_t cw = csr.col[e];
-            const uint32_t j = csr.w ? cw : (cw & ~kSignBit);
-            if ((int)j <= node) continue;
-            const float w = csr.w ? csr.w[e] : ((cw & kSignBit) ? -1.0f : 1.0f);
-            const float4 tj = *reinterpret_cast<const float4*>(theta + (size_t)j * R_pad + 4 * quad);
-            // per node the sum has at most max_deg terms; FP32 is exact for integer w
-            // below 2^24 / max_deg and close otherwise, the FP64 sum carries it on
+        auto add = [&](uint32_t cw, float wv, const float4& tj) {
+            const float w = csr.uw ? wv : ((cw & kSignBit) ? -1.0f : 1.0f);
             f0 += (si0 == spin_of(tj.x, q)) ? w : 0.f;
             f1 += (si1 == spin_of(tj.y, q)) ? w : 0.f;
             f2 += (si2 == spin_of(tj.z, q)) ? w : 0.f;
             f3 += (si3 == spin_of(tj.w, q)) ? w : 0.f;
+        };
+        auto row_of = [&](uint32_t cw) {
+            const uint32_t j = csr.uw ? cw : (cw & ~kSignBit);
+            return *reinterpret_cast<const float4*>(theta + (size_t)j * R_pad + 4 * quad);
+        };
+        const int e_end = csr.urowp[node + 1];
+        int e = csr.urowp[node];
+        for (; e + 4 <= e_end; e += 4) {
+            const uint32_t c0 = csr.ucol[e], c1 = csr.ucol[e + 1], c2 = csr.ucol[e + 2], c3 = csr.ucol[e + 3];
+            const float4 t0 = row_of(c0), t1 = row_of(c1), t2 = row_of(c2), t3 = row_of(c3);
+            add(c0, csr.uw ? csr.uw[e] : 0.f, t0);
+            add(c1, csr.uw ? csr.uw[e + 1] : 0.f, t1);
+            add(c2, csr.uw ? csr.uw[e + 2] : 0.f, t2);
+            add(c3, csr.uw ? csr.uw[e + 3] : 0.f, t3);
         }
+        for (; e < e_end; ++e) add(csr.ucol[e], csr.uw ? csr.uw[e] : 0.f, row_of(csr.ucol[e]));
         acc[0] += f0;
         acc[1] += f1;
         acc[2] += f2;
