@@ -282,9 +282,9 @@ def kernels_per_run(form, steps, readout_every):
     # the per-step forms first store the run's seed on the device (one tiny kernel)
     if form == 2:          # resident: one launch covers every step and readout
         return 1
-    if form == 3:          # dense: init, a step kernel per step, relayout + score per readout, final relayout
-        return 1 + 1 + steps + 2 * readouts + 1
-    return 1 + 1 + steps + readouts   # stream: init, a step kernel per step, a score pass per readout
+    if form == 3:          # dense: init, a step kernel per step, relayout + spins + score per readout,
+        return 1 + 1 + steps + 3 * readouts + 1   # final relayout
+    return 1 + 1 + steps + 2 * readouts   # stream: init, a step kernel per step, spins + score per readout
 
 
 def main():

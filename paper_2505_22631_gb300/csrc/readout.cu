@@ -16,20 +16,39 @@ namespace oim {
 
 namespace {
 
-// Thread = (replica quad, chunk of `npt` consecutive nodes).  Each thread sums the
-// agreeing weight of its nodes' upper-triangle entries (j > i, kept as a separate
-// CSR in row order) for its four replicas, four entries at a time so that four
-// gathers are in flight, and flushes with one FP64 atomic per replica whenever the
-// graph changes or the chunk ends.
-__global__ void __launch_bounds__(256) score_kernel(CSRDev csr, const float* __restrict__ theta,
-                                                    int R_pad, int q,
-                                                    double* __restrict__ agree,
-                                                    int64_t row_stride, int64_t k, int npt) {
+// Spins of every (node, replica) for the score pass: spins[node][R_pad] =
+// floor(q theta + 1/2) mod q (the FP32 decision of spin_of), four replicas a thread.
+__global__ void __launch_bounds__(256) spin_kernel(const float* __restrict__ theta, int64_t quads, int q,
+                                                   int8_t* __restrict__ spins) {
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= quads) return;
+    const float4 t = reinterpret_cast<const float4*>(theta)[gid];
+    reinterpret_cast<char4*>(spins)[gid] =
+        make_char4((signed char)spin_of(t.x, q), (signed char)spin_of(t.y, q), (signed char)spin_of(t.z, q),
+                   (signed char)spin_of(t.w, q));
+}
+
+// Block = 32 replica quads x 8 node lanes; it owns a chunk of 8 * npt consecutive
+// nodes, lane y taking nodes y, y + 8, ...  Each thread sums, for its four replicas,
+// the agreeing weight of its nodes' upper-triangle entries (j > i, a separate CSR in
+// row order) from the spins, four entries at a time so that four gathers are in
+// flight.  When the chunk lies in one graph the eight lanes are summed in shared
+// memory and one FP64 atomic per replica and block goes out (thousands of blocks
+// adding into the same few replica sums is what limits the pass otherwise); a chunk
+// that straddles graphs flushes per thread at each graph change.
+constexpr int kScoreQuads = 32, kScoreLanes = 8;
+
+__global__ void __launch_bounds__(kScoreQuads * kScoreLanes) score_kernel(
+    CSRDev csr, const int8_t* __restrict__ spins, int R_pad, double* __restrict__ agree, int64_t row_stride,
+    int64_t k, int npt) {
+    __shared__ double red[kScoreLanes][kScoreQuads][4];
     const int quads = R_pad >> 2;
-    const int quad = blockIdx.x * blockDim.x + threadIdx.x;
-    if (quad >= quads) return;
-    const int first = blockIdx.y * npt;
-    const int last = min(first + npt, csr.nodes);
+    const int quad = blockIdx.x * kScoreQuads + threadIdx.x;
+    const bool valid = quad < quads;      // no early exit: the block synchronises below
+    const int chunk0 = blockIdx.y * kScoreLanes * npt;
+    const int chunk1 = min(chunk0 + kScoreLanes * npt, csr.nodes);
+    const bool one_graph = csr.node_graph[chunk0] == csr.node_graph[chunk1 - 1];
+    const char4* sp = reinterpret_cast<const char4*>(spins) + (valid ? quad : 0);
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
     int g_cur = -1;
     auto flush = [&]() {
@@ -41,38 +60,33 @@ __global__ void __launch_bounds__(256) score_kernel(CSRDev csr, const float* __r
 #pragma unroll
         for (int c = 0; c < 4; ++c) acc[c] = 0.0;
     };
-    for (int node = first; node < last; ++node) {
+    for (int node = chunk0 + threadIdx.y; valid && node < chunk1; node += kScoreLanes) {
         const int g = csr.node_graph[node];
         if (g != g_cur) {
-            flush();
+            if (!one_graph) flush();
             g_cur = g;
         }
-        const float4 ti = *reinterpret_cast<const float4*>(theta + (size_t)node * R_pad + 4 * quad);
-        const int si0 = spin_of(ti.x, q), si1 = spin_of(ti.y, q), si2 = spin_of(ti.z, q),
-                  si3 = spin_of(ti.w, q);
+        const char4 si = sp[(size_t)node * quads];
         // per node the sum has at most max_deg terms; FP32 is exact for integer w
         // below 2^24 / max_deg and close otherwise, the FP64 sum carries it on
         float f0 = 0.f, f1 = 0.f, f2 = 0.f, f3 = 0.f;
-        auto add = [&](uint32_t cw, float wv, const float4& tj) {
+        auto add = [&](uint32_t cw, float wv, char4 sj) {
             const float w = csr.uw ? wv : ((cw & kSignBit) ? -1.0f : 1.0f);
-            f0 += (si0 == spin_of(tj.x, q)) ? w : 0.f;
-            f1 += (si1 == spin_of(tj.y, q)) ? w : 0.f;
-            f2 += (si2 == spin_of(tj.z, q)) ? w : 0.f;
-            f3 += (si3 == spin_of(tj.w, q)) ? w : 0.f;
+            f0 += (si.x == sj.x) ? w : 0.f;
+            f1 += (si.y == sj.y) ? w : 0.f;
+            f2 += (si.z == sj.z) ? w : 0.f;
+            f3 += (si.w == sj.w) ? w : 0.f;
         };
-        auto row_of = [&](uint32_t cw) {
-            const uint32_t j = csr.uw ? cw : (cw & ~kSignBit);
-            return *reinterpret_cast<const float4*>(theta + (size_t)j * R_pad + 4 * quad);
-        };
+        auto row_of = [&](uint32_t cw) { return sp[(size_t)(csr.uw ? cw : (cw & ~kSignBit)) * quads]; };
         const int e_end = csr.urowp[node + 1];
         int e = csr.urowp[node];
         for (; e + 4 <= e_end; e += 4) {
             const uint32_t c0 = csr.ucol[e], c1 = csr.ucol[e + 1], c2 = csr.ucol[e + 2], c3 = csr.ucol[e + 3];
-            const float4 t0 = row_of(c0), t1 = row_of(c1), t2 = row_of(c2), t3 = row_of(c3);
-            add(c0, csr.uw ? csr.uw[e] : 0.f, t0);
-            add(c1, csr.uw ? csr.uw[e + 1] : 0.f, t1);
-            add(c2, csr.uw ? csr.uw[e + 2] : 0.f, t2);
-            add(c3, csr.uw ? csr.uw[e + 3] : 0.f, t3);
+            const char4 s0 = row_of(c0), s1 = row_of(c1), s2 = row_of(c2), s3 = row_of(c3);
+            add(c0, csr.uw ? csr.uw[e] : 0.f, s0);
+            add(c1, csr.uw ? csr.uw[e + 1] : 0.f, s1);
+            add(c2, csr.uw ? csr.uw[e + 2] : 0.f, s2);
+            add(c3, csr.uw ? csr.uw[e + 3] : 0.f, s3);
         }
         for (; e < e_end; ++e) add(csr.ucol[e], csr.uw ? csr.uw[e] : 0.f, row_of(csr.ucol[e]));
         acc[0] += f0;
@@ -80,7 +94,24 @@ __global__ void __launch_bounds__(256) score_kernel(CSRDev csr, const float* __r
         acc[2] += f2;
         acc[3] += f3;
     }
-    flush();
+    if (!one_graph) {
+        if (valid) flush();
+        return;   // uniform across the block: every thread took this branch
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) red[threadIdx.y][threadIdx.x][c] = acc[c];
+    __syncthreads();
+    if (threadIdx.y == 0 && valid) {
+        const int g = csr.node_graph[chunk0];
+        double* dst = agree + ((int64_t)g * row_stride + k) * R_pad + 4 * quad;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            double v = 0.0;
+#pragma unroll
+            for (int y = 0; y < kScoreLanes; ++y) v += red[y][threadIdx.x][c];
+            if (v != 0.0) atomicAdd(dst + c, v);
+        }
+    }
 }
 
 // E_r = sum_{i<j} w_ij cos(2 pi (theta_i - theta_j)) with FP32 terms, FP64 sum.
@@ -181,12 +212,14 @@ int nodes_per_thread(const oim_run_s& r) {
 }  // namespace
 
 cudaError_t launch_score(const oim_run_s& r, const float* theta, int64_t k, cudaStream_t s) {
+    const int64_t quads_total = (int64_t)r.p->nodes * (r.R_pad / 4);
+    spin_kernel<<<(unsigned)((quads_total + 255) / 256), 256, 0, s>>>(theta, quads_total, r.p->q, r.d_spins);
     const int quads = r.R_pad / 4;
     const int npt = nodes_per_thread(r);
-    dim3 block(min(256, ((quads + 31) / 32) * 32));
-    dim3 grid((quads + block.x - 1) / block.x, (unsigned)((r.p->nodes + npt - 1) / npt));
-    score_kernel<<<grid, block, 0, s>>>(r.p->csr(), theta, r.R_pad, r.p->q, r.d_trace,
-                                        r.readouts_cap, k, npt);
+    const int chunk = kScoreLanes * npt;
+    dim3 block(kScoreQuads, kScoreLanes);
+    dim3 grid((quads + kScoreQuads - 1) / kScoreQuads, (unsigned)((r.p->nodes + chunk - 1) / chunk));
+    score_kernel<<<grid, block, 0, s>>>(r.p->csr(), r.d_spins, r.R_pad, r.d_trace, r.readouts_cap, k, npt);
     return cudaGetLastError();
 }
 
