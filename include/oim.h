@@ -82,7 +82,9 @@ typedef struct oim_run_opts {
     void*   stream;             /* cudaStream_t to queue the work on               */
     int32_t use_graph;          /* stream form: replay steps from a CUDA graph     */
     int32_t replicas_per_block; /* resident form: 0 = chosen by the library        */
-    int32_t threads_per_block;  /* 0 = chosen by the library                       */
+    int32_t threads_per_block;  /* 0 = chosen by the library; resident form: block */
+                                /* size; dense form: 320 (128-wide tiles) or 576  */
+                                /* (256-wide tiles)                                */
     int32_t checkpoint_every;   /* keep phases every this many steps for           */
                                 /* oim_backward (0: no checkpoints)                */
     int32_t reserved[8];

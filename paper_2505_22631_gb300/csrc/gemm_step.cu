@@ -46,28 +46,39 @@ struct GemmArgs {
 };
 
 // Block layout: warp 0 lane 0 streams the K blocks with TMA, warp 1 lane 0 issues the
-// MMAs, warps 2..9 are the epilogue.  TMEM lanes are split by warp index mod 4, so
-// the epilogue warps cover the four 32-lane quadrants twice: warp w takes quadrant
-// w & 3 and column half (w - 2) >> 2.  While the K loop runs, the epilogue warps
-// already do everything that does not need the coupling sums (load theta, its cos
-// and sin, the injection term, the Philox draws and Box-Muller noise) and park the
-// results in TMEM columns beside the accumulator; once the product is complete
-// only the coupling, the update, the new cos / sin and the stores remain.  The two
-// warps of a quadrant share its TMEM lanes, so each column half has its own stash:
-// per 16-column chunk 8 FP32 bases and 8 (cos, sin) pairs packed as FP16
-// (2^-11 relative, far below the BF16 operands' 2^-9).
-constexpr int kBN = 128;                   // tile columns (nodes)
-constexpr int kStages = 3;                 // shared-memory ring depth
-constexpr int kThreads = 320;              // 10 warps
-constexpr uint32_t kCols = 256;            // TMEM: accumulator [0, 128), stashes [128, 256)
-constexpr uint32_t kStash = 128;           // half h, chunk k: columns 128 + 64 h + 16 k
-constexpr size_t kSmemBytes = (size_t)kStages * (kABytes + kBN * 128) + 1024;
+// MMAs, the remaining warps are the epilogue.  TMEM lanes are split by warp index
+// mod 4, so the epilogue warps cover the four 32-lane quadrants once per 64-column
+// part of the tile: warp w takes quadrant w & 3 and part (w - 2) >> 2.  While the K
+// loop runs, the epilogue warps already do everything that does not need the
+// coupling sums (load theta, its cos and sin, the injection term, the Philox draws
+// and Box-Muller noise) and park the results in TMEM columns beside the
+// accumulator; once the product is complete only the coupling, the update, the new
+// cos / sin and the stores remain.  The warps of a quadrant share its TMEM lanes, so
+// each part has its own stash: per 16-column chunk 8 FP32 bases and 8 (cos, sin)
+// pairs packed as FP16 (2^-11 relative, far below the BF16 operands' 2^-9).
+//
+// Two tile shapes: 128 columns (10 warps, 3 stages, 97 KB of shared memory, 256 TMEM
+// columns: two blocks per SM) and 256 columns (18 warps, 4 stages, 193 KB, all 512
+// TMEM columns: one block per SM, half the X^T re-reads from L2).
+template <int BN>
+struct TileShape {
+    static constexpr int kParts = BN / 64;                       // 64-column parts
+    static constexpr int kThreads = 64 + 128 * kParts;           // TMA + MMA warps, 4 per part
+    static constexpr int kStages = BN == 128 ? 3 : 4;
+    static constexpr int kMinBlocks = BN == 128 ? 2 : 1;
+    static constexpr uint32_t kCols = 2 * BN;                    // accumulator, then stashes
+    static constexpr uint32_t kStash = BN;                       // part p, chunk k: BN + 64 p + 16 k
+    static constexpr size_t kSmemBytes = (size_t)kStages * (kABytes + BN * 128) + 1024;
+};
 
-template <int S>
-__global__ void __launch_bounds__(kThreads, 2)
+template <int BN>
+__global__ void __launch_bounds__(TileShape<BN>::kThreads, TileShape<BN>::kMinBlocks)
     gemm_step_kernel(const __grid_constant__ CUtensorMap mX, const __grid_constant__ CUtensorMap mW,
                      GemmArgs a) {
     using namespace tc;
+    using Sh = TileShape<BN>;
+    constexpr int kBN = BN, S = Sh::kStages;
+    constexpr uint32_t kCols = Sh::kCols, kStash = Sh::kStash;
     constexpr int kBBytes = kBN * 128;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base =
@@ -133,7 +144,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         }
         __syncwarp();
     } else {
-        const int quad = warp & 3, half = (warp - 2) >> 2;
+        const int quad = warp & 3, part = (warp - 2) >> 2;
         const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16);
         const int row = m0 + quad * 32 + lane;            // row of X^T: 2 r + comp
         const int r = row >> 1, comp = row & 1;
@@ -141,7 +152,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         const float dtK = a.dt * K, dtKs = a.dt * Ks, kick = Kn * a.sqrt_dt;
         float* th_row = a.theta + (size_t)r * a.n_pad;
         const unsigned full_mask = 0xffffffffu;
-        constexpr int kChunks = kBN / 2 / 16;              // 16-column chunks per half
+        constexpr int kChunks = 64 / 16;                   // 16-column chunks per part
 
         // ---- before the product: per node-replica base = theta - dt Ks sin(2 pi q theta)
         //      + Kn sqrt(dt) xi, and (cos, sin) of theta, parked in TMEM
@@ -149,7 +160,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         // each chunk, the sin lane nodes 8..15
 #pragma unroll 1
         for (int k = 0; k < kChunks; ++k) {
-            const int c0 = half * (kBN / 2) + 16 * k;
+            const int c0 = part * 64 + 16 * k;
             const int i0 = n0 + c0 + 8 * comp;             // first node of this lane's eight
             float th[8];
             const float4 t0 = *reinterpret_cast<const float4*>(th_row + i0);
@@ -185,7 +196,7 @@ __global__ void __launch_bounds__(kThreads, 2)
                 const __half2 h = __floats2half2_rn(cs.x, cs.y);
                 vcs[j] = *reinterpret_cast<const uint32_t*>(&h);
             }
-            const uint32_t col = kStash + 64u * (uint32_t)half + 16u * (uint32_t)k;
+            const uint32_t col = kStash + 64u * (uint32_t)part + 16u * (uint32_t)k;
             tmem_st8(lane_base + col, vb);
             tmem_st8(lane_base + col + 8, vcs);
         }
@@ -200,11 +211,11 @@ __global__ void __launch_bounds__(kThreads, 2)
             __nv_bfloat16* xs = xc + a.n_pad;                              // sin row
 #pragma unroll 1
             for (int k = 0; k < kChunks; ++k) {
-                const int c0 = half * (kBN / 2) + 16 * k;
+                const int c0 = part * 64 + 16 * k;
                 const int i0 = n0 + c0 + 8 * comp;
                 uint32_t v[16], st[16];
                 tmem_ld16x2(lane_base + (uint32_t)c0,
-                            lane_base + kStash + 64u * (uint32_t)half + 16u * (uint32_t)k, v, st);
+                            lane_base + kStash + 64u * (uint32_t)part + 16u * (uint32_t)k, v, st);
                 // each lane of the pair needs the other's sums for its eight nodes
                 float A[8], B[8];
 #pragma unroll
@@ -290,10 +301,14 @@ __global__ void gemm_to_common_kernel(int n, int n_pad, int R_pad, int node_off,
 
 // 128-wide tiles with three stages use 97 KB of shared memory and 256 TMEM columns,
 // so two blocks share an SM (and its 512 TMEM columns).
-int gemm_bn_for(int) { return kBN; }
-int gemm_n_pad(int n) {
-    const int bn = gemm_bn_for(n);
-    return ((n + bn - 1) / bn) * bn;
+// Tile width of the dense form: threads_per_block 320 (128-wide tiles) or 576
+// (256-wide tiles) as asked; otherwise 256-wide tiles for graphs of 3000 nodes or
+// more (measured: 4-5 % faster at n = 4000, slower at n <= 2000 with 4096
+// replicas; the autotuner times both).
+int gemm_bn_for(const oim_run_s& r, int n) {
+    if (r.opts.threads_per_block == TileShape<128>::kThreads) return 128;
+    if (r.opts.threads_per_block == TileShape<256>::kThreads) return 256;
+    return n >= 3000 ? 256 : 128;
 }
 
 // Device state of the dense form, one graph (kept in oim_run_s::gemm).
@@ -301,8 +316,8 @@ int gemm_setup(oim_run_s& r) {
     const GraphDev& gd = r.p->graphs[0];
     GemmState& st = r.gemm;
     st.n = gd.n;
-    st.bn = gemm_bn_for(gd.n);
-    st.n_pad = gemm_n_pad(gd.n);
+    st.bn = gemm_bn_for(r, gd.n);
+    st.n_pad = ((gd.n + st.bn - 1) / st.bn) * st.bn;
     const size_t nth = (size_t)r.R_pad * st.n_pad;
     cudaError_t e = cudaMalloc(&st.theta, nth * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&st.x[0], 2 * nth * sizeof(__nv_bfloat16));
@@ -321,8 +336,11 @@ int gemm_setup(oim_run_s& r) {
         rc = make_map_bf16(&st.map_x[b], st.x[b], st.n_pad, 2 * (uint64_t)r.R_pad, (uint64_t)st.n_pad * 2, 128);
     if (rc != OIM_OK) return rc;
     // opt in to the large shared-memory footprint once, outside any stream capture
-    e = cudaFuncSetAttribute(gemm_step_kernel<kStages>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kSmemBytes);
+    e = cudaFuncSetAttribute(gemm_step_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)TileShape<128>::kSmemBytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(gemm_step_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)TileShape<256>::kSmemBytes);
     if (e != cudaSuccess) return cuda_fail(e, "dense form shared memory");
     return OIM_OK;
 }
@@ -364,8 +382,13 @@ cudaError_t launch_gemm_step(const oim_run_s& r, int64_t t, cudaStream_t s) {
     a.n = st.n;
     a.n_pad = st.n_pad;
     a.err = r.d_err;
-    dim3 grid(st.n_pad / kBN, (2 * r.R_pad) / kBM);
-    gemm_step_kernel<kStages><<<grid, kThreads, kSmemBytes, s>>>(st.map_x[t & 1], st.map_w, a);
+    const dim3 grid(st.n_pad / st.bn, (2 * r.R_pad) / kBM);
+    if (st.bn == 256)
+        gemm_step_kernel<256><<<grid, TileShape<256>::kThreads, TileShape<256>::kSmemBytes, s>>>(
+            st.map_x[t & 1], st.map_w, a);
+    else
+        gemm_step_kernel<128><<<grid, TileShape<128>::kThreads, TileShape<128>::kSmemBytes, s>>>(
+            st.map_x[t & 1], st.map_w, a);
     return cudaGetLastError();
 }
 

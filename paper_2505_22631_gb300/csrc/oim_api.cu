@@ -253,6 +253,10 @@ int choose_form(oim_run_s* r) {
             return fail(OIM_EUNSUPPORTED, "the dense form multiplies BF16 operands");
         if (r->opts.checkpoint_every > 0)
             return fail(OIM_EUNSUPPORTED, "checkpoints (for oim_backward) need the FP32 stream form");
+        if (r->opts.threads_per_block != 0 && r->opts.threads_per_block != 320 &&
+            r->opts.threads_per_block != 576)
+            return fail(OIM_EINVAL, "dense form: threads_per_block is 0, 320 (128-wide tiles) or 576 "
+                                    "(256-wide tiles)");
         r->form = OIM_FORM_GEMM;
         r->prec = OIM_PREC_BF16;
         r->R_pad = (r->R + 63) & ~63;    // X^T tiles hold 64 replicas (128 rows)

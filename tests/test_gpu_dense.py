@@ -116,3 +116,24 @@ def test_dense_potts_readout_and_short_run_parity(orc, q):
     assert np.max(np.abs(out["score"][0] - orc.scores(g, q, spins))) <= bound
     ref = oracle_phases(orc, g, q, K, Ks, Kn, 0.01, T, R, 9)
     assert np.median(rad_dist(th, ref)) <= 1e-3
+
+
+@pytest.mark.parametrize("n,R", [(800, 64), (1000, 192)])
+def test_dense_tile_widths_agree_bitwise(n, R):
+    # 128- and 256-wide tiles run the same K-ordered products (zero padding adds
+    # exact zeros), so the two launch shapes give identical phases and scores
+    g = erdos_renyi(n, 0.05, 17, "pm1")
+    T = 30
+    args = (g, 2, constant(T, 0.3), linear_ramp(T, 0, 1), constant(T, 0.1), 0.01, T, R, 3)
+    a = gpu_run(*args, form="gemm", precision="bf16", readout_every=10, threads_per_block=320)
+    b = gpu_run(*args, form="gemm", precision="bf16", readout_every=10, threads_per_block=576)
+    assert np.array_equal(a.phases()[0], b.phases()[0])
+    assert np.array_equal(a.readout()["trace"], b.readout()["trace"])
+
+
+def test_dense_rejects_unknown_tile_request():
+    from paper_2505_22631_gb300 import OimError
+    g = erdos_renyi(200, 0.05, 1, "+1")
+    with pytest.raises(OimError) as ei:
+        gpu_run(g, 2, 0.3, 0.5, 0.1, 0.01, 2, 64, 1, form="gemm", precision="bf16", threads_per_block=512)
+    assert ei.value.code == -1
