@@ -80,7 +80,9 @@ typedef struct oim_run_opts {
     int64_t readout_every;      /* score all replicas every this many steps (0: at */
                                 /* the end only); a trace entry per readout        */
     void*   stream;             /* cudaStream_t to queue the work on               */
-    int32_t use_graph;          /* stream form: replay steps from a CUDA graph     */
+    int32_t use_graph;          /* per-step forms: replay a repeated run shape     */
+                                /* from a CUDA graph (its first run launches       */
+                                /* directly)                                       */
     int32_t replicas_per_block; /* resident form: 0 = chosen by the library        */
     int32_t threads_per_block;  /* 0 = chosen by the library; resident form: block */
                                 /* size; dense form: 320 (128-wide tiles) or 576  */

@@ -368,6 +368,16 @@ int enqueue_stream_form(oim_run_s* r) {
     }
     // the seed is read from device memory, so one graph serves every seed
     const bool same = r->chunk_exec && r->graph_steps == r->steps && r->graph_dt == r->dt;
+    if (!same && (r->seen_steps != r->steps || r->seen_dt != r->dt)) {
+        // first execution of this shape: launch directly (the GPU runs while the host
+        // queues; capturing and instantiating thousands of nodes would cost more than
+        // it saves for a run made once), and capture if the shape comes back
+        r->seen_steps = r->steps;
+        r->seen_dt = r->dt;
+        cudaError_t e = body(r->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "stream-form launch");
+        return OIM_OK;
+    }
     if (!same) {
         if (r->chunk_exec) cudaGraphExecDestroy(r->chunk_exec);
         r->chunk_exec = nullptr;

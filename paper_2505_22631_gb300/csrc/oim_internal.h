@@ -145,6 +145,8 @@ struct oim_run_s {
     cudaGraphExec_t chunk_exec = nullptr;
     int64_t graph_steps = -1;
     float graph_dt = 0.f;
+    int64_t seen_steps = -1;                  // shape of the last direct execution
+    float seen_dt = 0.f;
     int32_t* d_t0 = nullptr;                  // device step counter (graph replays)
     // adjoint support: phases every ckpt_every steps ([n_ckpt][nodes][R_pad])
     int32_t ckpt_every = 0;

@@ -75,7 +75,9 @@ def test_dense_graph_capture_matches_direct(R):
     g = erdos_renyi(400, 0.1, 2, "+1")
     T = 40
     args = (g, 2, constant(T, 0.3), linear_ramp(T, 0, 1), constant(T, 0.1), 0.01, T, R, 3)
-    a = gpu_run(*args, form="gemm", precision="bf16", use_graph=True).phases()[0]
+    ra = gpu_run(*args, form="gemm", precision="bf16", use_graph=True)
+    ra.rerun(constant(T, 0.3), linear_ramp(T, 0, 1), constant(T, 0.1), 0.01, T, 3)   # graph replay
+    a = ra.phases()[0]
     b = gpu_run(*args, form="gemm", precision="bf16", use_graph=False).phases()[0]
     assert np.array_equal(a, b)
 

@@ -198,6 +198,9 @@ def test_stream_graph_capture_matches_direct_launches(c1):
     args = (g, 2, c1.K[0][:T], c1.Ks[0][:T], c1.Kn[0][:T], c1.dt, T, R, 9)
     a = gpu_run(*args, form="stream", use_graph=True, readout_every=40)
     b = gpu_run(*args, form="stream", use_graph=False, readout_every=40)
+    # a run's first execution is launched directly; the same shape again is captured
+    # into a CUDA graph and replayed
+    a.rerun(c1.K[0][:T], c1.Ks[0][:T], c1.Kn[0][:T], c1.dt, T, 9)
     assert np.array_equal(a.phases()[0], b.phases()[0])
     assert np.array_equal(a.readout()["trace"], b.readout()["trace"])
 
