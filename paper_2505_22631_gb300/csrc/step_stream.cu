@@ -89,10 +89,10 @@ __global__ void __launch_bounds__(256) init_stream_kernel(CSRDev csr, StepParams
                                                           float* __restrict__ theta,
                                                           typename C::T* __restrict__ cs) {
     const int quads = P.R_pad >> 2;
-    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (gid >= (int64_t)csr.nodes * quads) return;
-    const int node = (int)(gid / quads);
-    const int r = 4 * (int)(gid - (int64_t)node * quads);
+    const int node = blockIdx.x * blockDim.y + threadIdx.y;
+    const int quad = blockIdx.y * blockDim.x + threadIdx.x;
+    if (node >= csr.nodes || quad >= quads) return;
+    const int r = 4 * quad;
     const int g = csr.node_graph[node];
     const int i = node - csr.graphs[g].node_off;
     const uint64_t seed = P.seed_dev ? *P.seed_dev : P.seed;
@@ -121,11 +121,11 @@ __global__ void __launch_bounds__(256, C::kMinBlocks) step_stream_kernel(CSRDev 
                                                           int64_t t_fixed,
                                                           const int32_t* __restrict__ d_t0,
                                                           int32_t t_add) {
+    // block = blockDim.x replica quads x blockDim.y nodes (no index division)
     const int quads = P.R_pad >> 2;
-    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (gid >= (int64_t)csr.nodes * quads) return;
-    const int node = (int)(gid / quads);
-    const int quad = (int)(gid - (int64_t)node * quads);
+    const int node = blockIdx.x * blockDim.y + threadIdx.y;
+    const int quad = blockIdx.y * blockDim.x + threadIdx.x;
+    if (node >= csr.nodes || quad >= quads) return;
     const int g = csr.node_graph[node];
     const int i = node - csr.graphs[g].node_off;
     const int64_t t = d_t0 ? (int64_t)(*d_t0) + t_add : t_fixed;
@@ -229,6 +229,22 @@ cudaError_t launch_set_seed(uint64_t* d_seed, uint64_t seed, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// Launch shape of the thread = (node, replica quad) kernels: blocks of 256 threads,
+// x over quads (a warp covers consecutive quads of a node: coalesced rows), y over
+// nodes; the grid runs nodes along x (up to 2^31 - 1 blocks) and quads along y.
+struct QuadGrid {
+    dim3 grid, block;
+};
+static QuadGrid quad_grid(int64_t nodes, int quads) {
+    int qx = 1;
+    while (qx < quads && qx < 32) qx <<= 1;
+    const int ny = 256 / qx;
+    QuadGrid q;
+    q.block = dim3((unsigned)qx, (unsigned)ny);
+    q.grid = dim3((unsigned)((nodes + ny - 1) / ny), (unsigned)((quads + qx - 1) / qx));
+    return q;
+}
+
 static StepParams params_of(const oim_run_s& r) {
     StepParams P;
     const int G = r.p->G;
@@ -251,10 +267,8 @@ StepParams make_params(const oim_run_s& r) { return params_of(r); }
 template <typename C>
 static cudaError_t init_stream_as(const oim_run_s& r, cudaStream_t s) {
     const StepParams P = params_of(r);
-    const int64_t total = r.p->nodes * (r.R_pad / 4);
-    const int threads = 256;
-    const int64_t blocks = (total + threads - 1) / threads;
-    init_stream_kernel<C><<<(unsigned)blocks, threads, 0, s>>>(
+    const QuadGrid q = quad_grid(r.p->nodes, r.R_pad / 4);
+    init_stream_kernel<C><<<q.grid, q.block, 0, s>>>(
         r.p->csr(), P, r.d_theta[0], reinterpret_cast<typename C::T*>(r.d_cs[0]));
     return cudaGetLastError();
 }
@@ -286,14 +300,12 @@ cudaError_t launch_step_stream_buffers(const oim_run_s& r, int64_t t, const floa
                                        const float2* cs_in, float* th_out, float2* cs_out,
                                        cudaStream_t s) {
     const StepParams P = params_of(r);
-    const int64_t total = r.p->nodes * (r.R_pad / 4);
-    const int threads = 256;
-    const int64_t blocks = (total + threads - 1) / threads;
+    const QuadGrid q = quad_grid(r.p->nodes, r.R_pad / 4);
     if (r.p->unit_weights)
-        step_stream_kernel<true, CacheF32><<<(unsigned)blocks, threads, 0, s>>>(
+        step_stream_kernel<true, CacheF32><<<q.grid, q.block, 0, s>>>(
             r.p->csr(), P, th_in, cs_in, th_out, cs_out, t, nullptr, 0);
     else
-        step_stream_kernel<false, CacheF32><<<(unsigned)blocks, threads, 0, s>>>(
+        step_stream_kernel<false, CacheF32><<<q.grid, q.block, 0, s>>>(
             r.p->csr(), P, th_in, cs_in, th_out, cs_out, t, nullptr, 0);
     return cudaGetLastError();
 }
@@ -302,9 +314,7 @@ template <typename C>
 static cudaError_t step_stream_as(const oim_run_s& r, int64_t t, const int32_t* d_t0, cudaStream_t s) {
     // with d_t0 the step is *d_t0 + t (graph replay); otherwise t itself.
     const StepParams P = params_of(r);
-    const int64_t total = r.p->nodes * (r.R_pad / 4);
-    const int threads = 256;
-    const int64_t blocks = (total + threads - 1) / threads;
+    const QuadGrid q = quad_grid(r.p->nodes, r.R_pad / 4);
     const int in = (int)(t & 1);   // buffer parity follows the step index
     const int out = in ^ 1;
     using T = typename C::T;
@@ -313,10 +323,10 @@ static cudaError_t step_stream_as(const oim_run_s& r, int64_t t, const int32_t* 
     float* th_out = r.d_theta[out];
     T* cs_out = reinterpret_cast<T*>(r.d_cs[out]);
     if (r.p->unit_weights)
-        step_stream_kernel<true, C><<<(unsigned)blocks, threads, 0, s>>>(
+        step_stream_kernel<true, C><<<q.grid, q.block, 0, s>>>(
             r.p->csr(), P, th_in, cs_in, th_out, cs_out, t, d_t0, (int32_t)t);
     else
-        step_stream_kernel<false, C><<<(unsigned)blocks, threads, 0, s>>>(
+        step_stream_kernel<false, C><<<q.grid, q.block, 0, s>>>(
             r.p->csr(), P, th_in, cs_in, th_out, cs_out, t, d_t0, (int32_t)t);
     return cudaGetLastError();
 }
