@@ -127,6 +127,19 @@ __device__ __forceinline__ int spin_of(float theta, int q) {
     return (k >= q) ? k - q : k;
 }
 
+// acc += the two 16-bit halves of h2 (FP16 or BF16), each converted exactly and
+// added with one FP32 rounding: the mixed-precision add of the sm_100 family.
+__device__ __forceinline__ void add_f16x2(float2& acc, uint32_t h2) {
+    asm("{\n\t.reg .b16 l, h;\n\tmov.b32 {l, h}, %2;\n\t"
+        "add.rn.f32.f16 %0, l, %0;\n\tadd.rn.f32.f16 %1, h, %1;\n\t}"
+        : "+f"(acc.x), "+f"(acc.y) : "r"(h2));
+}
+__device__ __forceinline__ void add_bf16x2(float2& acc, uint32_t h2) {
+    asm("{\n\t.reg .b16 l, h;\n\tmov.b32 {l, h}, %2;\n\t"
+        "add.rn.f32.bf16 %0, l, %0;\n\tadd.rn.f32.bf16 %1, h, %1;\n\t}"
+        : "+f"(acc.x), "+f"(acc.y) : "r"(h2));
+}
+
 __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
     return __ffma2_rn(a, b, c);
 }

@@ -330,16 +330,6 @@ struct QuadF32 {
 };
 // acc += (lo, hi) of a packed 16-bit pair, each half widened inside the add
 // (PTX mixed-precision add: f32 = f16 + f32, exact widening, one rounding).
-__device__ __forceinline__ void add_f16x2(float2& acc, uint32_t h2) {
-    asm("{\n\t.reg .b16 l, h;\n\tmov.b32 {l, h}, %2;\n\t"
-        "add.rn.f32.f16 %0, l, %0;\n\tadd.rn.f32.f16 %1, h, %1;\n\t}"
-        : "+f"(acc.x), "+f"(acc.y) : "r"(h2));
-}
-__device__ __forceinline__ void add_bf16x2(float2& acc, uint32_t h2) {
-    asm("{\n\t.reg .b16 l, h;\n\tmov.b32 {l, h}, %2;\n\t"
-        "add.rn.f32.bf16 %0, l, %0;\n\tadd.rn.f32.bf16 %1, h, %1;\n\t}"
-        : "+f"(acc.x), "+f"(acc.y) : "r"(h2));
-}
 
 template <typename H2, typename Cvt>
 struct QuadHalf {
