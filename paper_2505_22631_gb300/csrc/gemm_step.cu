@@ -57,18 +57,22 @@ struct GemmArgs {
 // each part has its own stash: per 16-column chunk 8 FP32 bases and 8 (cos, sin)
 // pairs packed as FP16 (2^-11 relative, far below the BF16 operands' 2^-9).
 //
-// Two tile shapes: 128 columns (10 warps, 3 stages, 97 KB of shared memory, 256 TMEM
-// columns: two blocks per SM) and 256 columns (18 warps, 4 stages, 193 KB, all 512
-// TMEM columns: one block per SM, half the X^T re-reads from L2).
+// Tile shapes: 128 columns (10 warps, 3 stages, 97 KB of shared memory, 256 TMEM
+// columns: two blocks per SM), 112 columns (the same, with a short second part: more
+// tiles, so that the tiles spread over more SMs when 128-wide ones leave SMs with a
+// single tile) and 256 columns (18 warps, 4 stages, 193 KB, all 512 TMEM columns: one
+// block per SM, half the X^T re-reads from L2).
 template <int BN>
 struct TileShape {
-    static constexpr int kParts = BN / 64;                       // 64-column parts
+    static constexpr int kParts = (BN + 63) / 64;                // 64-column parts (the last may be short)
     static constexpr int kThreads = 64 + 128 * kParts;           // TMA + MMA warps, 4 per part
-    static constexpr int kStages = BN == 128 ? 3 : 4;
-    static constexpr int kMinBlocks = BN == 128 ? 2 : 1;
-    static constexpr uint32_t kCols = 2 * BN;                    // accumulator, then stashes
-    static constexpr uint32_t kStash = BN;                       // part p, chunk k: BN + 64 p + 16 k
+    static constexpr int kStages = BN <= 128 ? 3 : 4;
+    static constexpr int kMinBlocks = BN <= 128 ? 2 : 1;
+    static constexpr uint32_t kCols = BN <= 128 ? 256 : 512;      // accumulator, then stashes
+    static constexpr uint32_t kStash = kCols / 2;                // part p, chunk k: kStash + 64 p + 16 k
     static constexpr size_t kSmemBytes = (size_t)kStages * (kABytes + BN * 128) + 1024;
+    // 16-column chunks of part p
+    __host__ __device__ static constexpr int chunks(int p) { return (BN - 64 * p) >= 64 ? 4 : (BN - 64 * p) / 16; }
 };
 
 template <int BN>
@@ -152,7 +156,7 @@ __global__ void __launch_bounds__(TileShape<BN>::kThreads, TileShape<BN>::kMinBl
         const float dtK = a.dt * K, dtKs = a.dt * Ks, kick = Kn * a.sqrt_dt;
         float* th_row = a.theta + (size_t)r * a.n_pad;
         const unsigned full_mask = 0xffffffffu;
-        constexpr int kChunks = 64 / 16;                   // 16-column chunks per part
+        const int kChunks = Sh::chunks(part);              // 16-column chunks of this part
 
         // ---- before the product: per node-replica base = theta - dt Ks sin(2 pi q theta)
         //      + Kn sqrt(dt) xi, and (cos, sin) of theta, parked in TMEM
@@ -301,14 +305,28 @@ __global__ void gemm_to_common_kernel(int n, int n_pad, int R_pad, int node_off,
 
 // 128-wide tiles with three stages use 97 KB of shared memory and 256 TMEM columns,
 // so two blocks share an SM (and its 512 TMEM columns).
-// Tile width of the dense form: threads_per_block 320 (128-wide tiles) or 576
-// (256-wide tiles) as asked; otherwise 256-wide tiles for graphs of 3000 nodes or
-// more (measured: 4-5 % faster at n = 4000, slower at n <= 2000 with 4096
-// replicas; the autotuner times both).
+// Tile width of the dense form.  threads_per_block 576 asks for 256-wide tiles; 320
+// for 112- or 128-wide ones; 0 takes 256-wide tiles for graphs of 3000 nodes or more
+// (measured: 4-5 % faster at n = 4000, slower at n <= 2000 with 4096 replicas; the
+// autotuner times both).  Between 112 and 128 the one whose busiest SM (two blocks
+// per SM) carries the fewest tile columns wins, 128 on a tie (fewer X^T re-reads).
 int gemm_bn_for(const oim_run_s& r, int n) {
-    if (r.opts.threads_per_block == TileShape<128>::kThreads) return 128;
     if (r.opts.threads_per_block == TileShape<256>::kThreads) return 256;
-    return n >= 3000 ? 256 : 128;
+    if (r.opts.threads_per_block == 0 && n >= 3000) return 256;
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0, v = 0;
+        sms = (cudaGetDevice(&dev) == cudaSuccess &&
+               cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+                  ? v
+                  : 152;
+    }
+    const int64_t mt = (2 * (int64_t)r.R_pad) / kBM;
+    auto cost = [&](int bn) {
+        const int64_t tiles = (int64_t)((n + bn - 1) / bn) * mt;
+        return ((tiles + sms - 1) / sms) * bn;
+    };
+    return cost(112) < cost(128) ? 112 : 128;
 }
 
 // Device state of the dense form, one graph (kept in oim_run_s::gemm).
@@ -317,7 +335,9 @@ int gemm_setup(oim_run_s& r) {
     GemmState& st = r.gemm;
     st.n = gd.n;
     st.bn = gemm_bn_for(r, gd.n);
-    st.n_pad = ((gd.n + st.bn - 1) / st.bn) * st.bn;
+    st.tiles_n = (gd.n + st.bn - 1) / st.bn;
+    // row length and K extent: the tiles' columns, rounded up to the 64-wide K blocks
+    st.n_pad = ((st.tiles_n * st.bn + kBK - 1) / kBK) * kBK;
     const size_t nth = (size_t)r.R_pad * st.n_pad;
     cudaError_t e = cudaMalloc(&st.theta, nth * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&st.x[0], 2 * nth * sizeof(__nv_bfloat16));
@@ -338,6 +358,9 @@ int gemm_setup(oim_run_s& r) {
     // opt in to the large shared-memory footprint once, outside any stream capture
     e = cudaFuncSetAttribute(gemm_step_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)TileShape<128>::kSmemBytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(gemm_step_kernel<112>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)TileShape<112>::kSmemBytes);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(gemm_step_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)TileShape<256>::kSmemBytes);
@@ -382,9 +405,12 @@ cudaError_t launch_gemm_step(const oim_run_s& r, int64_t t, cudaStream_t s) {
     a.n = st.n;
     a.n_pad = st.n_pad;
     a.err = r.d_err;
-    const dim3 grid(st.n_pad / st.bn, (2 * r.R_pad) / kBM);
+    const dim3 grid(st.tiles_n, (2 * r.R_pad) / kBM);
     if (st.bn == 256)
         gemm_step_kernel<256><<<grid, TileShape<256>::kThreads, TileShape<256>::kSmemBytes, s>>>(
+            st.map_x[t & 1], st.map_w, a);
+    else if (st.bn == 112)
+        gemm_step_kernel<112><<<grid, TileShape<112>::kThreads, TileShape<112>::kSmemBytes, s>>>(
             st.map_x[t & 1], st.map_w, a);
     else
         gemm_step_kernel<128><<<grid, TileShape<128>::kThreads, TileShape<128>::kSmemBytes, s>>>(

@@ -52,7 +52,7 @@ struct ResidentPlan {
 
 // Device state of the dense (tensor-core) form of one graph.
 struct GemmState {
-    int n = 0, n_pad = 0, bn = 0;
+    int n = 0, n_pad = 0, bn = 0, tiles_n = 0;   // n_pad: row length and K extent
     float* theta = nullptr;            // [R_pad][n_pad] phases, replica-major
     void* x[2] = {nullptr, nullptr};   // [2 R_pad][n_pad] bf16 (cos; sin) rows, ping-pong
     void* w = nullptr;                 // [n_pad][n_pad] bf16 coupling matrix

@@ -120,10 +120,11 @@ def test_dense_potts_readout_and_short_run_parity(orc, q):
     assert np.median(rad_dist(th, ref)) <= 1e-3
 
 
-@pytest.mark.parametrize("n,R", [(800, 64), (1000, 192)])
+@pytest.mark.parametrize("n,R", [(800, 64), (1000, 192), (2000, 4096)])
 def test_dense_tile_widths_agree_bitwise(n, R):
-    # 128- and 256-wide tiles run the same K-ordered products (zero padding adds
-    # exact zeros), so the two launch shapes give identical phases and scores
+    # 112-, 128- and 256-wide tiles run the same K-ordered products (zero padding adds
+    # exact zeros), so the launch shapes give identical phases and scores (320 threads
+    # takes 112-wide tiles for the first two shapes and 128-wide for the third)
     g = erdos_renyi(n, 0.05, 17, "pm1")
     T = 30
     args = (g, 2, constant(T, 0.3), linear_ramp(T, 0, 1), constant(T, 0.1), 0.01, T, R, 3)
