@@ -47,12 +47,11 @@ __global__ void __launch_bounds__(256) adj_terminal_kernel(CSRDev csr, int R, in
                                                            float* __restrict__ lam,
                                                            double* __restrict__ loss) {
     const int quads = R_pad >> 2;
-    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int node = blockIdx.x * blockDim.y + threadIdx.y;   // block: quads x nodes
+    const int quad = blockIdx.y * blockDim.x + threadIdx.x;
     double e = 0.0;
     int g = -1;
-    if (gid < (int64_t)csr.nodes * quads) {
-        const int node = (int)(gid / quads);
-        const int quad = (int)(gid - (int64_t)node * quads);
+    if (node < csr.nodes && quad < quads) {
         g = csr.node_graph[node];
         const size_t at = (size_t)node * R_pad + 4 * quad;
         const size_t state = (size_t)csr.nodes * R_pad;
@@ -94,13 +93,12 @@ __global__ void __launch_bounds__(256) adj_step_kernel(CSRDev csr, StepParams P,
                                                        double* __restrict__ dK, double* __restrict__ dKs,
                                                        double* __restrict__ dKn, int64_t T) {
     const int quads = P.R_pad >> 2;
-    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool valid = gid < (int64_t)csr.nodes * quads;   // no early exit: the warp shuffles below
+    const int node = blockIdx.x * blockDim.y + threadIdx.y;   // block: quads x nodes
+    const int quad = blockIdx.y * blockDim.x + threadIdx.x;
+    const bool valid = node < csr.nodes && quad < quads;   // no early exit: the warp shuffles below
     int g = -1;
     double gK = 0.0, gS = 0.0, gN = 0.0;
     if (valid) {
-        const int node = (int)(gid / quads);
-        const int quad = (int)(gid - (int64_t)node * quads);
         g = csr.node_graph[node];
         const int i = node - csr.graphs[g].node_off;
         const size_t sidx = (size_t)g * P.steps + t;
@@ -164,7 +162,8 @@ __global__ void __launch_bounds__(256) adj_step_kernel(CSRDev csr, StepParams P,
             gS += __shfl_xor_sync(full, gS, m);
             gN += __shfl_xor_sync(full, gN, m);
         }
-        if ((threadIdx.x & 31) != 0 || g < 0) return;
+        const int lane = (threadIdx.y * blockDim.x + threadIdx.x) & 31;   // warps run over the linear index
+        if (lane != 0 || g < 0) return;
     } else if (g < 0) {
         return;
     }
@@ -176,6 +175,21 @@ __global__ void __launch_bounds__(256) adj_step_kernel(CSRDev csr, StepParams P,
 }  // namespace
 
 StepParams make_params(const oim_run_s& r);
+
+// Blocks of 256 threads: x over replica quads (a warp covers consecutive quads of a
+// node), y over nodes; the grid runs nodes along x and quads along y.
+struct QuadGridA {
+    dim3 grid, block;
+};
+static QuadGridA quad_grid_a(int64_t nodes, int quads) {
+    int qx = 1;
+    while (qx < quads && qx < 32) qx <<= 1;
+    const int ny = 256 / qx;
+    QuadGridA q;
+    q.block = dim3((unsigned)qx, (unsigned)ny);
+    q.grid = dim3((unsigned)((nodes + ny - 1) / ny), (unsigned)((quads + qx - 1) / qx));
+    return q;
+}
 
 // Y (four planes of [node][R_pad] floats, in a buffer of node-replica float4s) from
 // (theta, lambda).
@@ -190,9 +204,9 @@ cudaError_t launch_adj_prep(const oim_run_s& r, const float* theta, const float*
 // lambda_T and the loss sums from Y(theta_T) (its lambda columns are unused).
 cudaError_t launch_adj_terminal(const oim_run_s& r, const float4* Y, float* lam, double* loss,
                                 cudaStream_t s) {
-    const int64_t total = r.p->nodes * (r.R_pad / 4);
     const float scale = -6.28318530717958647f / (float)r.R;
-    adj_terminal_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
+    const QuadGridA q = quad_grid_a(r.p->nodes, r.R_pad / 4);
+    adj_terminal_kernel<<<q.grid, q.block, 0, s>>>(
         r.p->csr(), r.R, r.R_pad, scale, reinterpret_cast<const float*>(Y), lam, loss);
     return cudaGetLastError();
 }
@@ -201,8 +215,8 @@ cudaError_t launch_adj_step(const oim_run_s& r, int64_t t, const float* theta, c
                             const float* lam_in, float* lam_out, double* dK, double* dKs, double* dKn,
                             cudaStream_t s) {
     const StepParams P = make_params(r);
-    const int64_t total = r.p->nodes * (r.R_pad / 4);
-    adj_step_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
+    const QuadGridA q = quad_grid_a(r.p->nodes, r.R_pad / 4);
+    adj_step_kernel<<<q.grid, q.block, 0, s>>>(
         r.p->csr(), P, t, theta, reinterpret_cast<const float*>(Y), lam_in, lam_out, dK, dKs, dKn, r.steps);
     return cudaGetLastError();
 }
