@@ -62,6 +62,34 @@ def test_batched_maxcut_full_run_scores_exact(orc):
         assert out["score"][gi].mean() > rnd.max() + 0.1 * g.num_edges
 
 
+def test_batched_maxcut_in_the_autotuned_stream_form(orc):
+    # the form the autotuner picks for the benchmark workload on the GB300 (16-bit stream
+    # form, mixed-add gather, CUDA-graph replay on the repeat): sampled replicas against
+    # the oracle over a short horizon (16-bit pairs: median bound), then the full 5000-step
+    # run replayed from its graph, every replica's score recounted from its own spins
+    w = make_workload("torus_er2000")
+    T = 15
+    run = run_workload(w, steps=T, form="stream", precision="fp16", seed=3)
+    ph = run.phases()
+    for gi, g in enumerate(w.graphs):
+        for r0 in (0, 517, 1020):
+            ref = oracle_phases(orc, g, 2, w.K[gi], w.Ks[gi], w.Kn[gi], w.dt, T, 4, 3, graph=gi,
+                                replica_offset=r0, nthreads=8)
+            assert np.median(rad_dist(ph[gi][r0:r0 + 4], ref)) <= 1e-3
+    run = run_workload(w, form="stream", precision="fp16", readout_every=50, seed=5)
+    K, Ks, Kn = (np.stack(x).astype(np.float32) for x in (w.K, w.Ks, w.Kn))
+    run.rerun(K, Ks, Kn, w.dt, w.steps, 6)          # the same shape again: graph replay
+    out = run.readout()
+    ph = run.phases()
+    for gi, g in enumerate(w.graphs):
+        spins = orc.readout_f32(2, ph[gi])
+        assert np.array_equal(out["spins"][gi], spins)
+        assert np.array_equal(out["score"][gi], orc.scores(g, 2, spins))
+        assert np.array_equal(out["trace"][gi, -1], out["score"][gi])
+        rnd = orc.scores(g, 2, np.random.default_rng(gi).integers(0, 2, (64, g.n)).astype(np.int8))
+        assert out["score"][gi].mean() > rnd.max() + 0.1 * g.num_edges
+
+
 def test_dense_workload_in_the_tensor_core_form(orc):
     # the dense benchmark workload at full size in the form the autotuner picks for it
     # (BF16 tensor cores): sampled replicas against the oracle over a short horizon (the
