@@ -373,3 +373,17 @@ def test_rerun_with_a_new_seed_replays_the_captured_graph(c1, form, precision, R
     assert np.array_equal(again, fresh.phases()[0])
     assert np.array_equal(trace, fresh.readout()["trace"])
     assert not np.array_equal(first, again)
+
+
+def test_stream_launch_shapes_agree_bitwise():
+    # replicas are independent trajectories keyed by their index, so the first 16 replicas
+    # of a 128-replica run (warps of 32 quads of one node) and of a 16-replica run (warps
+    # spanning eight nodes) must agree bit for bit; the +-1 graph, 18 entries a row, takes
+    # the mixed-add gather with its negated -1 runs in both
+    g = erdos_renyi(600, 0.03, 19, "pm1")
+    T = 40
+    args = (g, 2, constant(T, 0.5), linear_ramp(T, 0, 1.5), constant(T, 0.1), 0.01, T)
+    a = gpu_run(*args, 128, 7, form="stream", precision="fp16", readout_every=10)
+    b = gpu_run(*args, 16, 7, form="stream", precision="fp16", readout_every=10)
+    assert np.array_equal(a.phases()[0][:16], b.phases()[0])
+    assert np.array_equal(a.readout()["trace"][:, :, :16], b.readout()["trace"])
