@@ -110,6 +110,16 @@ int upload_problem(oim_problem_s* p) {
     OIM_CUDA(dev_alloc(&p->d_split, (size_t)p->nodes), "cudaMalloc(split)");
     OIM_CUDA(dev_alloc(&p->d_order, (size_t)p->nodes), "cudaMalloc(order)");
     OIM_CUDA(dev_alloc(&p->d_graphs, p->graphs.size()), "cudaMalloc(graphs)");
+    OIM_CUDA(dev_alloc(&p->d_sorder, (size_t)p->nodes), "cudaMalloc(stream order)");
+    // the stream form's blocks take nodes heaviest rows first across the whole batch, so
+    // the blocks that run last are the short ones (longest-processing-time-first order)
+    std::vector<int32_t> sorder((size_t)p->nodes);
+    for (int64_t i = 0; i < p->nodes; ++i) sorder[i] = (int32_t)i;
+    std::stable_sort(sorder.begin(), sorder.end(), [&](int32_t a, int32_t b) {
+        return p->h_rowp[a + 1] - p->h_rowp[a] > p->h_rowp[b + 1] - p->h_rowp[b];
+    });
+    OIM_CUDA(cudaMemcpy(p->d_sorder, sorder.data(), sorder.size() * 4, cudaMemcpyHostToDevice),
+             "upload stream order");
     std::vector<int32_t> ng((size_t)p->nodes);
     for (int g = 0; g < p->G; ++g)
         std::fill(ng.begin() + p->graphs[g].node_off,
@@ -173,6 +183,7 @@ void free_problem(oim_problem_s* p) {
     dev_free(p->d_node_graph);
     dev_free(p->d_split);
     dev_free(p->d_order);
+    dev_free(p->d_sorder);
     dev_free(p->d_graphs);
     dev_free(p->d_urowp);
     dev_free(p->d_ucol);
@@ -190,6 +201,7 @@ void pack_columns(oim_problem_s* p) {
 }
 
 void free_run_buffers(oim_run_s* r) {
+    if (r->d_theta[1] == r->d_theta[0]) r->d_theta[1] = nullptr;   // the stream form's alias
     dev_free(r->d_theta[0]);
     dev_free(r->d_theta[1]);
     if (r->d_cs[0]) cudaFree(r->d_cs[0]);
@@ -306,7 +318,10 @@ int allocate_run(oim_run_s* r) {
     OIM_CUDA(dev_alloc(&r->d_seed, 1), "cudaMalloc(seed)");
     OIM_CUDA(dev_alloc(&r->d_t0, 1), "cudaMalloc(t0)");
     if (r->form == OIM_FORM_STREAM) {
-        OIM_CUDA(dev_alloc(&r->d_theta[1], state), "cudaMalloc(theta)");
+        // a step reads and writes only its own node's phases, so they are updated in
+        // place (one buffer under both parities); only the (cos, sin) cache, which the
+        // neighbours read, needs the second buffer
+        r->d_theta[1] = r->d_theta[0];
         // (cos, sin) pairs: float2, or two 16-bit values in the FP16 / BF16 variant
         const size_t pair = r->prec == OIM_PREC_FP32 ? sizeof(float2) : sizeof(uint32_t);
         OIM_CUDA(cudaMalloc(&r->d_cs[0], state * pair), "cudaMalloc(cs)");

@@ -11,8 +11,9 @@
 // loads that a warp turns into fully used 128-byte lines, and one Philox block
 // feeds the four noise draws of the quad.
 //
-// Per step and node (Eq. 5 / Algorithm 1, synchronous update from the old phases,
-// written to the other buffer as in Sec. III-B):
+// Per step and node (Eq. 5 / Algorithm 1, synchronous update from the old phases;
+// the (cos, sin) cache the neighbours read is double-buffered as in Sec. III-B, and
+// th_in may equal th_out because a thread reads and writes only its own phases):
 //   (A, B)   = sum_j w_ij (cos 2 pi theta_j, sin 2 pi theta_j)
 //   D_i      = sin(2 pi theta_i) A - cos(2 pi theta_i) B = sum_j w_ij sin 2 pi (theta_i - theta_j)
 //   theta_i' = wrap(theta_i + dt (K D_i - Ks sin 2 pi q theta_i) + Kn sqrt(dt) xi)
@@ -135,18 +136,24 @@ __global__ void __launch_bounds__(256) init_stream_kernel(CSRDev csr, StepParams
 // edge: faster on denser rows, slower on rows of 4-8 entries; chosen per problem).
 template <bool kUnit, typename C, bool kMixed = false>
 __global__ void __launch_bounds__(256, kMixed ? 6 : C::kMinBlocks) step_stream_kernel(CSRDev csr, StepParams P,
-                                                          const float* __restrict__ th_in,
+                                                          const float* th_in,
                                                           const typename C::T* __restrict__ cs_in,
-                                                          float* __restrict__ th_out,
+                                                          float* th_out,
                                                           typename C::T* __restrict__ cs_out,
                                                           int64_t t_fixed,
                                                           const int32_t* __restrict__ d_t0,
-                                                          int32_t t_add) {
-    // block = blockDim.x replica quads x blockDim.y nodes (no index division)
+                                                          int32_t t_add, int quads_fast) {
+    // block = blockDim.x replica quads x blockDim.y nodes (no index division); the
+    // blocks take their nodes in the batch's heaviest-rows-first order, and with
+    // quads_fast the grid's fast dimension runs over replica blocks, so the blocks
+    // are dispatched longest first and the short rows fill the tail
     const int quads = P.R_pad >> 2;
-    const int node = blockIdx.x * blockDim.y + threadIdx.y;
-    const int quad = blockIdx.y * blockDim.x + threadIdx.x;
-    if (node >= csr.nodes || quad >= quads) return;
+    const int nblk = quads_fast ? blockIdx.y : blockIdx.x;
+    const int qblk = quads_fast ? blockIdx.x : blockIdx.y;
+    const int slot = nblk * blockDim.y + threadIdx.y;
+    const int quad = qblk * blockDim.x + threadIdx.x;
+    if (slot >= csr.nodes || quad >= quads) return;
+    const int node = __ldg(csr.sorder + slot);
     const int g = csr.node_graph[node];
     const int i = node - csr.graphs[g].node_off;
     const int64_t t = d_t0 ? (int64_t)(*d_t0) + t_add : t_fixed;
@@ -287,6 +294,22 @@ static QuadGrid quad_grid(int64_t nodes, int quads) {
     return q;
 }
 
+// The step kernels' grid: replica blocks along x (dispatched first) and node blocks
+// along y while the node blocks fit grid.y (65535), else the quad_grid orientation.
+struct StepGrid {
+    dim3 grid, block;
+    int quads_fast;
+};
+static StepGrid step_grid(int64_t nodes, int quads) {
+    const QuadGrid q = quad_grid(nodes, quads);
+    StepGrid sg{q.grid, q.block, 0};
+    if (q.grid.x <= 65535u) {
+        sg.grid = dim3(q.grid.y, q.grid.x);
+        sg.quads_fast = 1;
+    }
+    return sg;
+}
+
 static StepParams params_of(const oim_run_s& r) {
     StepParams P;
     const int G = r.p->G;
@@ -342,13 +365,13 @@ cudaError_t launch_step_stream_buffers(const oim_run_s& r, int64_t t, const floa
                                        const float2* cs_in, float* th_out, float2* cs_out,
                                        cudaStream_t s) {
     const StepParams P = params_of(r);
-    const QuadGrid q = quad_grid(r.p->nodes, r.R_pad / 4);
+    const StepGrid q = step_grid(r.p->nodes, r.R_pad / 4);
     if (r.p->unit_weights)
         step_stream_kernel<true, CacheF32><<<q.grid, q.block, 0, s>>>(
-            r.p->csr(), P, th_in, cs_in, th_out, cs_out, t, nullptr, 0);
+            r.p->csr(), P, th_in, cs_in, th_out, cs_out, t, nullptr, 0, q.quads_fast);
     else
         step_stream_kernel<false, CacheF32><<<q.grid, q.block, 0, s>>>(
-            r.p->csr(), P, th_in, cs_in, th_out, cs_out, t, nullptr, 0);
+            r.p->csr(), P, th_in, cs_in, th_out, cs_out, t, nullptr, 0, q.quads_fast);
     return cudaGetLastError();
 }
 
@@ -356,7 +379,7 @@ template <typename C>
 static cudaError_t step_stream_as(const oim_run_s& r, int64_t t, const int32_t* d_t0, cudaStream_t s) {
     // with d_t0 the step is *d_t0 + t (graph replay); otherwise t itself.
     const StepParams P = params_of(r);
-    const QuadGrid q = quad_grid(r.p->nodes, r.R_pad / 4);
+    const StepGrid q = step_grid(r.p->nodes, r.R_pad / 4);
     const int in = (int)(t & 1);   // buffer parity follows the step index
     const int out = in ^ 1;
     using T = typename C::T;
@@ -370,13 +393,16 @@ static cudaError_t step_stream_as(const oim_run_s& r, int64_t t, const int32_t* 
     const bool mixed = !C::kOwnFromCache && r.p->unit_weights && r.p->nnz >= 8 * r.p->nodes;
     if (mixed)
         step_stream_kernel<true, C, !C::kOwnFromCache><<<q.grid, q.block, 0, s>>>(
-            r.p->csr(), P, th_in, cs_in, th_out, cs_out, t, d_t0, (int32_t)t);
+            r.p->csr(), P, th_in, cs_in, th_out, cs_out, t, d_t0, (int32_t)t,
+            q.quads_fast);
     else if (r.p->unit_weights)
         step_stream_kernel<true, C><<<q.grid, q.block, 0, s>>>(
-            r.p->csr(), P, th_in, cs_in, th_out, cs_out, t, d_t0, (int32_t)t);
+            r.p->csr(), P, th_in, cs_in, th_out, cs_out, t, d_t0, (int32_t)t,
+            q.quads_fast);
     else
         step_stream_kernel<false, C><<<q.grid, q.block, 0, s>>>(
-            r.p->csr(), P, th_in, cs_in, th_out, cs_out, t, d_t0, (int32_t)t);
+            r.p->csr(), P, th_in, cs_in, th_out, cs_out, t, d_t0, (int32_t)t,
+            q.quads_fast);
     return cudaGetLastError();
 }
 
