@@ -110,16 +110,22 @@ int upload_problem(oim_problem_s* p) {
     OIM_CUDA(dev_alloc(&p->d_split, (size_t)p->nodes), "cudaMalloc(split)");
     OIM_CUDA(dev_alloc(&p->d_order, (size_t)p->nodes), "cudaMalloc(order)");
     OIM_CUDA(dev_alloc(&p->d_graphs, p->graphs.size()), "cudaMalloc(graphs)");
-    OIM_CUDA(dev_alloc(&p->d_sorder, (size_t)p->nodes), "cudaMalloc(stream order)");
+    OIM_CUDA(dev_alloc(&p->d_srow, (size_t)p->nodes), "cudaMalloc(stream rows)");
     // the stream form's blocks take nodes heaviest rows first across the whole batch, so
-    // the blocks that run last are the short ones (longest-processing-time-first order)
+    // the blocks that run last are the short ones (longest-processing-time-first order);
+    // each slot's row bounds travel with the node in one 16-byte descriptor
     std::vector<int32_t> sorder((size_t)p->nodes);
     for (int64_t i = 0; i < p->nodes; ++i) sorder[i] = (int32_t)i;
     std::stable_sort(sorder.begin(), sorder.end(), [&](int32_t a, int32_t b) {
         return p->h_rowp[a + 1] - p->h_rowp[a] > p->h_rowp[b + 1] - p->h_rowp[b];
     });
-    OIM_CUDA(cudaMemcpy(p->d_sorder, sorder.data(), sorder.size() * 4, cudaMemcpyHostToDevice),
-             "upload stream order");
+    std::vector<int4> srow((size_t)p->nodes);
+    for (size_t k = 0; k < sorder.size(); ++k) {
+        const int32_t v = sorder[k];
+        srow[k] = make_int4(v, p->h_rowp[v], p->h_split[v], p->h_rowp[v + 1]);
+    }
+    OIM_CUDA(cudaMemcpy(p->d_srow, srow.data(), srow.size() * sizeof(int4), cudaMemcpyHostToDevice),
+             "upload stream rows");
     std::vector<int32_t> ng((size_t)p->nodes);
     for (int g = 0; g < p->G; ++g)
         std::fill(ng.begin() + p->graphs[g].node_off,
@@ -183,7 +189,7 @@ void free_problem(oim_problem_s* p) {
     dev_free(p->d_node_graph);
     dev_free(p->d_split);
     dev_free(p->d_order);
-    dev_free(p->d_sorder);
+    dev_free(p->d_srow);
     dev_free(p->d_graphs);
     dev_free(p->d_urowp);
     dev_free(p->d_ucol);

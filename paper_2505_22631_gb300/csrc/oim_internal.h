@@ -74,9 +74,10 @@ struct CSRDev {
     const int32_t* urowp;       // [nodes + 1]
     const uint32_t* ucol;       // packed like col
     const float* uw;            // or nullptr when every |w| == 1
-    // [nodes] every node of the batch by decreasing row length (stable): the order in
-    // which the stream form's blocks take their nodes, heaviest rows first
-    const int32_t* sorder;
+    // [nodes] the stream form's row descriptors {node, row start, first -1 entry, row end},
+    // every node of the batch by decreasing row length (stable): the order in which the
+    // blocks take their nodes, heaviest rows first
+    const int4* srow;
 };
 
 }  // namespace oim
@@ -107,12 +108,12 @@ struct oim_problem_s {
     int32_t* d_urowp = nullptr;    // upper triangle of the rows (score passes)
     uint32_t* d_ucol = nullptr;
     float* d_uw = nullptr;
-    int32_t* d_sorder = nullptr;   // stream-form node order, heaviest rows first
+    int4* d_srow = nullptr;        // stream-form row descriptors, heaviest rows first
     int32_t max_n = 0;             // largest graph
     oim::CSRDev csr() const {
         return oim::CSRDev{d_rowp, d_col, unit_weights ? nullptr : d_w, d_node_graph, d_split,
                            d_order, d_graphs, G, (int32_t)nodes, d_urowp, d_ucol,
-                           unit_weights ? nullptr : d_uw, d_sorder};
+                           unit_weights ? nullptr : d_uw, d_srow};
     }
 };
 

@@ -153,7 +153,8 @@ __global__ void __launch_bounds__(256, kMixed ? 6 : C::kMinBlocks) step_stream_k
     const int slot = nblk * blockDim.y + threadIdx.y;
     const int quad = qblk * blockDim.x + threadIdx.x;
     if (slot >= csr.nodes || quad >= quads) return;
-    const int node = __ldg(csr.sorder + slot);
+    const int4 row = __ldg(csr.srow + slot);   // {node, row start, first -1 entry, row end}
+    const int node = row.x;
     const int g = csr.node_graph[node];
     const int i = node - csr.graphs[g].node_off;
     const int64_t t = d_t0 ? (int64_t)(*d_t0) + t_add : t_fixed;
@@ -164,23 +165,18 @@ __global__ void __launch_bounds__(256, kMixed ? 6 : C::kMinBlocks) step_stream_k
     const float4 th = *reinterpret_cast<const float4*>(th_in + at);
     const float t0[4] = {th.x, th.y, th.z, th.w};
     float2 own[4];
-    if (C::kOwnFromCache) {
-        C::load4(cs_in + at, own);
-    } else {
-#pragma unroll
-        for (int v = 0; v < 4; ++v) own[v] = cos_sin_2pi_fast(t0[v]);
-    }
+    if (C::kOwnFromCache) C::load4(cs_in + at, own);
 
     float2 acc[4];
 #pragma unroll
     for (int v = 0; v < 4; ++v) acc[v] = make_float2(0.f, 0.f);
-    const int e_beg = __ldg(csr.rowp + node), e_end = __ldg(csr.rowp + node + 1);
+    const int e_beg = row.y, e_end = row.w;
     if constexpr (kMixed) {
         // +-1 weights, 16-bit pairs: rows hold the +1 entries first; mixed f16 + f32 adds
         // (one rounding each, as the FMA by +-1 would give), the -1 run accumulated with
         // the accumulator negated: -(-acc + x) = acc - x in round-to-nearest
         using H2 = typename C::T;
-        const int e_split = __ldg(csr.split + node);
+        const int e_split = row.z;
         for (int e = e_beg; e < e_split; ++e) {
             const uint32_t j = __ldg(csr.col + e) & ~kSignBit;
             add_raw4<H2>(acc, __ldg(reinterpret_cast<const uint4*>(cs_in + (size_t)j * P.R_pad + 4 * quad)));
@@ -214,6 +210,12 @@ __global__ void __launch_bounds__(256, kMixed ? 6 : C::kMinBlocks) step_stream_k
         for (int v = 0; v < 4; ++v) acc[v] = ffma2(nb[v], ww, acc[v]);
     }
 
+    // the 16-bit forms' own (cos, sin) in FP32 from the phases, after the gather, so the
+    // phase load's latency overlaps the neighbour loads
+    if (!C::kOwnFromCache) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) own[v] = cos_sin_2pi_fast(t0[v]);
+    }
     const uint4 x = draw_block(P.seed_dev ? *P.seed_dev : P.seed, (uint32_t)g, kStreamNoise, (uint32_t)i,
                                (uint32_t)t, (uint32_t)quad);
     const float2 z01 = C::kFastMath ? box_muller_fast(x.x, x.y) : box_muller(x.x, x.y);
