@@ -119,13 +119,23 @@ int upload_problem(oim_problem_s* p) {
     std::stable_sort(sorder.begin(), sorder.end(), [&](int32_t a, int32_t b) {
         return p->h_rowp[a + 1] - p->h_rowp[a] > p->h_rowp[b + 1] - p->h_rowp[b];
     });
+    OIM_CUDA(dev_alloc(&p->d_shead, (size_t)p->nodes), "cudaMalloc(stream row heads)");
     std::vector<int4> srow((size_t)p->nodes);
+    std::vector<uint4> shead((size_t)p->nodes);
     for (size_t k = 0; k < sorder.size(); ++k) {
         const int32_t v = sorder[k];
         srow[k] = make_int4(v, p->h_rowp[v], p->h_split[v], p->h_rowp[v + 1]);
+        uint32_t h[4];
+        for (int u = 0; u < 4; ++u) {
+            const int64_t e = (int64_t)p->h_rowp[v] + u;
+            h[u] = e < p->h_rowp[v + 1] ? p->h_col[(size_t)e] : (uint32_t)v;
+        }
+        shead[k] = make_uint4(h[0], h[1], h[2], h[3]);
     }
     OIM_CUDA(cudaMemcpy(p->d_srow, srow.data(), srow.size() * sizeof(int4), cudaMemcpyHostToDevice),
              "upload stream rows");
+    OIM_CUDA(cudaMemcpy(p->d_shead, shead.data(), shead.size() * sizeof(uint4), cudaMemcpyHostToDevice),
+             "upload stream row heads");
     std::vector<int32_t> ng((size_t)p->nodes);
     for (int g = 0; g < p->G; ++g)
         std::fill(ng.begin() + p->graphs[g].node_off,
@@ -190,6 +200,7 @@ void free_problem(oim_problem_s* p) {
     dev_free(p->d_split);
     dev_free(p->d_order);
     dev_free(p->d_srow);
+    dev_free(p->d_shead);
     dev_free(p->d_graphs);
     dev_free(p->d_urowp);
     dev_free(p->d_ucol);

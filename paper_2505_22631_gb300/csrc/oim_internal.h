@@ -78,6 +78,9 @@ struct CSRDev {
     // every node of the batch by decreasing row length (stable): the order in which the
     // blocks take their nodes, heaviest rows first
     const int4* srow;
+    // [nodes] the first four packed column words of each slot's row, in row order (the
+    // slot's own node where the row is shorter: in bounds, never added)
+    const uint4* shead;
 };
 
 }  // namespace oim
@@ -109,11 +112,12 @@ struct oim_problem_s {
     uint32_t* d_ucol = nullptr;
     float* d_uw = nullptr;
     int4* d_srow = nullptr;        // stream-form row descriptors, heaviest rows first
+    uint4* d_shead = nullptr;      // and the first four column words of each of those rows
     int32_t max_n = 0;             // largest graph
     oim::CSRDev csr() const {
         return oim::CSRDev{d_rowp, d_col, unit_weights ? nullptr : d_w, d_node_graph, d_split,
                            d_order, d_graphs, G, (int32_t)nodes, d_urowp, d_ucol,
-                           unit_weights ? nullptr : d_uw, d_srow};
+                           unit_weights ? nullptr : d_uw, d_srow, d_shead};
     }
 };
 

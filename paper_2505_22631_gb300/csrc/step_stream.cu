@@ -34,6 +34,7 @@ struct CacheF32 {
     static constexpr bool kOwnFromCache = true;   // the plain form reads its own pairs back
     static constexpr bool kFastMath = false;      // correctly rounded sincospi, logf, sqrtf
     static constexpr int kMinBlocks = 0;          // no occupancy target (registers as the compiler likes)
+    static constexpr int kHead = 0;               // row-head columns taken from the descriptor
     __device__ static void load4(const T* p, float2 (&v)[4]) {
         const float4 a = __ldg(reinterpret_cast<const float4*>(p));
         const float4 b = __ldg(reinterpret_cast<const float4*>(p) + 1);
@@ -57,13 +58,19 @@ struct Cache16 {
     // 32 registers, 8 blocks of 256 per SM: more warps to cover the gathers' latency
     // (measured 200 -> 177 us per step on the 16-graph uneven batch)
     static constexpr int kMinBlocks = 8;
+    // the first entries of a row come from the slot's head descriptor, so their pair
+    // loads start one dependent load earlier (a row of 4 needs no column load)
+    static constexpr int kHead = 2;
+    static constexpr int kHeadMixed = 3;
     __device__ static float2 to_f2(H2 h);
     __device__ static H2 from_f2(float2 f);
-    __device__ static void load4(const T* p, float2 (&v)[4]) {
-        const uint4 a = __ldg(reinterpret_cast<const uint4*>(p));
+    __device__ static void cvt4(uint4 a, float2 (&v)[4]) {
         const uint32_t w[4] = {a.x, a.y, a.z, a.w};
 #pragma unroll
         for (int k = 0; k < 4; ++k) v[k] = to_f2(*reinterpret_cast<const H2*>(&w[k]));
+    }
+    __device__ static void load4(const T* p, float2 (&v)[4]) {
+        cvt4(__ldg(reinterpret_cast<const uint4*>(p)), v);
     }
     __device__ static void store4(T* p, const float2 (&v)[4]) {
         uint32_t w[4];
@@ -171,28 +178,68 @@ __global__ void __launch_bounds__(256, kMixed ? 6 : C::kMinBlocks) step_stream_k
 #pragma unroll
     for (int v = 0; v < 4; ++v) acc[v] = make_float2(0.f, 0.f);
     const int e_beg = row.y, e_end = row.w;
+    auto negate = [&]() {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[v] = make_float2(-acc[v].x, -acc[v].y);
+    };
+    // neighbour pairs of the quad: a row of the 16-bit cache is R_pad / 4 groups of 16 bytes
+    const uint4* cs16 = reinterpret_cast<const uint4*>(cs_in) + quad;
+    const size_t rs16 = (size_t)(P.R_pad >> 2);
     if constexpr (kMixed) {
         // +-1 weights, 16-bit pairs: rows hold the +1 entries first; mixed f16 + f32 adds
         // (one rounding each, as the FMA by +-1 would give), the -1 run accumulated with
-        // the accumulator negated: -(-acc + x) = acc - x in round-to-nearest
+        // the accumulator negated: -(-acc + x) = acc - x in round-to-nearest.  Entries are
+        // added in row order; the accumulator is negated at the first -1 entry and back
+        // after the last one.
         using H2 = typename C::T;
+        constexpr int kH = C::kHeadMixed;
         const int e_split = row.z;
-        for (int e = e_beg; e < e_split; ++e) {
-            const uint32_t j = __ldg(csr.col + e) & ~kSignBit;
-            add_raw4<H2>(acc, __ldg(reinterpret_cast<const uint4*>(cs_in + (size_t)j * P.R_pad + 4 * quad)));
-        }
-        if (e_split < e_end) {
+        if constexpr (kH > 0) {
+            const uint4 hd = __ldg(csr.shead + slot);
+            const uint32_t hc[4] = {hd.x, hd.y, hd.z, hd.w};
+            uint4 hq[kH > 0 ? kH : 1];
 #pragma unroll
-            for (int v = 0; v < 4; ++v) acc[v] = make_float2(-acc[v].x, -acc[v].y);
-            for (int e = e_split; e < e_end; ++e) {
-                const uint32_t j = __ldg(csr.col + e) & ~kSignBit;
-                add_raw4<H2>(acc, __ldg(reinterpret_cast<const uint4*>(cs_in + (size_t)j * P.R_pad + 4 * quad)));
+            for (int u = 0; u < kH; ++u) hq[u] = __ldg(cs16 + (size_t)(hc[u] & ~kSignBit) * rs16);
+#pragma unroll
+            for (int u = 0; u < kH; ++u) {
+                if (e_beg + u < e_end) {
+                    if (e_beg + u == e_split) negate();
+                    add_raw4<H2>(acc, hq[u]);
+                }
             }
-#pragma unroll
-            for (int v = 0; v < 4; ++v) acc[v] = make_float2(-acc[v].x, -acc[v].y);
         }
-    } else
-    for (int e = e_beg; e < e_end; ++e) {
+        int e = e_beg + kH;
+        for (; e < e_split; ++e) {
+            const uint32_t j = __ldg(csr.col + e) & ~kSignBit;
+            add_raw4<H2>(acc, __ldg(cs16 + (size_t)j * rs16));
+        }
+        if (e_split >= e_beg + kH && e_split < e_end) negate();
+        for (; e < e_end; ++e) {
+            const uint32_t j = __ldg(csr.col + e) & ~kSignBit;
+            add_raw4<H2>(acc, __ldg(cs16 + (size_t)j * rs16));
+        }
+        if (e_split < e_end) negate();
+    } else {
+    constexpr int kH = C::kHead;
+    if constexpr (kH > 0) {
+        const uint4 hd = __ldg(csr.shead + slot);
+        const uint32_t hc[4] = {hd.x, hd.y, hd.z, hd.w};
+        uint4 hq[kH > 0 ? kH : 1];
+#pragma unroll
+        for (int u = 0; u < kH; ++u) hq[u] = __ldg(cs16 + (size_t)(hc[u] & ~kSignBit) * rs16);
+#pragma unroll
+        for (int u = 0; u < kH; ++u) {
+            if (e_beg + u < e_end) {
+                const float w = kUnit ? ((hc[u] & kSignBit) ? -1.0f : 1.0f) : __ldg(csr.w + e_beg + u);
+                float2 nb[4];
+                C::cvt4(hq[u], nb);
+                const float2 ww = make_float2(w, w);
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[v] = ffma2(nb[v], ww, acc[v]);
+            }
+        }
+    }
+    for (int e = e_beg + kH; e < e_end; ++e) {
         const uint32_t cw = __ldg(csr.col + e);
         float w;
         uint32_t j;
@@ -208,6 +255,7 @@ __global__ void __launch_bounds__(256, kMixed ? 6 : C::kMinBlocks) step_stream_k
         const float2 ww = make_float2(w, w);
 #pragma unroll
         for (int v = 0; v < 4; ++v) acc[v] = ffma2(nb[v], ww, acc[v]);
+    }
     }
 
     // the 16-bit forms' own (cos, sin) in FP32 from the phases, after the gather, so the
