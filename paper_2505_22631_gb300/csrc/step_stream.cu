@@ -162,17 +162,6 @@ __global__ void __launch_bounds__(256, kMixed ? 6 : C::kMinBlocks) step_stream_k
     if (slot >= csr.nodes || quad >= quads) return;
     const int4 row = __ldg(csr.srow + slot);   // {node, row start, first -1 entry, row end}
     const int node = row.x;
-    const int g = csr.node_graph[node];
-    const int i = node - csr.graphs[g].node_off;
-    const int64_t t = d_t0 ? (int64_t)(*d_t0) + t_add : t_fixed;
-    const size_t sidx = (size_t)g * P.steps + t;
-    const float K = __ldg(P.K + sidx), Ks = __ldg(P.Ks + sidx), Kn = __ldg(P.Kn + sidx);
-
-    const size_t at = (size_t)node * P.R_pad + 4 * quad;
-    const float4 th = *reinterpret_cast<const float4*>(th_in + at);
-    const float t0[4] = {th.x, th.y, th.z, th.w};
-    float2 own[4];
-    if (C::kOwnFromCache) C::load4(cs_in + at, own);
 
     float2 acc[4];
 #pragma unroll
@@ -258,9 +247,19 @@ __global__ void __launch_bounds__(256, kMixed ? 6 : C::kMinBlocks) step_stream_k
     }
     }
 
-    // the 16-bit forms' own (cos, sin) in FP32 from the phases, after the gather, so the
-    // phase load's latency overlaps the neighbour loads
-    if (!C::kOwnFromCache) {
+    // the node's own state after the gather: only the gather's state is live during it
+    const int g = csr.node_graph[node];
+    const int i = node - csr.graphs[g].node_off;
+    const int64_t t = d_t0 ? (int64_t)(*d_t0) + t_add : t_fixed;
+    const size_t sidx = (size_t)g * P.steps + t;
+    const float K = __ldg(P.K + sidx), Ks = __ldg(P.Ks + sidx), Kn = __ldg(P.Kn + sidx);
+    const size_t at = (size_t)node * P.R_pad + 4 * quad;
+    const float4 th = *reinterpret_cast<const float4*>(th_in + at);
+    const float t0[4] = {th.x, th.y, th.z, th.w};
+    float2 own[4];
+    if (C::kOwnFromCache) {
+        C::load4(cs_in + at, own);
+    } else {
 #pragma unroll
         for (int v = 0; v < 4; ++v) own[v] = cos_sin_2pi_fast(t0[v]);
     }
