@@ -60,8 +60,8 @@ struct Cache16 {
     static constexpr int kMinBlocks = 8;
     // the first entries of a row come from the slot's head descriptor, so their pair
     // loads start one dependent load earlier (a row of 4 needs no column load)
-    static constexpr int kHead = 2;
-    static constexpr int kHeadMixed = 3;
+    static constexpr int kHead = 3;
+    static constexpr int kHeadMixed = 4;
     __device__ static float2 to_f2(H2 h);
     __device__ static H2 from_f2(float2 f);
     __device__ static void cvt4(uint4 a, float2 (&v)[4]) {
