@@ -34,7 +34,7 @@ struct CacheF32 {
     static constexpr bool kOwnFromCache = true;   // the plain form reads its own pairs back
     static constexpr bool kFastMath = false;      // correctly rounded sincospi, logf, sqrtf
     static constexpr int kMinBlocks = 0;          // no occupancy target (registers as the compiler likes)
-    static constexpr int kHead = 0;               // row-head columns taken from the descriptor
+    static constexpr int kHead = 2;               // row-head entries taken from the descriptor
     __device__ static void load4(const T* p, float2 (&v)[4]) {
         const float4 a = __ldg(reinterpret_cast<const float4*>(p));
         const float4 b = __ldg(reinterpret_cast<const float4*>(p) + 1);
@@ -210,7 +210,24 @@ __global__ void __launch_bounds__(256, kMixed ? 6 : C::kMinBlocks) step_stream_k
         if (e_split < e_end) negate();
     } else {
     constexpr int kH = C::kHead;
-    if constexpr (kH > 0) {
+    if constexpr (kH > 0 && C::kOwnFromCache) {
+        // FP32 pairs: the head entries' pairs are read as floats
+        const uint4 hd = __ldg(csr.shead + slot);
+        const uint32_t hc[4] = {hd.x, hd.y, hd.z, hd.w};
+        float2 hv[kH > 0 ? kH : 1][4];
+#pragma unroll
+        for (int u = 0; u < kH; ++u)
+            C::load4(cs_in + (size_t)(hc[u] & ~kSignBit) * P.R_pad + 4 * quad, hv[u]);
+#pragma unroll
+        for (int u = 0; u < kH; ++u) {
+            if (e_beg + u < e_end) {
+                const float w = kUnit ? ((hc[u] & kSignBit) ? -1.0f : 1.0f) : __ldg(csr.w + e_beg + u);
+                const float2 ww = make_float2(w, w);
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[v] = ffma2(hv[u][v], ww, acc[v]);
+            }
+        }
+    } else if constexpr (kH > 0) {
         const uint4 hd = __ldg(csr.shead + slot);
         const uint32_t hc[4] = {hd.x, hd.y, hd.z, hd.w};
         uint4 hq[kH > 0 ? kH : 1];
