@@ -26,6 +26,8 @@ int cuda_fail(cudaError_t e, const char* what) {
 
 // implemented in the kernel translation units
 cudaError_t launch_score(const oim_run_s& r, const float* theta, int64_t k, cudaStream_t s);
+cudaError_t launch_score_at(const oim_run_s& r, const float* theta, int64_t k, const int32_t* d_t0,
+                            int32_t t_add, cudaStream_t s);
 cudaError_t launch_finalize(const oim_run_s& r, int64_t k, double* score, cudaStream_t s);
 cudaError_t launch_energy_of(const oim_run_s& r, const float* theta, double* energy, cudaStream_t s);
 cudaError_t launch_gather(const oim_run_s& r, const float* theta, int8_t* spins, float* th_out,
@@ -42,6 +44,7 @@ int gemm_setup(oim_run_s& r);
 void gemm_free(oim_run_s& r);
 cudaError_t launch_gemm_init(const oim_run_s& r, cudaStream_t s);
 cudaError_t launch_set_seed(uint64_t* d_seed, uint64_t seed, cudaStream_t s);
+cudaError_t launch_advance_t0(int32_t* d_t0, int32_t steps, cudaStream_t s);
 cudaError_t launch_gemm_step(const oim_run_s& r, int64_t t, cudaStream_t s);
 cudaError_t launch_gemm_to_common(const oim_run_s& r, float* out, cudaStream_t s);
 cudaError_t launch_adj_prep(const oim_run_s& r, const float* theta, const float* lam, float4* Y,
@@ -237,6 +240,8 @@ void free_run_buffers(oim_run_s* r) {
     gemm_free(*r);
     if (r->chunk_exec) cudaGraphExecDestroy(r->chunk_exec);
     r->chunk_exec = nullptr;
+    if (r->step_chunk_exec) cudaGraphExecDestroy(r->step_chunk_exec);
+    r->step_chunk_exec = nullptr;
 }
 
 int validate_schedule_args(float dt, int64_t steps) {
@@ -245,11 +250,23 @@ int validate_schedule_args(float dt, int64_t steps) {
     return OIM_OK;
 }
 
+// Captured graphs hold the buffer pointers and strides of the run: any reallocation
+// below drops them (they are captured again when needed).
+static void drop_graphs(oim_run_s* r) {
+    if (r->chunk_exec) cudaGraphExecDestroy(r->chunk_exec);
+    r->chunk_exec = nullptr;
+    r->graph_steps = -1;
+    if (r->step_chunk_exec) cudaGraphExecDestroy(r->step_chunk_exec);
+    r->step_chunk_exec = nullptr;
+    r->step_chunk_len = 0;
+}
+
 // (Re)allocate the buffers whose size depends on steps / readouts.
 int ensure_step_buffers(oim_run_s* r, int64_t steps) {
     const int G = r->p->G;
     const int64_t n_ro = r->readout_every > 0 ? steps / r->readout_every : 0;
     if (steps > r->steps_cap || !r->d_sched) {
+        drop_graphs(r);
         dev_free(r->d_sched);
         r->steps_cap = std::max<int64_t>(steps, 1);
         OIM_CUDA(dev_alloc(&r->d_sched, (size_t)3 * G * r->steps_cap), "cudaMalloc(schedules)");
@@ -257,6 +274,7 @@ int ensure_step_buffers(oim_run_s* r, int64_t steps) {
     if (r->ckpt_every > 0) {
         const int64_t need = steps / r->ckpt_every + 1;
         if (need > r->ckpt_cap || !r->d_ckpt) {
+            drop_graphs(r);
             dev_free(r->d_ckpt);
             r->ckpt_cap = need;
             OIM_CUDA(dev_alloc(&r->d_ckpt, (size_t)need * r->p->nodes * r->R_pad), "cudaMalloc(checkpoints)");
@@ -264,6 +282,7 @@ int ensure_step_buffers(oim_run_s* r, int64_t steps) {
     }
     const int64_t ro_need = n_ro + 1;   // one extra row for the final scores
     if (ro_need > r->readouts_cap || !r->d_trace) {
+        drop_graphs(r);
         dev_free(r->d_trace);
         r->readouts_cap = ro_need;
         OIM_CUDA(dev_alloc(&r->d_trace, (size_t)G * r->readouts_cap * r->R_pad), "cudaMalloc(trace)");
@@ -359,6 +378,67 @@ int allocate_run(oim_run_s* r) {
     return OIM_OK;
 }
 
+// Steps per replay of a captured chunk: the readout period (so each chunk ends on a
+// readout), doubled until it is even (the buffer parity follows the step index) and at
+// least 32 steps; 0 where chunks do not apply (the dense form, checkpointed runs, runs
+// shorter than a chunk).
+int64_t step_chunk_length(const oim_run_s& r) {
+    if (r.form != OIM_FORM_STREAM || r.ckpt_every > 0) return 0;
+    int64_t L = r.readout_every > 0 ? r.readout_every : 64;
+    while ((L & 1) || L < 32) L *= 2;
+    return (L <= r.steps && L <= (1 << 20)) ? L : 0;
+}
+
+// The CSR stream form as init, steps / L replays of one captured chunk of L steps and
+// its score passes (steps and readout slots read from the device step base, which the
+// chunk's last node moves on by L), and the remaining steps launched directly.  The
+// chunk is captured once per (L, dt, readout period) and kept with the run.
+int enqueue_stream_chunks(oim_run_s* r, int64_t L) {
+    cudaStream_t s = r->stream;
+    cudaError_t e = launch_init_stream(*r, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(r->d_t0, 0, sizeof(int32_t), s);
+    if (e != cudaSuccess) return cuda_fail(e, "stream-form launch");
+    if (!r->step_chunk_exec || r->step_chunk_len != L || r->step_chunk_dt != r->dt ||
+        r->step_chunk_every != r->readout_every) {
+        if (r->step_chunk_exec) cudaGraphExecDestroy(r->step_chunk_exec);
+        r->step_chunk_exec = nullptr;
+        cudaStream_t cap = nullptr;
+        OIM_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "create capture stream");
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            for (int64_t m = 0; m < L && e == cudaSuccess; ++m) {
+                e = launch_step_stream(*r, m, r->d_t0, cap);
+                if (e == cudaSuccess && r->readout_every > 0 && (m + 1) % r->readout_every == 0)
+                    e = launch_score_at(*r, r->d_theta[(m + 1) & 1], 0, r->d_t0, (int32_t)(m + 1), cap);
+            }
+            if (e == cudaSuccess) e = launch_advance_t0(r->d_t0, (int32_t)L, cap);
+            cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+            if (e == cudaSuccess) e = e2;
+        }
+        cudaStreamDestroy(cap);
+        if (e != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return cuda_fail(e, "capture step chunk");
+        }
+        e = cudaGraphInstantiate(&r->step_chunk_exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(e, "instantiate step chunk");
+        r->step_chunk_len = L;
+        r->step_chunk_dt = r->dt;
+        r->step_chunk_every = r->readout_every;
+    }
+    const int64_t chunks = r->steps / L;
+    for (int64_t c = 0; c < chunks; ++c) OIM_CUDA(cudaGraphLaunch(r->step_chunk_exec, s), "chunk launch");
+    for (int64_t t = chunks * L; t < r->steps && e == cudaSuccess; ++t) {
+        e = launch_step_stream(*r, t, nullptr, s);
+        if (e == cudaSuccess && r->readout_every > 0 && (t + 1) % r->readout_every == 0)
+            e = launch_score(*r, r->d_theta[(t + 1) & 1], (t + 1) / r->readout_every - 1, s);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "stream-form launch");
+    return OIM_OK;
+}
+
 // Queue the stream form: init, then every step, with a score pass after each
 // readout step.  When capture is on, the whole sequence is recorded once into a
 // CUDA graph (kernel arguments baked in) and replayed on later identical runs.
@@ -401,11 +481,15 @@ int enqueue_stream_form(oim_run_s* r) {
     // the seed is read from device memory, so one graph serves every seed
     const bool same = r->chunk_exec && r->graph_steps == r->steps && r->graph_dt == r->dt;
     if (!same && (r->seen_steps != r->steps || r->seen_dt != r->dt)) {
-        // first execution of this shape: launch directly (the GPU runs while the host
-        // queues; capturing and instantiating thousands of nodes would cost more than
-        // it saves for a run made once), and capture if the shape comes back
+        // first execution of this shape: capturing and instantiating thousands of nodes
+        // would cost more than it saves for a run made once, so the CSR stream form
+        // replays a short captured chunk of steps (its step base in device memory) and
+        // the other cases launch directly; the whole run is captured if the shape
+        // comes back
         r->seen_steps = r->steps;
         r->seen_dt = r->dt;
+        const int64_t L = step_chunk_length(*r);
+        if (L > 0) return enqueue_stream_chunks(r, L);
         cudaError_t e = body(r->stream);
         if (e != cudaSuccess) return cuda_fail(e, "stream-form launch");
         return OIM_OK;

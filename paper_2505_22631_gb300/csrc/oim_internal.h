@@ -156,6 +156,11 @@ struct oim_run_s {
     float graph_dt = 0.f;
     int64_t seen_steps = -1;                  // shape of the last direct execution
     float seen_dt = 0.f;
+    // a replayable chunk of steps (step base in d_t0) for first executions
+    cudaGraphExec_t step_chunk_exec = nullptr;
+    int64_t step_chunk_len = 0;
+    float step_chunk_dt = 0.f;
+    int64_t step_chunk_every = -1;
     int32_t* d_t0 = nullptr;                  // device step counter (graph replays)
     // adjoint support: phases every ckpt_every steps ([n_ckpt][nodes][R_pad])
     int32_t ckpt_every = 0;

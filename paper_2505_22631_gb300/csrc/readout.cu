@@ -40,8 +40,10 @@ constexpr int kScoreQuads = 32, kScoreLanes = 8;
 
 __global__ void __launch_bounds__(kScoreQuads * kScoreLanes) score_kernel(
     CSRDev csr, const int8_t* __restrict__ spins, int R_pad, double* __restrict__ agree, int64_t row_stride,
-    int64_t k, int npt) {
+    int64_t k_fixed, int npt, const int32_t* __restrict__ d_t0, int32_t t_add, int32_t every) {
     __shared__ double red[kScoreLanes][kScoreQuads][4];
+    // readout slot: fixed, or (in a replayed chunk of steps) from the device step base
+    const int64_t k = d_t0 ? ((int64_t)(*d_t0) + t_add) / every - 1 : k_fixed;
     const int quads = R_pad >> 2;
     const int quad = blockIdx.x * kScoreQuads + threadIdx.x;
     const bool valid = quad < quads;      // no early exit: the block synchronises below
@@ -211,7 +213,16 @@ int nodes_per_thread(const oim_run_s& r) {
 
 }  // namespace
 
+cudaError_t launch_score_at(const oim_run_s& r, const float* theta, int64_t k, const int32_t* d_t0,
+                            int32_t t_add, cudaStream_t s);
+
 cudaError_t launch_score(const oim_run_s& r, const float* theta, int64_t k, cudaStream_t s) {
+    return launch_score_at(r, theta, k, nullptr, 0, s);
+}
+
+// With d_t0 the readout slot is (*d_t0 + t_add) / readout_every - 1, read on the device.
+cudaError_t launch_score_at(const oim_run_s& r, const float* theta, int64_t k, const int32_t* d_t0,
+                            int32_t t_add, cudaStream_t s) {
     const int64_t quads_total = (int64_t)r.p->nodes * (r.R_pad / 4);
     spin_kernel<<<(unsigned)((quads_total + 255) / 256), 256, 0, s>>>(theta, quads_total, r.p->q, r.d_spins);
     const int quads = r.R_pad / 4;
@@ -219,7 +230,8 @@ cudaError_t launch_score(const oim_run_s& r, const float* theta, int64_t k, cuda
     const int chunk = kScoreLanes * npt;
     dim3 block(kScoreQuads, kScoreLanes);
     dim3 grid((quads + kScoreQuads - 1) / kScoreQuads, (unsigned)((r.p->nodes + chunk - 1) / chunk));
-    score_kernel<<<grid, block, 0, s>>>(r.p->csr(), r.d_spins, r.R_pad, r.d_trace, r.readouts_cap, k, npt);
+    score_kernel<<<grid, block, 0, s>>>(r.p->csr(), r.d_spins, r.R_pad, r.d_trace, r.readouts_cap, k, npt,
+                                        d_t0, t_add, (int32_t)std::max<int64_t>(1, r.readout_every));
     return cudaGetLastError();
 }
 

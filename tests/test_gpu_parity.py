@@ -205,6 +205,44 @@ def test_stream_graph_capture_matches_direct_launches(c1):
     assert np.array_equal(a.readout()["trace"], b.readout()["trace"])
 
 
+@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+def test_stream_chunked_first_execution_matches_direct_launches(orc, precision):
+    """A run's first execution replays a captured chunk of steps (step base and readout
+    slot read from device memory) and launches the remaining steps directly: phases,
+    trace and scores equal those of plain direct launches bit for bit, also after a
+    rerun that grows the run (its buffers, and with them the chunk, are made again)."""
+    g0 = erdos_renyi(400, 0.04, 5, "pm1")
+    g1 = torus(12, 10, 6, "pm1")
+    K = [constant(400, 4.0 / g.mean_degree) for g in (g0, g1)]
+    Ks, Kn = linear_ramp(400, 0, 1), constant(400, 0.1)
+    R = 64
+    # readout every 25 steps: chunks of 50; 130 steps = 2 chunks and a 30-step tail
+    # holding one readout, 260 steps = 5 chunks and a 10-step tail
+    a = gpu_run([g0, g1], 2, [k[:130] for k in K], Ks[:130], Kn[:130], 0.01, 130, R, 3,
+                form="stream", precision=precision, readout_every=25, use_graph=True)
+    b = gpu_run([g0, g1], 2, [k[:130] for k in K], Ks[:130], Kn[:130], 0.01, 130, R, 3,
+                form="stream", precision=precision, readout_every=25, use_graph=False)
+
+    def same(x, y):
+        px, py = x.phases(), y.phases()
+        for gi in range(2):
+            assert np.array_equal(px[gi], py[gi])
+        ox, oy = x.readout(), y.readout()
+        assert np.array_equal(ox["trace"], oy["trace"])
+        assert np.array_equal(ox["score"], oy["score"])
+        return ox
+
+    out = same(a, b)
+    assert out["trace"].shape[1] == 130 // 25
+    for gi, g in enumerate((g0, g1)):
+        th = a.phases()[gi]
+        assert np.array_equal(out["score"][gi], orc.scores(g, 2, orc.readout_f32(2, th)))
+    for steps, seed in ((260, 4), (260, 5)):   # the second pass replays the captured run
+        a.rerun([k[:steps] for k in K], Ks[:steps], Kn[:steps], 0.01, steps, seed)
+        b.rerun([k[:steps] for k in K], Ks[:steps], Kn[:steps], 0.01, steps, seed)
+        same(a, b)
+
+
 @pytest.mark.parametrize("form", FORMS)
 def test_batch_uses_graph_index_streams(orc, form):
     g0 = erdos_renyi(300, 0.05, 1, "+1")
