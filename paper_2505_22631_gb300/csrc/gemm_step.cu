@@ -38,7 +38,8 @@ struct GemmArgs {
     const float* K;             // schedules of this graph, indexed by t
     const float* Ks;
     const float* Kn;
-    int64_t t;
+    int64_t t;                  // the step, or its offset from *t0 when t0 is set
+    const int32_t* t0;          // step base in device memory (a replayed chunk of steps)
     float dt, sqrt_dt;
     const uint64_t* seed;       // device copy of the run's seed (graph replays serve any seed)
     int32_t graph, q, n, n_pad;
@@ -152,7 +153,8 @@ __global__ void __launch_bounds__(TileShape<BN>::kThreads, TileShape<BN>::kMinBl
         const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16);
         const int row = m0 + quad * 32 + lane;            // row of X^T: 2 r + comp
         const int r = row >> 1, comp = row & 1;
-        const float K = __ldg(a.K + a.t), Ks = __ldg(a.Ks + a.t), Kn = __ldg(a.Kn + a.t);
+        const int64_t t = a.t0 ? (int64_t)(*a.t0) + a.t : a.t;
+        const float K = __ldg(a.K + t), Ks = __ldg(a.Ks + t), Kn = __ldg(a.Kn + t);
         const float dtK = a.dt * K, dtKs = a.dt * Ks, kick = Kn * a.sqrt_dt;
         float* th_row = a.theta + (size_t)r * a.n_pad;
         const unsigned full_mask = 0xffffffffu;
@@ -178,9 +180,9 @@ __global__ void __launch_bounds__(TileShape<BN>::kThreads, TileShape<BN>::kMinBl
             const uint32_t rq = (uint32_t)(r >> 2);
             const uint64_t seed = *a.seed;
             const uint4 blk0 = draw_block(seed, (uint32_t)a.graph, kStreamNoise, (uint32_t)(i0 + rho),
-                                          (uint32_t)a.t, rq);
+                                          (uint32_t)t, rq);
             const uint4 blk1 = draw_block(seed, (uint32_t)a.graph, kStreamNoise, (uint32_t)(i0 + rho + 4),
-                                          (uint32_t)a.t, rq);
+                                          (uint32_t)t, rq);
             uint32_t vb[8], vcs[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
@@ -387,7 +389,15 @@ cudaError_t launch_gemm_init(const oim_run_s& r, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+cudaError_t launch_gemm_step_at(const oim_run_s& r, int64_t t, const int32_t* d_t0, cudaStream_t s);
+
 cudaError_t launch_gemm_step(const oim_run_s& r, int64_t t, cudaStream_t s) {
+    return launch_gemm_step_at(r, t, nullptr, s);
+}
+
+// With d_t0 the step is *d_t0 + t (t the offset in a replayed chunk, whose parity is
+// the step's: chunks have an even length).
+cudaError_t launch_gemm_step_at(const oim_run_s& r, int64_t t, const int32_t* d_t0, cudaStream_t s) {
     const GemmState& st = r.gemm;
     const StepParams P = make_params(r);
     GemmArgs a;
@@ -397,6 +407,7 @@ cudaError_t launch_gemm_step(const oim_run_s& r, int64_t t, cudaStream_t s) {
     a.Ks = P.Ks;
     a.Kn = P.Kn;
     a.t = t;
+    a.t0 = d_t0;
     a.dt = P.dt;
     a.sqrt_dt = P.sqrt_dt;
     a.seed = r.d_seed;

@@ -46,6 +46,7 @@ cudaError_t launch_gemm_init(const oim_run_s& r, cudaStream_t s);
 cudaError_t launch_set_seed(uint64_t* d_seed, uint64_t seed, cudaStream_t s);
 cudaError_t launch_advance_t0(int32_t* d_t0, int32_t steps, cudaStream_t s);
 cudaError_t launch_gemm_step(const oim_run_s& r, int64_t t, cudaStream_t s);
+cudaError_t launch_gemm_step_at(const oim_run_s& r, int64_t t, const int32_t* d_t0, cudaStream_t s);
 cudaError_t launch_gemm_to_common(const oim_run_s& r, float* out, cudaStream_t s);
 cudaError_t launch_adj_prep(const oim_run_s& r, const float* theta, const float* lam, float4* Y,
                             cudaStream_t s);
@@ -380,22 +381,34 @@ int allocate_run(oim_run_s* r) {
 
 // Steps per replay of a captured chunk: the readout period (so each chunk ends on a
 // readout), doubled until it is even (the buffer parity follows the step index) and at
-// least 32 steps; 0 where chunks do not apply (the dense form, checkpointed runs, runs
-// shorter than a chunk).
+// least 32 steps; 0 where chunks do not apply (checkpointed runs, runs shorter than a
+// chunk).
 int64_t step_chunk_length(const oim_run_s& r) {
-    if (r.form != OIM_FORM_STREAM || r.ckpt_every > 0) return 0;
+    if ((r.form != OIM_FORM_STREAM && r.form != OIM_FORM_GEMM) || r.ckpt_every > 0) return 0;
     int64_t L = r.readout_every > 0 ? r.readout_every : 64;
     while ((L & 1) || L < 32) L *= 2;
     return (L <= r.steps && L <= (1 << 20)) ? L : 0;
 }
 
-// The CSR stream form as init, steps / L replays of one captured chunk of L steps and
-// its score passes (steps and readout slots read from the device step base, which the
+// A per-step form as init, steps / L replays of one captured chunk of L steps and its
+// score passes (steps and readout slots read from the device step base, which the
 // chunk's last node moves on by L), and the remaining steps launched directly.  The
 // chunk is captured once per (L, dt, readout period) and kept with the run.
 int enqueue_stream_chunks(oim_run_s* r, int64_t L) {
     cudaStream_t s = r->stream;
-    cudaError_t e = launch_init_stream(*r, s);
+    const bool dense = r->form == OIM_FORM_GEMM;
+    // one step (offset t from *d_t0, or the step t itself) and, where a readout falls,
+    // its score pass (the dense form first copies its phases to the common layout)
+    auto step = [&](int64_t t, const int32_t* d_t0, cudaStream_t q) -> cudaError_t {
+        cudaError_t x = dense ? launch_gemm_step_at(*r, t, d_t0, q) : launch_step_stream(*r, t, d_t0, q);
+        if (x != cudaSuccess || r->readout_every <= 0 || (t + 1) % r->readout_every != 0) return x;
+        float* th = dense ? r->d_theta[0] : r->d_theta[(t + 1) & 1];
+        if (dense) x = launch_gemm_to_common(*r, th, q);
+        if (x != cudaSuccess) return x;
+        return d_t0 ? launch_score_at(*r, th, 0, d_t0, (int32_t)(t + 1), q)
+                    : launch_score(*r, th, (t + 1) / r->readout_every - 1, q);
+    };
+    cudaError_t e = dense ? launch_gemm_init(*r, s) : launch_init_stream(*r, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(r->d_t0, 0, sizeof(int32_t), s);
     if (e != cudaSuccess) return cuda_fail(e, "stream-form launch");
     if (!r->step_chunk_exec || r->step_chunk_len != L || r->step_chunk_dt != r->dt ||
@@ -407,11 +420,7 @@ int enqueue_stream_chunks(oim_run_s* r, int64_t L) {
         cudaGraph_t graph = nullptr;
         e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            for (int64_t m = 0; m < L && e == cudaSuccess; ++m) {
-                e = launch_step_stream(*r, m, r->d_t0, cap);
-                if (e == cudaSuccess && r->readout_every > 0 && (m + 1) % r->readout_every == 0)
-                    e = launch_score_at(*r, r->d_theta[(m + 1) & 1], 0, r->d_t0, (int32_t)(m + 1), cap);
-            }
+            for (int64_t m = 0; m < L && e == cudaSuccess; ++m) e = step(m, r->d_t0, cap);
             if (e == cudaSuccess) e = launch_advance_t0(r->d_t0, (int32_t)L, cap);
             cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
             if (e == cudaSuccess) e = e2;
@@ -430,11 +439,8 @@ int enqueue_stream_chunks(oim_run_s* r, int64_t L) {
     }
     const int64_t chunks = r->steps / L;
     for (int64_t c = 0; c < chunks; ++c) OIM_CUDA(cudaGraphLaunch(r->step_chunk_exec, s), "chunk launch");
-    for (int64_t t = chunks * L; t < r->steps && e == cudaSuccess; ++t) {
-        e = launch_step_stream(*r, t, nullptr, s);
-        if (e == cudaSuccess && r->readout_every > 0 && (t + 1) % r->readout_every == 0)
-            e = launch_score(*r, r->d_theta[(t + 1) & 1], (t + 1) / r->readout_every - 1, s);
-    }
+    for (int64_t t = chunks * L; t < r->steps && e == cudaSuccess; ++t) e = step(t, nullptr, s);
+    if (e == cudaSuccess && dense) e = launch_gemm_to_common(*r, r->d_theta[0], s);
     if (e != cudaSuccess) return cuda_fail(e, "stream-form launch");
     return OIM_OK;
 }
@@ -482,10 +488,9 @@ int enqueue_stream_form(oim_run_s* r) {
     const bool same = r->chunk_exec && r->graph_steps == r->steps && r->graph_dt == r->dt;
     if (!same && (r->seen_steps != r->steps || r->seen_dt != r->dt)) {
         // first execution of this shape: capturing and instantiating thousands of nodes
-        // would cost more than it saves for a run made once, so the CSR stream form
-        // replays a short captured chunk of steps (its step base in device memory) and
-        // the other cases launch directly; the whole run is captured if the shape
-        // comes back
+        // would cost more than it saves for a run made once, so the run replays a short
+        // captured chunk of steps (its step base in device memory; checkpointed runs
+        // launch directly); the whole run is captured if the shape comes back
         r->seen_steps = r->steps;
         r->seen_dt = r->dt;
         const int64_t L = step_chunk_length(*r);

@@ -82,6 +82,35 @@ def test_dense_graph_capture_matches_direct(R):
     assert np.array_equal(a, b)
 
 
+def test_dense_chunked_first_execution_matches_direct(orc):
+    """The dense form's first execution replays a captured chunk of steps (step base and
+    readout slot read from device memory) and launches the remaining steps directly:
+    phases, trace and scores equal those of direct launches bit for bit, also after a
+    rerun that grows the run."""
+    g = erdos_renyi(500, 0.08, 4, "pm1")
+    R = 128
+    K, Ks, Kn = constant(300, 0.2), linear_ramp(300, 0, 1), constant(300, 0.1)
+    # readout every 25 steps: chunks of 50; 130 steps = 2 chunks and a 30-step tail
+    a = gpu_run(g, 2, K[:130], Ks[:130], Kn[:130], 0.01, 130, R, 3, form="gemm", precision="bf16",
+                readout_every=25, use_graph=True)
+    b = gpu_run(g, 2, K[:130], Ks[:130], Kn[:130], 0.01, 130, R, 3, form="gemm", precision="bf16",
+                readout_every=25, use_graph=False)
+
+    def same(x, y):
+        assert np.array_equal(x.phases()[0], y.phases()[0])
+        ox, oy = x.readout(), y.readout()
+        assert np.array_equal(ox["trace"], oy["trace"])
+        assert np.array_equal(ox["score"], oy["score"])
+        return ox
+
+    out = same(a, b)
+    assert np.array_equal(out["score"][0], orc.scores(g, 2, orc.readout_f32(2, a.phases()[0])))
+    for steps, seed in ((300, 4), (300, 5)):   # the second pass replays the captured run
+        a.rerun(K[:steps], Ks[:steps], Kn[:steps], 0.01, steps, seed)
+        b.rerun(K[:steps], Ks[:steps], Kn[:steps], 0.01, steps, seed)
+        same(a, b)
+
+
 def test_dense_real_valued_all_to_all_coupling_within_1e2_per_row(orc):
     # Gaussian couplings on every pair: the BF16 operands still meet the per-row bound
     g = sherrington_kirkpatrick(384, 11)
