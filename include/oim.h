@@ -82,11 +82,10 @@ typedef struct oim_run_opts {
     void*   stream;             /* cudaStream_t to queue the work on               */
     int32_t use_graph;          /* per-step forms: replay a repeated run shape     */
                                 /* from a CUDA graph.  Its first run replays a     */
-                                /* captured chunk of steps (CSR stream form        */
-                                /* without checkpoints: one readout period, made   */
-                                /* even and at least 32 steps) and launches the    */
-                                /* rest directly; the dense form and checkpointed  */
-                                /* runs launch their first run directly            */
+                                /* captured chunk of steps (one readout period,    */
+                                /* made even and at least 32 steps) and launches   */
+                                /* the rest directly; checkpointed runs launch     */
+                                /* their first run directly                        */
     int32_t replicas_per_block; /* resident form: 0 = chosen by the library        */
     int32_t threads_per_block;  /* 0 = chosen by the library; resident form: block */
                                 /* size; dense form: 320 (128-wide tiles) or 576  */
