@@ -624,16 +624,24 @@ int oim_create_problem(int32_t n, int32_t q, int64_t nnz, const int64_t* row_ptr
         }
     }
     if (!(flags & OIM_FLAG_SKIP_SYMMETRY_CHECK)) {
+        // Rows are visited in increasing order, so for each row j the entries (j, i) that
+        // mirror the visited (i, j) come in increasing i, that is in row j's column
+        // order: one cursor per row walks them, and every cursor must end at its row's
+        // end (each entry matched exactly once, with the same weight).
+        std::vector<int64_t> cur(rp.begin(), rp.end() - 1);
         for (int32_t i = 0; i < n; ++i)
             for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
                 const int32_t j = ci[e];
-                const int32_t* b = ci.data() + rp[j];
-                const int32_t* en = ci.data() + rp[j + 1];
-                const int32_t* f = std::lower_bound(b, en, i);
-                if (f == en || *f != i || w[f - ci.data()] != w[e])
+                const int64_t f = cur[j];
+                if (f >= rp[j + 1] || ci[f] != i || w[f] != w[e])
                     return fail(OIM_EINVAL, "coupling matrix is not symmetric at (" + std::to_string(i) +
                                                 ", " + std::to_string(j) + ")");
+                cur[j] = f + 1;
             }
+        for (int32_t j = 0; j < n; ++j)
+            if (cur[j] != rp[j + 1])
+                return fail(OIM_EINVAL, "coupling matrix is not symmetric: entry (" + std::to_string(j) +
+                                            ", " + std::to_string(ci[cur[j]]) + ") has no mirror");
     }
     oim_problem_s* p = new (std::nothrow) oim_problem_s();
     if (!p) return fail(OIM_ENOMEM, "host allocation");

@@ -113,6 +113,43 @@ def test_malformed_problems_rejected(capi, case):
     assert capi.oim_last_error() != ""
 
 
+def test_symmetry_check_agrees_with_the_dense_definition(capi):
+    """The library accepts a CSR exactly when its dense matrix equals its transpose
+    (W = W^T, the coupling of Eq. 1-2): random symmetric graphs, and the same graphs
+    with one entry dropped, one weight changed or one entry added."""
+    rng = np.random.default_rng(5)
+    for trial in range(60):
+        n = int(rng.integers(2, 30))
+        W = np.triu(rng.integers(-2, 3, size=(n, n)).astype(np.float32) * (rng.random((n, n)) < 0.3), 1)
+        W = W + W.T
+        kind = trial % 4
+        if kind and np.count_nonzero(W):
+            nz = np.argwhere(W != 0)
+            i, j = nz[rng.integers(len(nz))]
+            if kind == 1:
+                W[i, j] = 0.0                       # drop (i, j), keep (j, i)
+            elif kind == 2:
+                W[i, j] += 1.0 if W[i, j] != -1.0 else 2.0   # a different weight
+        if kind == 3:
+            i, j = rng.choice(n, 2, replace=False)
+            W[i, j] = 7.0 if W[j, i] != 7.0 else 9.0   # an entry whose mirror differs
+        rows, cols = np.nonzero(W)
+        rp = np.zeros(n + 1, np.int64)
+        np.add.at(rp, rows + 1, 1)
+        rp = np.cumsum(rp)
+        col = cols.astype(np.int32)
+        w = W[rows, cols].astype(np.float32)
+        symmetric = np.array_equal(W, W.T)
+        try:
+            h = capi.oim_create_problem(n, 2, col.shape[0], rp, col, w, capi.OIM_FLAG_DEFER_UPLOAD)
+            capi.oim_destroy_problem(h)
+            accepted = True
+        except capi.OimError as e:
+            assert e.code == capi.OIM_EINVAL
+            accepted = False
+        assert accepted == symmetric, (trial, kind)
+
+
 def test_null_handles_rejected(capi):
     with pytest.raises(capi.OimError) as ei:
         capi.oim_run_sync(None)
