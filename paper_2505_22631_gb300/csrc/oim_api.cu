@@ -44,7 +44,6 @@ int gemm_setup(oim_run_s& r);
 void gemm_free(oim_run_s& r);
 cudaError_t launch_gemm_init(const oim_run_s& r, cudaStream_t s);
 cudaError_t launch_set_seed(uint64_t* d_seed, uint64_t seed, cudaStream_t s);
-cudaError_t launch_advance_t0(int32_t* d_t0, int32_t steps, cudaStream_t s);
 cudaError_t launch_gemm_step(const oim_run_s& r, int64_t t, cudaStream_t s);
 cudaError_t launch_gemm_step_at(const oim_run_s& r, int64_t t, const int32_t* d_t0, cudaStream_t s);
 cudaError_t launch_gemm_to_common(const oim_run_s& r, float* out, cudaStream_t s);
@@ -377,6 +376,14 @@ int allocate_run(oim_run_s* r) {
     }
     OIM_CUDA(cudaMemset(r->d_err, 0, sizeof(int32_t)), "cudaMemset(err)");
     return OIM_OK;
+}
+
+// The step base of a replayed chunk of steps moves on by the chunk's length.
+__global__ void advance_t0_kernel(int32_t* d_t0, int32_t steps) { *d_t0 += steps; }
+
+cudaError_t launch_advance_t0(int32_t* d_t0, int32_t steps, cudaStream_t s) {
+    advance_t0_kernel<<<1, 1, 0, s>>>(d_t0, steps);
+    return cudaGetLastError();
 }
 
 // Steps per replay of a captured chunk: the readout period (so each chunk ends on a

@@ -344,14 +344,6 @@ cudaError_t launch_set_seed(uint64_t* d_seed, uint64_t seed, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// The step base of a replayed chunk of steps moves on by the chunk's length.
-__global__ void advance_t0_kernel(int32_t* d_t0, int32_t steps) { *d_t0 += steps; }
-
-cudaError_t launch_advance_t0(int32_t* d_t0, int32_t steps, cudaStream_t s) {
-    advance_t0_kernel<<<1, 1, 0, s>>>(d_t0, steps);
-    return cudaGetLastError();
-}
-
 // Launch shape of the thread = (node, replica quad) kernels: blocks of 256 threads,
 // x over quads (a warp covers consecutive quads of a node: coalesced rows), y over
 // nodes; the grid runs nodes along x (up to 2^31 - 1 blocks) and quads along y.
