@@ -95,8 +95,9 @@ __global__ void __launch_bounds__(256, 4) adj_step_kernel(CSRDev csr, StepParams
                                                        double* __restrict__ dK, double* __restrict__ dKs,
                                                        double* __restrict__ dKn, int64_t T,
                                                        int quads_fast) {
-    // block: quads x nodes; the blocks take their nodes heaviest row first (the stream
-    // form's row descriptors), with the replica blocks dispatched first under quads_fast
+    // block: quads x nodes; the blocks take their nodes graph by graph, heaviest row
+    // first within a graph (so a warp's nodes share a graph for the gradient
+    // reductions), with the replica blocks dispatched first under quads_fast
     const int quads = P.R_pad >> 2;
     const int nblk = quads_fast ? blockIdx.y : blockIdx.x;
     const int qblk = quads_fast ? blockIdx.x : blockIdx.y;
@@ -106,7 +107,7 @@ __global__ void __launch_bounds__(256, 4) adj_step_kernel(CSRDev csr, StepParams
     int g = -1;
     double gK = 0.0, gS = 0.0, gN = 0.0;
     if (valid) {
-        const int4 row = __ldg(csr.srow + slot);   // {node, row start, first -1 entry, row end}
+        const int4 row = __ldg(csr.arow + slot);   // {node, row start, first -1 entry, row end}
         const int node = row.x;
         const size_t at = (size_t)node * P.R_pad + 4 * quad;
         const size_t state = (size_t)csr.nodes * P.R_pad;

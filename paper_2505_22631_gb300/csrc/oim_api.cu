@@ -139,6 +139,18 @@ int upload_problem(oim_problem_s* p) {
              "upload stream rows");
     OIM_CUDA(cudaMemcpy(p->d_shead, shead.data(), shead.size() * sizeof(uint4), cudaMemcpyHostToDevice),
              "upload stream row heads");
+    // the adjoint's descriptors: graph by graph, each graph's rows by decreasing length
+    OIM_CUDA(dev_alloc(&p->d_arow, (size_t)p->nodes), "cudaMalloc(adjoint rows)");
+    std::vector<int4> arow((size_t)p->nodes);
+    for (int g = 0; g < p->G; ++g) {
+        const int32_t off = p->graphs[g].node_off;
+        for (int32_t k = 0; k < p->graphs[g].n; ++k) {
+            const int32_t v = off + p->h_order[(size_t)off + k];
+            arow[(size_t)off + k] = make_int4(v, p->h_rowp[v], p->h_split[v], p->h_rowp[v + 1]);
+        }
+    }
+    OIM_CUDA(cudaMemcpy(p->d_arow, arow.data(), arow.size() * sizeof(int4), cudaMemcpyHostToDevice),
+             "upload adjoint rows");
     std::vector<int32_t> ng((size_t)p->nodes);
     for (int g = 0; g < p->G; ++g)
         std::fill(ng.begin() + p->graphs[g].node_off,
@@ -204,6 +216,7 @@ void free_problem(oim_problem_s* p) {
     dev_free(p->d_order);
     dev_free(p->d_srow);
     dev_free(p->d_shead);
+    dev_free(p->d_arow);
     dev_free(p->d_graphs);
     dev_free(p->d_urowp);
     dev_free(p->d_ucol);

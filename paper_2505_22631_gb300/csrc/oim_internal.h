@@ -81,6 +81,9 @@ struct CSRDev {
     // [nodes] the first four packed column words of each slot's row, in row order (the
     // slot's own node where the row is shorter: in bounds, never added)
     const uint4* shead;
+    // [nodes] row descriptors like srow, graph by graph, heaviest row first within each
+    // graph (the adjoint step: a warp's nodes then share a graph for its reductions)
+    const int4* arow;
 };
 
 }  // namespace oim
@@ -113,11 +116,12 @@ struct oim_problem_s {
     float* d_uw = nullptr;
     int4* d_srow = nullptr;        // stream-form row descriptors, heaviest rows first
     uint4* d_shead = nullptr;      // and the first four column words of each of those rows
+    int4* d_arow = nullptr;        // adjoint row descriptors, graph by graph
     int32_t max_n = 0;             // largest graph
     oim::CSRDev csr() const {
         return oim::CSRDev{d_rowp, d_col, unit_weights ? nullptr : d_w, d_node_graph, d_split,
                            d_order, d_graphs, G, (int32_t)nodes, d_urowp, d_ucol,
-                           unit_weights ? nullptr : d_uw, d_srow, d_shead};
+                           unit_weights ? nullptr : d_uw, d_srow, d_shead, d_arow};
     }
 };
 
