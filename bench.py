@@ -300,6 +300,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-quality", action="store_true")
+    ap.add_argument("--quality-seeds", type=int, default=8,
+                    help="seeds of the time-to-99%% comparison (mean and 95%% CI)")
     ap.add_argument("--euler-steps", type=int, default=0, help="override the workload's steps")
     ap.add_argument("--replicas", type=int, default=0, help="override the workload's replicas")
     ap.add_argument("--adjoint", action="store_true",
@@ -594,12 +596,35 @@ def run_adjoint(args, rank, world):
         print(json.dumps(line), flush=True)
 
 
+def _mean_ci(xs):
+    """Mean and the half-width of its 95 % confidence interval (Student t)."""
+    x = np.asarray([v for v in xs if v is not None], dtype=np.float64)
+    if x.size == 0:
+        return None, None
+    if x.size == 1:
+        return float(x[0]), None
+    try:
+        from scipy.stats import t as student_t
+        q = float(student_t.ppf(0.975, x.size - 1))
+    except Exception:
+        q = 1.96
+    return float(x.mean()), float(q * x.std(ddof=1) / np.sqrt(x.size))
+
+
 def quality(w, prob, problems, args, stream, ms_step_chosen, chosen_cfg):
-    """Time to 99% of the best known cut: chosen form vs the plain FP32 CSR form."""
+    """Time to 99 % of the best known cut, chosen form vs the plain FP32 CSR form, over
+    several seeds, with one stopping rule for both: a graph stops at the first readout
+    where its best score over the replicas reaches 99 % of the best known score.  The
+    chosen form steps every graph of the batch together, so it stops when the last graph
+    reaches its target; the plain form runs the graphs one after another, each stopping
+    at its own hit.  Also the final best-score distributions of both forms (equal
+    quality)."""
     import torch
     from paper_2505_22631_gb300 import Run
     re = args.readout_every
     q2 = w.q == 2
+    G = len(w.graphs)
+    seeds = [777 + 13 * k for k in range(args.quality_seeds)]
     # best known: best score of a 4x longer run of the chosen form
     form, precision, rpb, threads = chosen_cfg
     K4, Ks4, Kn4, T4 = stretched(w, 4)
@@ -608,59 +633,94 @@ def quality(w, prob, problems, args, stream, ms_step_chosen, chosen_cfg):
     tr = long.readout(spins=False)["trace"]
     long.close()
     best_known = tr.max(axis=(1, 2)) if q2 else tr.min(axis=(1, 2))
+    target = [0.99 * b if q2 else b / 0.99 for b in best_known]
     K, Ks, Kn = schedules(w)
-    chosen = Run(prob, K, Ks, Kn, w.dt, w.steps, w.replicas, 777, form=form, precision=precision,
-                 readout_every=re, stream=stream, replicas_per_block=rpb,
-                 threads_per_block=threads).readout(spins=False)
     per_step_chosen = ms_step_chosen / 1e3 / w.steps
-    res = {"best_known": best_known.tolist(), "graphs": []}
-    for gi, g in enumerate(w.graphs):
-        # the plain form: one graph per launch, one launch per step, FP32 CSR
-        plain = Run(problems[gi], K[gi], Ks[gi], Kn[gi], w.dt, w.steps, w.replicas, 777,
-                    form="stream", precision="fp32", readout_every=re, use_graph=False,
-                    stream=stream)
-        plain.sync()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        plain.rerun(K[gi], Ks[gi], Kn[gi], w.dt, w.steps, 777)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        per_step_plain = e0.elapsed_time(e1) / 1e3 / w.steps
-        po = plain.readout(spins=False)
-        plain.close()
-        target = 0.99 * best_known[gi] if q2 else best_known[gi] / 0.99
-        rows = {}
-        for name, out, row, per in (("chosen", chosen, gi, per_step_chosen),
-                                    ("plain_fp32_csr", po, 0, per_step_plain)):
+
+    def hits_and_finals(out, rows):
+        hs, fs = [], []
+        for gi, row in rows:
             tr_g, sc_g = out["trace"][row], out["score"][row]
             tb = tr_g.max(axis=1) if q2 else -tr_g.min(axis=1)
-            hit = first_hit(tb, target if q2 else -target)
-            rows[name] = {"time_to_99pct_s": None if hit is None else (hit + 1) * re * per,
-                          "steps_to_99pct": None if hit is None else (hit + 1) * re,
-                          "final_best": float(sc_g.max() if q2 else sc_g.min()),
-                          "final_mean": float(sc_g.mean()),
-                          "s_per_euler_step": per}
-        res["graphs"].append({"graph": g.name, **rows})
-    # Whole workload: time until every graph has reached 99% of its best known
-    # score.  The chosen form advances all graphs together; the plain form runs
-    # one graph per launch sequence, each for its full schedule, so the last
-    # graph starts after the others have finished (best order taken).
-    G = len(w.graphs)
-    hits = [[r[name]["steps_to_99pct"] for r in res["graphs"]] for name in ("chosen", "plain_fp32_csr")]
-    per = [[r[name]["s_per_euler_step"] for r in res["graphs"]] for name in ("chosen", "plain_fp32_csr")]
-    # null when some graph never reaches its target within the schedule
-    t_chosen = None if any(h is None for h in hits[0]) else max(hits[0]) * per[0][0]
-    t_plain = None
-    if not any(h is None for h in hits[1]):
-        full = sum(w.steps * per[1][g] for g in range(G))
-        for last in range(G):   # the graph run last stops at its hit; the others run fully
-            t = full - w.steps * per[1][last] + hits[1][last] * per[1][last]
-            t_plain = t if t_plain is None else min(t_plain, t)
-    res["time_to_99pct_best_cut_s"] = {"chosen": t_chosen, "plain_fp32_csr": t_plain}
-    res["graphs_reaching_99pct"] = {"chosen": sum(h is not None for h in hits[0]),
-                                    "plain_fp32_csr": sum(h is not None for h in hits[1]),
-                                    "of": G}
-    return res
+            h = first_hit(tb, target[gi] if q2 else -target[gi])
+            hs.append(None if h is None else (h + 1) * re)
+            fs.append(float(sc_g.max() if q2 else sc_g.min()))
+        return hs, fs
+
+    # the plain form: one graph per launch sequence, one launch per step, FP32 CSR; its
+    # time per step measured on a rerun of each graph
+    plain_runs, per_step_plain = [], []
+    for gi in range(G):
+        pr = Run(problems[gi], K[gi], Ks[gi], Kn[gi], w.dt, w.steps, w.replicas, seeds[0],
+                 form="stream", precision="fp32", readout_every=re, use_graph=False, stream=stream)
+        pr.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pr.rerun(K[gi], Ks[gi], Kn[gi], w.dt, w.steps, seeds[0])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        per_step_plain.append(e0.elapsed_time(e1) / 1e3 / w.steps)
+        plain_runs.append(pr)
+    chosen_run = Run(prob, K, Ks, Kn, w.dt, w.steps, w.replicas, seeds[0], form=form,
+                     precision=precision, readout_every=re, stream=stream, replicas_per_block=rpb,
+                     threads_per_block=threads)
+    per_seed = []
+    for sd in seeds:
+        chosen_run.rerun(K, Ks, Kn, w.dt, w.steps, sd)
+        hc, fc = hits_and_finals(chosen_run.readout(spins=False), [(gi, gi) for gi in range(G)])
+        hp, fp = [], []
+        for gi in range(G):
+            plain_runs[gi].rerun(K[gi], Ks[gi], Kn[gi], w.dt, w.steps, sd)
+            h, f = hits_and_finals(plain_runs[gi].readout(spins=False), [(gi, 0)])
+            hp += h
+            fp += f
+        t_c = None if any(h is None for h in hc) else max(hc) * per_step_chosen
+        t_p = None if any(h is None for h in hp) else sum(h * p for h, p in zip(hp, per_step_plain))
+        per_seed.append({"seed": sd, "steps_to_99pct": {"chosen": hc, "plain_fp32_csr": hp},
+                         "time_to_99pct_s": {"chosen": t_c, "plain_fp32_csr": t_p},
+                         "final_best": {"chosen": fc, "plain_fp32_csr": fp}})
+    chosen_run.close()
+    for pr in plain_runs:
+        pr.close()
+
+    tc = [r["time_to_99pct_s"]["chosen"] for r in per_seed]
+    tp = [r["time_to_99pct_s"]["plain_fp32_csr"] for r in per_seed]
+    ratio = [p / c for p, c in zip(tp, tc) if p is not None and c is not None]
+    m_c, ci_c = _mean_ci(tc)
+    m_p, ci_p = _mean_ci(tp)
+    m_r, ci_r = _mean_ci(ratio)
+    graphs = []
+    for gi, g in enumerate(w.graphs):
+        fc = [r["final_best"]["chosen"][gi] for r in per_seed]
+        fp = [r["final_best"]["plain_fp32_csr"][gi] for r in per_seed]
+        mc, cc = _mean_ci(fc)
+        mp, cp = _mean_ci(fp)
+        graphs.append({"graph": g.name, "best_known": float(best_known[gi]),
+                       "final_best_mean": {"chosen": mc, "plain_fp32_csr": mp},
+                       "final_best_ci95": {"chosen": cc, "plain_fp32_csr": cp},
+                       "final_best_diff_pct": None if not mp else 100.0 * (mc - mp) / abs(mp),
+                       "steps_to_99pct_mean": {
+                           "chosen": _mean_ci([r["steps_to_99pct"]["chosen"][gi] for r in per_seed])[0],
+                           "plain_fp32_csr": _mean_ci([r["steps_to_99pct"]["plain_fp32_csr"][gi]
+                                                       for r in per_seed])[0]},
+                       "s_per_euler_step": {"chosen (whole batch)": per_step_chosen,
+                                            "plain_fp32_csr (this graph)": per_step_plain[gi]}})
+    return {
+        "rule": "each graph stops at the first readout (every %d steps) whose best score over the "
+                "replicas reaches 99 %% of the best known; chosen: all graphs in one batch, time = "
+                "(last graph's hit) x (batch step time); plain: graphs one after another, time = "
+                "sum over graphs of (its hit) x (its step time)" % re,
+        "best_known_from": "a 4x longer run of the chosen form (seed 4242)",
+        "seeds": seeds,
+        "time_to_99pct_best_cut_s": {"chosen": m_c, "plain_fp32_csr": m_p,
+                                     "chosen_ci95": ci_c, "plain_fp32_csr_ci95": ci_p,
+                                     "seeds_reaching": {"chosen": sum(v is not None for v in tc),
+                                                        "plain_fp32_csr": sum(v is not None for v in tp),
+                                                        "of": len(seeds)}},
+        "plain_over_chosen": {"mean": m_r, "ci95": ci_r, "per_seed": ratio},
+        "graphs": graphs,
+        "per_seed": per_seed,
+    }
 
 
 if __name__ == "__main__":

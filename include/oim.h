@@ -271,6 +271,22 @@ void oim_destroy_run(oim_run_t r);
 int oim_debug_tc_gemm(const void* A, const void* B, float* D, int32_t M, int32_t N, int32_t K);
 
 /*
+ * oim_debug_tc_gemm_withhold -- the same self-test with the failure path of its
+ * pipeline exercised on purpose: every mbarrier wait gives up after `wait_polls`
+ * polls (instead of the library's fixed limit of about a second), and when
+ * withhold_k_block >= 0 the TMA producer never loads that K block, so the MMA
+ * thread's wait for it runs out.  The kernel then records the error in its error
+ * word, lets the loads already in flight land, frees its TMEM and returns; the call
+ * reports OIM_ETIMEOUT and the device stays usable (failure detection by a bounded
+ * device wait, with no fault and no hang).  withhold_k_block = -1 withholds nothing
+ * (the plain self-test with the given poll limit).  D is then partly written.
+ * Errors: as oim_debug_tc_gemm; OIM_EINVAL for wait_polls < 1 or
+ * withhold_k_block < -1.
+ */
+int oim_debug_tc_gemm_withhold(const void* A, const void* B, float* D, int32_t M, int32_t N, int32_t K,
+                               int32_t withhold_k_block, uint32_t wait_polls);
+
+/*
  * oim_score_phases_noalloc -- the cut / conflict scores of oim_readout, for
  * phases the caller supplies, computed without allocating any device memory.
  * (The paper has no counterpart: this is an interface for embedding.)
@@ -286,16 +302,19 @@ int oim_debug_tc_gemm(const void* A, const void* B, float* D, int32_t M, int32_t
  *
  *   p         problem (one graph or a batch) whose graph is on the device
  *             (not created with OIM_FLAG_DEFER_UPLOAD, or already run once)
- *   theta     device float[nodes][ld]: phase of replica r of global node v
- *             (graphs concatenated in batch order) at theta[v * ld + r], in [0,1)
+ *   theta     device float[nodes][ld], 16-byte aligned: phase of replica r of
+ *             global node v (graphs concatenated in batch order) at
+ *             theta[v * ld + r], in [0,1); read in groups of four replicas
  *   replicas  1 <= replicas <= ld;  ld a multiple of 4
  *   score     device double[graphs][replicas]: as oim_readout's score (spins
  *             thresholded in FP32, cut for q == 2, conflict weight for q >= 3)
  *   stream    cudaStream_t to queue the work on (NULL = legacy default stream)
  * The work is queued asynchronously; score is valid once the stream is synchronised.
- * Errors: OIM_EINVAL (NULL or host pointers, bad replicas / ld, or
- * graphs * ld > OIM_NOALLOC_MAX_ACCUM), OIM_ESTATE (graph not on the device),
- * OIM_ECUDA.
+ * Errors: OIM_EINVAL (NULL or host pointers, theta not 16-byte or score not
+ * 8-byte aligned, bad replicas / ld, or graphs * ld > OIM_NOALLOC_MAX_ACCUM),
+ * OIM_ESTATE (graph not on the device), OIM_ECUDA.  Any node count is served
+ * (the score pass strides over node chunks); the caller's current device is
+ * restored before the call returns.
  * Every call shares the one scratch area and clears the part it uses before
  * use; calls whose work overlaps on the GPU (other streams, other host threads)
  * race on it and must be serialised by the caller.  The first call on a device

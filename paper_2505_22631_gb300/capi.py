@@ -89,6 +89,7 @@ SIGNATURES = {
     "oim_autotune": (ctypes.c_int, [_vp, _i32, _i32, _i64, _vp, ctypes.POINTER(oim_run_opts),
                                     ctypes.POINTER(ctypes.c_double)]),
     "oim_debug_tc_gemm": (ctypes.c_int, [_vp, _vp, _vp, _i32, _i32, _i32]),
+    "oim_debug_tc_gemm_withhold": (ctypes.c_int, [_vp, _vp, _vp, _i32, _i32, _i32, _i32, _u32]),
     "oim_schedule_triangular": (ctypes.c_int, [_vp, _i64, _f32, _i32]),
     "oim_destroy_run": (None, [_vp]),
     "oim_score_phases_noalloc": (ctypes.c_int, [_vp, _vp, _i32, _i32, _vp, _vp]),
@@ -241,6 +242,14 @@ def oim_backward(r, dK=None, dKs=None, dKn=None, loss=None):
 def oim_debug_tc_gemm(A, B, D, M, N, K):
     """D = A B^T on the tensor cores (A bf16 [M,K], B bf16 [N,K], D float32 [M,N]; device)."""
     _check(load().oim_debug_tc_gemm(A.data_ptr(), B.data_ptr(), ptr(D, np.float32), int(M), int(N), int(K)))
+
+
+def oim_debug_tc_gemm_withhold(A, B, D, M, N, K, withhold_k_block, wait_polls):
+    """The tensor-core self-test with K block `withhold_k_block` never loaded and every
+    pipeline wait limited to `wait_polls` polls (raises OimError OIM_ETIMEOUT when a
+    wait gives up)."""
+    _check(load().oim_debug_tc_gemm_withhold(A.data_ptr(), B.data_ptr(), ptr(D, np.float32), int(M),
+                                             int(N), int(K), int(withhold_k_block), int(wait_polls)))
 
 
 def oim_autotune(p, replicas, precision_policy=OIM_PREC_AUTO, probe_steps=100, stream=None):

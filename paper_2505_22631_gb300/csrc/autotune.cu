@@ -112,8 +112,11 @@ extern "C" int oim_autotune(oim_problem_t p, int32_t replicas, int32_t precision
         add(OIM_FORM_GEMM, OIM_PREC_BF16, 0, 576);   // 256-wide tiles
     }
 
+    DeviceScope scope;   // the probes' stream and events on the problem's device
+    cudaError_t e = scope.enter(p->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
     cudaStream_t s = nullptr;
-    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
     if (e != cudaSuccess) return cuda_fail(e, "autotune stream");
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);

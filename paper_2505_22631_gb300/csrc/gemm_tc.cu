@@ -45,10 +45,15 @@ constexpr int kBM = 128;             // rows of a tile (TMEM lanes)
 constexpr int kBK = 64;              // K block: 64 bf16 = one 128-byte swizzle row
 constexpr int kABytes = kBM * 128;   // A stage: 128 rows x 128 B
 
+// With withhold >= 0 the producer skips the TMA load of K block `withhold`: the MMA
+// thread's wait for it then runs out after `polls` polls and records the error, the
+// loads already in flight are waited for (bounded), the TMEM is freed and the block
+// returns -- the path every bounded wait of the pipeline takes when it gives up.
 template <int BN, int S>
 __global__ void __launch_bounds__(128, 1)
     tc_gemm_test_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB,
-                        float* __restrict__ D, int M, int N, int K, int32_t* err) {
+                        float* __restrict__ D, int M, int N, int K, int32_t* err, int withhold,
+                        uint32_t polls) {
     using namespace tc;
     constexpr int kBBytes = BN * 128;
     constexpr uint32_t kCols = BN <= 32 ? 32 : (BN <= 64 ? 64 : (BN <= 128 ? 128 : 256));
@@ -81,18 +86,26 @@ __global__ void __launch_bounds__(128, 1)
 
     if (threadIdx.x == 0) {
         const uint32_t idesc = idesc_bf16_f32(kBM, BN);
+        // K block loaded into each stage and not yet waited for (-1: none)
+        int pending[S];
+        auto load = [&](int kb) {
+            const int s = kb % S;
+            if (kb == withhold) return;   // withheld: nothing will arrive on full[s]
+            mbar_arrive_expect_tx(&full[s], kABytes + kBBytes);
+            tma_load_2d(sA + s * kABytes, &mA, kb * kBK, m0, &full[s]);
+            tma_load_2d(sB + s * kBBytes, &mB, kb * kBK, n0, &full[s]);
+            pending[s] = kb;
+        };
+        for (int s = 0; s < S; ++s) pending[s] = -1;
+        for (int kb = 0; kb < KB && kb < S; ++kb) load(kb);
         bool ok = true;
-        for (int kb = 0; kb < KB && kb < S; ++kb) {
-            mbar_arrive_expect_tx(&full[kb], kABytes + kBBytes);
-            tma_load_2d(sA + kb * kABytes, &mA, kb * kBK, m0, &full[kb]);
-            tma_load_2d(sB + kb * kBBytes, &mB, kb * kBK, n0, &full[kb]);
-        }
         for (int kb = 0; kb < KB && ok; ++kb) {
             const int s = kb % S;
-            if (!mbar_wait(&full[s], (kb / S) & 1, err, kErrFullWait)) {
+            if (!mbar_wait_polls(&full[s], (kb / S) & 1, err, kErrFullWait, polls)) {
                 ok = false;
                 break;
             }
+            pending[s] = -1;
             tc_fence_after();
             const uint32_t a0 = smem_u32(sA + s * kABytes), b0 = smem_u32(sB + s * kBBytes);
 #pragma unroll
@@ -101,20 +114,22 @@ __global__ void __launch_bounds__(128, 1)
                           (kb | k) != 0);
             umma_commit(&empty[s]);
             if (kb + S < KB) {
-                if (!mbar_wait(&empty[s], (kb / S) & 1, err, kErrEmptyWait)) {
+                if (!mbar_wait_polls(&empty[s], (kb / S) & 1, err, kErrEmptyWait, polls)) {
                     ok = false;
                     break;
                 }
-                mbar_arrive_expect_tx(&full[s], kABytes + kBBytes);
-                tma_load_2d(sA + s * kABytes, &mA, (kb + S) * kBK, m0, &full[s]);
-                tma_load_2d(sB + s * kBBytes, &mB, (kb + S) * kBK, n0, &full[s]);
+                load(kb + S);
             }
         }
+        // after a wait that gave up, let the loads still in flight land before the
+        // shared memory they write is released
+        for (int s = 0; s < S; ++s)
+            if (pending[s] >= 0) mbar_wait_polls(&full[s], (pending[s] / S) & 1, err, kErrFullWait, polls);
         // completes when every MMA issued above has finished (also on the error path)
         umma_commit(&done);
     }
     __syncwarp();
-    const bool have = mbar_wait(&done, 0, err, kErrDoneWait);
+    const bool have = mbar_wait_polls(&done, 0, err, kErrDoneWait, polls);
     tc_fence_after();
     if (have) {
         const int row = warp * 32 + lane;
@@ -155,7 +170,10 @@ int make_map_bf16(CUtensorMap* m, const void* base, uint64_t cols, uint64_t rows
 
 using namespace oim;
 
-extern "C" int oim_debug_tc_gemm(const void* A, const void* B, float* D, int32_t M, int32_t N, int32_t K) {
+namespace {
+
+int tc_gemm_run(const void* A, const void* B, float* D, int32_t M, int32_t N, int32_t K, int withhold,
+                uint32_t polls) {
     if (!A || !B || !D) return fail(OIM_EINVAL, "NULL argument");
     if (M <= 0 || N <= 0 || K <= 0 || M % 128 || N % 128 || K % 64)
         return fail(OIM_EINVAL, "need M, N multiples of 128 and K a multiple of 64");
@@ -175,7 +193,7 @@ extern "C" int oim_debug_tc_gemm(const void* A, const void* B, float* D, int32_t
     auto fn = tc_gemm_test_kernel<128, S>;
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) {
-        fn<<<dim3(N / 128, M / 128), 128, smem>>>(mA, mB, D, M, N, K, d_err);
+        fn<<<dim3(N / 128, M / 128), 128, smem>>>(mA, mB, D, M, N, K, d_err, withhold, polls);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -185,4 +203,17 @@ extern "C" int oim_debug_tc_gemm(const void* A, const void* B, float* D, int32_t
     if (e != cudaSuccess) return cuda_fail(e, "tensor-core self-test");
     if (err) return fail(OIM_ETIMEOUT, "tensor-core self-test: a pipeline wait gave up (" + std::to_string(err) + ")");
     return OIM_OK;
+}
+
+}  // namespace
+
+extern "C" int oim_debug_tc_gemm(const void* A, const void* B, float* D, int32_t M, int32_t N, int32_t K) {
+    return tc_gemm_run(A, B, D, M, N, K, -1, tc::kWaitPolls);
+}
+
+extern "C" int oim_debug_tc_gemm_withhold(const void* A, const void* B, float* D, int32_t M, int32_t N,
+                                          int32_t K, int32_t withhold_k_block, uint32_t wait_polls) {
+    if (wait_polls < 1) return fail(OIM_EINVAL, "wait_polls must be >= 1");
+    if (withhold_k_block < -1) return fail(OIM_EINVAL, "withhold_k_block must be >= -1");
+    return tc_gemm_run(A, B, D, M, N, K, withhold_k_block, wait_polls);
 }

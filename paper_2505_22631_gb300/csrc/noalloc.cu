@@ -1,6 +1,8 @@
 // noalloc.cu -- oim_score_phases_noalloc: the score pass of oim_readout for
 // caller-supplied phases, with its accumulators in a fixed, file-scope device
 // array instead of memory obtained from cudaMalloc.
+#include <algorithm>
+#include <cstdint>
 #include <mutex>
 #include <string>
 
@@ -24,15 +26,19 @@ std::mutex g_setup_mutex;
 double* g_accum_ptr[kMaxDevices] = {nullptr};
 
 constexpr int kNodesPerThread = 16;
+constexpr unsigned kMaxGridY = 65535;   // the grid's y extent; chunks beyond it are strided
 
 // sum_{i<j} w_ij [spin_i == spin_j] per (graph, replica) into accum[g * ld + r].
-// Thread = (replica quad, chunk of kNodesPerThread nodes).
+// Thread = (replica quad, chunks of kNodesPerThread nodes: blockIdx.y, then every
+// gridDim.y-th chunk after it, so that any node count fits the grid).
 __global__ void __launch_bounds__(256) noalloc_agree_kernel(CSRDev csr, const float* __restrict__ theta,
                                                             int ld, int q, double* __restrict__ accum) {
     const int quads = ld >> 2;
     const int quad = blockIdx.x * blockDim.x + threadIdx.x;
     if (quad >= quads) return;
-    const int first = blockIdx.y * kNodesPerThread;
+    const int chunks = (csr.nodes + kNodesPerThread - 1) / kNodesPerThread;
+    for (int chunk = blockIdx.y; chunk < chunks; chunk += gridDim.y) {
+    const int first = chunk * kNodesPerThread;
     const int last = min(first + kNodesPerThread, csr.nodes);
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
     int g_cur = -1;
@@ -72,6 +78,7 @@ __global__ void __launch_bounds__(256) noalloc_agree_kernel(CSRDev csr, const fl
         acc[3] += f3;
     }
     flush();
+    }
 }
 
 // score[g][r] = wtot_g - agree (q == 2) or agree (q >= 3).
@@ -120,11 +127,15 @@ extern "C" int oim_score_phases_noalloc(oim_problem_t p, const float* theta, int
         return fail(OIM_EINVAL, "graphs * ld = " + std::to_string(need) +
                                     " exceeds the no-allocation scratch of " +
                                     std::to_string(OIM_NOALLOC_MAX_ACCUM) + " doubles");
+    // theta is read in 16-byte groups of four replicas and score written as doubles
+    if (reinterpret_cast<uintptr_t>(theta) % 16 != 0)
+        return fail(OIM_EINVAL, "theta must be 16-byte aligned");
+    if (reinterpret_cast<uintptr_t>(score) % sizeof(double) != 0)
+        return fail(OIM_EINVAL, "score must be 8-byte aligned");
     if (!p->uploaded) return fail(OIM_ESTATE, "the problem's graph is not on the device yet");
-    int cur = -1;
-    cudaGetDevice(&cur);
-    if (cur != p->device) {
-        cudaError_t e = cudaSetDevice(p->device);
+    DeviceScope scope;   // the caller's current device is restored on return
+    {
+        cudaError_t e = scope.enter(p->device);
         if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
     }
     if (!device_pointer(theta) || !device_pointer(score))
@@ -137,8 +148,8 @@ extern "C" int oim_score_phases_noalloc(oim_problem_t p, const float* theta, int
     if (e != cudaSuccess) return cuda_fail(e, "clear no-allocation scratch");
     const int quads = ld / 4;
     dim3 block(std::min(256, ((quads + 31) / 32) * 32));
-    dim3 grid((quads + block.x - 1) / block.x,
-              (unsigned)((p->nodes + kNodesPerThread - 1) / kNodesPerThread));
+    const int64_t chunks = (p->nodes + kNodesPerThread - 1) / kNodesPerThread;
+    dim3 grid((quads + block.x - 1) / block.x, (unsigned)std::min<int64_t>(chunks, kMaxGridY));
     noalloc_agree_kernel<<<grid, block, 0, s>>>(p->csr(), theta, ld, p->q, accum);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "no-allocation score launch");

@@ -585,10 +585,9 @@ int execute(oim_run_s* r, const float* K, const float* Ks, const float* Kn) {
     return OIM_OK;
 }
 
-int set_device_of(const oim_problem_s* p) {
-    int cur = -1;
-    cudaGetDevice(&cur);
-    if (cur != p->device) OIM_CUDA(cudaSetDevice(p->device), "cudaSetDevice");
+// Makes p's device current until `scope` ends (the caller's device is restored then).
+int set_device_of(const oim_problem_s* p, DeviceScope& scope) {
+    OIM_CUDA(scope.enter(p->device), "cudaSetDevice");
     return OIM_OK;
 }
 
@@ -794,6 +793,8 @@ int oim_problem_info(oim_problem_t p, int32_t* graphs, int64_t* nodes, int64_t* 
 
 void oim_destroy_problem(oim_problem_t p) {
     if (!p) return;
+    DeviceScope scope;
+    scope.enter(p->device);
     free_problem(p);
     delete p;
 }
@@ -812,7 +813,8 @@ int oim_run(oim_problem_t p, const float* K, const float* Ks, const float* Kn, f
     oim_run_opts o;
     if (opts) o = *opts; else oim_default_opts(&o);
     if (o.readout_every < 0) return fail(OIM_EINVAL, "readout_every must be >= 0");
-    rc = set_device_of(p);
+    DeviceScope scope;
+    rc = set_device_of(p, scope);
     if (rc != OIM_OK) return rc;
     rc = ensure_uploaded(p);
     if (rc != OIM_OK) return rc;
@@ -850,7 +852,8 @@ int oim_rerun(oim_run_t r, const float* K, const float* Ks, const float* Kn, flo
     int rc = validate_schedule_args(dt, steps);
     if (rc != OIM_OK) return rc;
     if (steps > 0 && (!K || !Ks || !Kn)) return fail(OIM_EINVAL, "NULL schedule");
-    rc = set_device_of(r->p);
+    DeviceScope scope;
+    rc = set_device_of(r->p, scope);
     if (rc != OIM_OK) return rc;
     r->steps = steps;
     r->seed = seed;
@@ -886,7 +889,8 @@ int oim_readout(oim_run_t r, int8_t* spins, double* score, int32_t* best_replica
     g_last_error.clear();
     if (!r) return fail(OIM_EINVAL, "NULL run");
     if (!r->ran) return fail(OIM_ESTATE, "run has not executed");
-    int rc = set_device_of(r->p);
+    DeviceScope scope;
+    int rc = set_device_of(r->p, scope);
     if (rc != OIM_OK) return rc;
     cudaStream_t s = r->stream;
     const int G = r->p->G;
@@ -960,7 +964,8 @@ int oim_get_phases(oim_run_t r, float* theta) {
     g_last_error.clear();
     if (!r || !theta) return fail(OIM_EINVAL, "NULL argument");
     if (!r->ran) return fail(OIM_ESTATE, "run has not executed");
-    int rc = set_device_of(r->p);
+    DeviceScope scope;
+    int rc = set_device_of(r->p, scope);
     if (rc != OIM_OK) return rc;
     float* tmp = nullptr;
     const size_t count = (size_t)r->p->nodes * r->R;
@@ -979,7 +984,8 @@ int oim_debug_derivative(oim_problem_t p, const float* theta, int32_t replicas, 
     if (!p || !theta || !f_out) return fail(OIM_EINVAL, "NULL argument");
     if (p->G != 1) return fail(OIM_EINVAL, "debug derivative takes a single graph");
     if (replicas < 1) return fail(OIM_EINVAL, "replicas must be >= 1");
-    int rc = set_device_of(p);
+    DeviceScope scope;
+    int rc = set_device_of(p, scope);
     if (rc == OIM_OK) rc = ensure_uploaded(p);
     if (rc != OIM_OK) return rc;
     const size_t count = (size_t)p->nodes * replicas;
@@ -1002,7 +1008,8 @@ int oim_backward(oim_run_t r, double* dK, double* dKs, double* dKn, double* loss
     if (!r->ran) return fail(OIM_ESTATE, "run has not executed");
     if (r->form != OIM_FORM_STREAM || r->prec != OIM_PREC_FP32 || r->ckpt_every <= 0 || !r->d_ckpt)
         return fail(OIM_ESTATE, "oim_backward needs a run with checkpoint_every > 0 (FP32 stream form)");
-    int rc = set_device_of(r->p);
+    DeviceScope scope;
+    int rc = set_device_of(r->p, scope);
     if (rc != OIM_OK) return rc;
     cudaStream_t s = r->stream;
     const int G = r->p->G;
@@ -1093,6 +1100,8 @@ int oim_schedule_triangular(float* out, int64_t steps, float ks_max, int32_t per
 
 void oim_destroy_run(oim_run_t r) {
     if (!r) return;
+    DeviceScope scope;
+    scope.enter(r->device);
     cudaStreamSynchronize(r->stream);
     free_run_buffers(r);
     delete r;

@@ -175,6 +175,35 @@ struct oim_run_s {
 
 namespace oim {
 
+// Makes a device current for the lifetime of the object and gives the calling thread
+// its previous current device back when the object goes out of scope, so that no entry
+// point leaves a multi-device caller switched to another GPU.
+class DeviceScope {
+public:
+    DeviceScope() = default;
+    DeviceScope(const DeviceScope&) = delete;
+    DeviceScope& operator=(const DeviceScope&) = delete;
+    cudaError_t enter(int device) {
+        int cur = -1;
+        cudaError_t e = cudaGetDevice(&cur);
+        if (e != cudaSuccess) return e;
+        if (cur == device) return cudaSuccess;
+        e = cudaSetDevice(device);
+        if (e == cudaSuccess) {
+            prev_ = cur;
+            switched_ = true;
+        }
+        return e;
+    }
+    ~DeviceScope() {
+        if (switched_) cudaSetDevice(prev_);
+    }
+
+private:
+    int prev_ = -1;
+    bool switched_ = false;
+};
+
 // error reporting (thread-local message)
 int fail(int code, const std::string& msg);
 int cuda_fail(cudaError_t e, const char* what);

@@ -44,12 +44,18 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait for the phase with the given parity; on timeout records `code`.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int32_t* err, int code) {
-    for (uint32_t it = 0; it < kWaitPolls; ++it)
+// Bounded wait for the phase with the given parity: gives up after `polls` polls
+// and records `code` in *err.
+__device__ __forceinline__ bool mbar_wait_polls(uint64_t* bar, uint32_t parity, int32_t* err, int code,
+                                                uint32_t polls) {
+    for (uint32_t it = 0; it < polls; ++it)
         if (mbar_try_wait(bar, parity)) return true;
     if (err) atomicCAS(err, 0, code);
     return false;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int32_t* err, int code) {
+    return mbar_wait_polls(bar, parity, err, code, kWaitPolls);
 }
 
 // 2D TMA tile load into shared memory, completing `bytes` on the mbarrier.
