@@ -137,6 +137,32 @@ int upload_problem(oim_problem_s* p) {
     }
     OIM_CUDA(cudaMemcpy(p->d_srow, srow.data(), srow.size() * sizeof(int4), cudaMemcpyHostToDevice),
              "upload stream rows");
+    // the 16-bit stream form's slot descriptors: one 32-byte load gives a slot's node, row
+    // bounds, graph, local index and first two column words
+    {
+        std::vector<int32_t> node_g((size_t)p->nodes);
+        for (int g = 0; g < p->G; ++g)
+            for (int32_t k = 0; k < p->graphs[g].n; ++k) node_g[(size_t)p->graphs[g].node_off + k] = g;
+        std::vector<uint32_t> sdesc((size_t)p->nodes * 8);
+        for (size_t k = 0; k < sorder.size(); ++k) {
+            const int32_t v = sorder[k];
+            const int g = node_g[(size_t)v];
+            uint32_t* d = sdesc.data() + 8 * k;
+            d[0] = (uint32_t)v;
+            d[1] = (uint32_t)p->h_rowp[v];
+            d[2] = (uint32_t)p->h_split[v];
+            d[3] = (uint32_t)p->h_rowp[v + 1];
+            d[4] = (uint32_t)g;
+            d[5] = (uint32_t)(v - p->graphs[g].node_off);
+            for (int u = 0; u < 2; ++u) {
+                const int64_t e = (int64_t)p->h_rowp[v] + u;
+                d[6 + u] = e < p->h_rowp[v + 1] ? p->h_col[(size_t)e] : (uint32_t)v;
+            }
+        }
+        OIM_CUDA(dev_alloc(&p->d_sdesc, sdesc.size()), "cudaMalloc(stream slot descriptors)");
+        OIM_CUDA(cudaMemcpy(p->d_sdesc, sdesc.data(), sdesc.size() * sizeof(uint32_t), cudaMemcpyHostToDevice),
+                 "upload stream slot descriptors");
+    }
     OIM_CUDA(cudaMemcpy(p->d_shead, shead.data(), shead.size() * sizeof(uint4), cudaMemcpyHostToDevice),
              "upload stream row heads");
     // the adjoint's descriptors: graph by graph, each graph's rows by decreasing length
@@ -217,6 +243,7 @@ void free_problem(oim_problem_s* p) {
     dev_free(p->d_srow);
     dev_free(p->d_shead);
     dev_free(p->d_arow);
+    dev_free(p->d_sdesc);
     dev_free(p->d_graphs);
     dev_free(p->d_urowp);
     dev_free(p->d_ucol);
@@ -345,6 +372,8 @@ int choose_form(oim_run_s* r) {
     }
     r->form = form;
     r->prec = prec;
+    // the 16-bit stream form moves octets of replicas with 32-byte accesses
+    if (form == OIM_FORM_STREAM && prec != OIM_PREC_FP32) r->R_pad = (r->R + 7) & ~7;
     if (form == OIM_FORM_RESIDENT) {
         cudaError_t e = plan_resident(*r->p, r->R_pad, prec, r->opts.replicas_per_block,
                                       r->opts.threads_per_block, &r->plan);

@@ -31,11 +31,34 @@ __device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
     return c;
 }
 
+// Two Philox blocks with the same key, advanced through one shared key schedule.
+__device__ __forceinline__ void philox10_pair(uint4& a, uint4& b, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint32_t alo0 = 0xD2511F53u * a.x, ahi0 = __umulhi(0xD2511F53u, a.x);
+        const uint32_t alo1 = 0xCD9E8D57u * a.z, ahi1 = __umulhi(0xCD9E8D57u, a.z);
+        const uint32_t blo0 = 0xD2511F53u * b.x, bhi0 = __umulhi(0xD2511F53u, b.x);
+        const uint32_t blo1 = 0xCD9E8D57u * b.z, bhi1 = __umulhi(0xCD9E8D57u, b.z);
+        a = make_uint4(ahi1 ^ a.y ^ k0, alo1, ahi0 ^ a.w ^ k1, alo0);
+        b = make_uint4(bhi1 ^ b.y ^ k0, blo1, bhi0 ^ b.w ^ k1, blo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+}
+
 // Block of four words for (node i, step t, replica quad rq) of one graph/stream.
 __device__ __forceinline__ uint4 draw_block(uint64_t seed, uint32_t graph, uint32_t stream,
                                             uint32_t i, uint32_t t, uint32_t rq) {
     return philox10(make_uint4(i, t, rq, (graph << 1) | stream), (uint32_t)seed,
                     (uint32_t)(seed >> 32));
+}
+
+// The blocks of replica quads rq and rq + 1 at (node i, step t) of one graph/stream.
+__device__ __forceinline__ void draw_block_pair(uint64_t seed, uint32_t graph, uint32_t stream, uint32_t i,
+                                                uint32_t t, uint32_t rq, uint4& a, uint4& b) {
+    a = make_uint4(i, t, rq, (graph << 1) | stream);
+    b = make_uint4(i, t, rq + 1, (graph << 1) | stream);
+    philox10_pair(a, b, (uint32_t)seed, (uint32_t)(seed >> 32));
 }
 
 // ((x >> 9) + 1/2) * 2^-23: an odd multiple of 2^-24 in (0,1), exact in FP32.
@@ -138,6 +161,39 @@ __device__ __forceinline__ void add_bf16x2(float2& acc, uint32_t h2) {
     asm("{\n\t.reg .b16 l, h;\n\tmov.b32 {l, h}, %2;\n\t"
         "add.rn.f32.bf16 %0, l, %0;\n\tadd.rn.f32.bf16 %1, h, %1;\n\t}"
         : "+f"(acc.x), "+f"(acc.y) : "r"(h2));
+}
+
+// acc = (the two 16-bit halves of h2) - acc, each with one FP32 rounding: the mixed
+// subtract that turns an accumulator into the negated sum of the -1 entries that follow
+// (-(acc - x) rounded to nearest equals x - acc rounded to nearest).
+__device__ __forceinline__ void rsub_f16x2(float2& acc, uint32_t h2) {
+    asm("{\n\t.reg .b16 l, h;\n\tmov.b32 {l, h}, %2;\n\t"
+        "sub.rn.f32.f16 %0, l, %0;\n\tsub.rn.f32.f16 %1, h, %1;\n\t}"
+        : "+f"(acc.x), "+f"(acc.y) : "r"(h2));
+}
+__device__ __forceinline__ void rsub_bf16x2(float2& acc, uint32_t h2) {
+    asm("{\n\t.reg .b16 l, h;\n\tmov.b32 {l, h}, %2;\n\t"
+        "sub.rn.f32.bf16 %0, l, %0;\n\tsub.rn.f32.bf16 %1, h, %1;\n\t}"
+        : "+f"(acc.x), "+f"(acc.y) : "r"(h2));
+}
+
+// 32-byte global loads and stores (the sm_100 family's 256-bit vector accesses); the
+// address must be 32-byte aligned.  ld256_nc reads data that no thread writes during
+// the kernel (read-only path); ld256 reads data the kernel itself writes afterwards.
+__device__ __forceinline__ void ld256_nc(const void* p, uint32_t (&r)[8]) {
+    asm("ld.global.nc.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+        : "l"(p));
+}
+__device__ __forceinline__ void ld256(const void* p, uint32_t (&r)[8]) {
+    asm("ld.global.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+        : "l"(p));
+}
+__device__ __forceinline__ void st256(void* p, const uint32_t (&r)[8]) {
+    asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "r"(r[0]), "r"(r[1]),
+                 "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+                 : "memory");
 }
 
 __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {

@@ -6,20 +6,24 @@
 // and Box-Muller (errors ~1e-6, far below the 16-bit storage's 2^-11 / 2^-8).
 //
 // Layout: theta[node][R_pad] (FP32) and cs[node][R_pad] = (cos 2 pi theta,
-// sin 2 pi theta) as float2, replicas contiguous.  One thread owns one node and
-// a quad of four consecutive replicas, so every neighbour gather is two 16-byte
-// loads that a warp turns into fully used 128-byte lines, and one Philox block
-// feeds the four noise draws of the quad.
+// sin 2 pi theta), replicas contiguous.  In the plain form one thread owns one node
+// and a quad of four consecutive replicas (two 16-byte loads per neighbour: a warp
+// turns them into fully used 128-byte lines) and one Philox block feeds the quad's
+// four noise draws.  In the 16-bit form one thread owns a node and an octet of eight
+// consecutive replicas: one 32-byte load per neighbour, the row's index work shared
+// by eight replicas, two Philox blocks sharing one key schedule.
 //
 // Per step and node (Eq. 5 / Algorithm 1, synchronous update from the old phases;
 // the (cos, sin) cache the neighbours read is double-buffered as in Sec. III-B, and
-// th_in may equal th_out because a thread reads and writes only its own phases):
+// the phases are updated in place because a thread reads and writes only its own):
 //   (A, B)   = sum_j w_ij (cos 2 pi theta_j, sin 2 pi theta_j)
 //   D_i      = sin(2 pi theta_i) A - cos(2 pi theta_i) B = sum_j w_ij sin 2 pi (theta_i - theta_j)
 //   theta_i' = wrap(theta_i + dt (K D_i - Ks sin 2 pi q theta_i) + Kn sqrt(dt) xi)
 //   cs_i'    = (cos 2 pi theta_i', sin 2 pi theta_i')
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+
+#include <type_traits>
 
 #include "oim_device.cuh"
 #include "oim_internal.h"
@@ -33,7 +37,6 @@ struct CacheF32 {
     using T = float2;
     static constexpr bool kOwnFromCache = true;   // the plain form reads its own pairs back
     static constexpr bool kFastMath = false;      // correctly rounded sincospi, logf, sqrtf
-    static constexpr int kMinBlocks = 0;          // no occupancy target (registers as the compiler likes)
     static constexpr int kHead = 2;               // row-head entries taken from the descriptor
     __device__ static void load4(const T* p, float2 (&v)[4]) {
         const float4 a = __ldg(reinterpret_cast<const float4*>(p));
@@ -55,23 +58,8 @@ struct Cache16 {
     static constexpr bool kOwnFromCache = false;  // own pairs recomputed in FP32
     // hardware sin / cos / log2 / sqrt (errors ~1e-6, far below the 16-bit storage's)
     static constexpr bool kFastMath = true;
-    // 32 registers, 8 blocks of 256 per SM: more warps to cover the gathers' latency
-    // (measured 200 -> 177 us per step on the 16-graph uneven batch)
-    static constexpr int kMinBlocks = 8;
-    // the first entries of a row come from the slot's head descriptor, so their pair
-    // loads start one dependent load earlier (a row of 4 needs no column load)
-    static constexpr int kHead = 3;
-    static constexpr int kHeadMixed = 4;
     __device__ static float2 to_f2(H2 h);
     __device__ static H2 from_f2(float2 f);
-    __device__ static void cvt4(uint4 a, float2 (&v)[4]) {
-        const uint32_t w[4] = {a.x, a.y, a.z, a.w};
-#pragma unroll
-        for (int k = 0; k < 4; ++k) v[k] = to_f2(*reinterpret_cast<const H2*>(&w[k]));
-    }
-    __device__ static void load4(const T* p, float2 (&v)[4]) {
-        cvt4(__ldg(reinterpret_cast<const uint4*>(p)), v);
-    }
     __device__ static void store4(T* p, const float2 (&v)[4]) {
         uint32_t w[4];
 #pragma unroll
@@ -82,23 +70,6 @@ struct Cache16 {
         *reinterpret_cast<uint4*>(p) = make_uint4(w[0], w[1], w[2], w[3]);
     }
 };
-// acc[v] += the v-th stored (cos, sin) pair of a 16-byte group of four (16-bit forms)
-template <typename H2>
-__device__ __forceinline__ void add_raw4(float2 (&acc)[4], uint4 q);
-template <>
-__device__ __forceinline__ void add_raw4<__half2>(float2 (&acc)[4], uint4 q) {
-    add_f16x2(acc[0], q.x);
-    add_f16x2(acc[1], q.y);
-    add_f16x2(acc[2], q.z);
-    add_f16x2(acc[3], q.w);
-}
-template <>
-__device__ __forceinline__ void add_raw4<__nv_bfloat162>(float2 (&acc)[4], uint4 q) {
-    add_bf16x2(acc[0], q.x);
-    add_bf16x2(acc[1], q.y);
-    add_bf16x2(acc[2], q.z);
-    add_bf16x2(acc[3], q.w);
-}
 
 template <>
 __device__ float2 Cache16<__half2>::to_f2(__half2 h) { return __half22float2(h); }
@@ -138,12 +109,9 @@ __global__ void __launch_bounds__(256) init_stream_kernel(CSRDev csr, StepParams
     C::store4(cs + at, v);
 }
 
-// kMixed (+-1 weights, 16-bit pairs): the gather adds the stored halves with mixed
-// f16 + f32 adds instead of converting and multiplying by +-1 (fewer instructions per
-// edge: faster on denser rows, slower on rows of 4-8 entries; chosen per problem).
-template <bool kUnit, typename C, bool kMixed = false>
-__global__ void __launch_bounds__(256, kMixed ? 6 : C::kMinBlocks) step_stream_kernel(CSRDev csr, StepParams P,
-                                                          const float* th_in,
+// The plain form (FP32 cache): thread = node x quad of replicas.
+template <bool kUnit, typename C>
+__global__ void __launch_bounds__(256) step_stream_kernel(CSRDev csr, StepParams P, const float* th_in,
                                                           const typename C::T* __restrict__ cs_in,
                                                           float* th_out,
                                                           typename C::T* __restrict__ cs_out,
@@ -167,57 +135,15 @@ __global__ void __launch_bounds__(256, kMixed ? 6 : C::kMinBlocks) step_stream_k
 #pragma unroll
     for (int v = 0; v < 4; ++v) acc[v] = make_float2(0.f, 0.f);
     const int e_beg = row.y, e_end = row.w;
-    auto negate = [&]() {
-#pragma unroll
-        for (int v = 0; v < 4; ++v) acc[v] = make_float2(-acc[v].x, -acc[v].y);
-    };
-    // neighbour pairs of the quad: a row of the 16-bit cache is R_pad / 4 groups of 16 bytes
-    const uint4* cs16 = reinterpret_cast<const uint4*>(cs_in) + quad;
-    const size_t rs16 = (size_t)(P.R_pad >> 2);
-    if constexpr (kMixed) {
-        // +-1 weights, 16-bit pairs: rows hold the +1 entries first; mixed f16 + f32 adds
-        // (one rounding each, as the FMA by +-1 would give), the -1 run accumulated with
-        // the accumulator negated: -(-acc + x) = acc - x in round-to-nearest.  Entries are
-        // added in row order; the accumulator is negated at the first -1 entry and back
-        // after the last one.
-        using H2 = typename C::T;
-        constexpr int kH = C::kHeadMixed;
-        const int e_split = row.z;
-        if constexpr (kH > 0) {
-            const uint4 hd = __ldg(csr.shead + slot);
-            const uint32_t hc[4] = {hd.x, hd.y, hd.z, hd.w};
-            uint4 hq[kH > 0 ? kH : 1];
-#pragma unroll
-            for (int u = 0; u < kH; ++u) hq[u] = __ldg(cs16 + (size_t)(hc[u] & ~kSignBit) * rs16);
-#pragma unroll
-            for (int u = 0; u < kH; ++u) {
-                if (e_beg + u < e_end) {
-                    if (e_beg + u == e_split) negate();
-                    add_raw4<H2>(acc, hq[u]);
-                }
-            }
-        }
-        int e = e_beg + kH;
-        for (; e < e_split; ++e) {
-            const uint32_t j = __ldg(csr.col + e) & ~kSignBit;
-            add_raw4<H2>(acc, __ldg(cs16 + (size_t)j * rs16));
-        }
-        if (e_split >= e_beg + kH && e_split < e_end) negate();
-        for (; e < e_end; ++e) {
-            const uint32_t j = __ldg(csr.col + e) & ~kSignBit;
-            add_raw4<H2>(acc, __ldg(cs16 + (size_t)j * rs16));
-        }
-        if (e_split < e_end) negate();
-    } else {
     constexpr int kH = C::kHead;
-    if constexpr (kH > 0 && C::kOwnFromCache) {
-        // FP32 pairs: the head entries' pairs are read as floats
+    {
+        // the head entries' pairs: their column words come with the slot's descriptor
         const uint4 hd = __ldg(csr.shead + slot);
         const uint32_t hc[4] = {hd.x, hd.y, hd.z, hd.w};
-        float2 hv[kH > 0 ? kH : 1][4];
+        float2 hv[kH][4];
 #pragma unroll
         for (int u = 0; u < kH; ++u)
-            C::load4(cs_in + (size_t)(hc[u] & ~kSignBit) * P.R_pad + 4 * quad, hv[u]);
+            C::load4(cs_in + (size_t)(kUnit ? (hc[u] & ~kSignBit) : hc[u]) * P.R_pad + 4 * quad, hv[u]);
 #pragma unroll
         for (int u = 0; u < kH; ++u) {
             if (e_beg + u < e_end) {
@@ -225,23 +151,6 @@ __global__ void __launch_bounds__(256, kMixed ? 6 : C::kMinBlocks) step_stream_k
                 const float2 ww = make_float2(w, w);
 #pragma unroll
                 for (int v = 0; v < 4; ++v) acc[v] = ffma2(hv[u][v], ww, acc[v]);
-            }
-        }
-    } else if constexpr (kH > 0) {
-        const uint4 hd = __ldg(csr.shead + slot);
-        const uint32_t hc[4] = {hd.x, hd.y, hd.z, hd.w};
-        uint4 hq[kH > 0 ? kH : 1];
-#pragma unroll
-        for (int u = 0; u < kH; ++u) hq[u] = __ldg(cs16 + (size_t)(hc[u] & ~kSignBit) * rs16);
-#pragma unroll
-        for (int u = 0; u < kH; ++u) {
-            if (e_beg + u < e_end) {
-                const float w = kUnit ? ((hc[u] & kSignBit) ? -1.0f : 1.0f) : __ldg(csr.w + e_beg + u);
-                float2 nb[4];
-                C::cvt4(hq[u], nb);
-                const float2 ww = make_float2(w, w);
-#pragma unroll
-                for (int v = 0; v < 4; ++v) acc[v] = ffma2(nb[v], ww, acc[v]);
             }
         }
     }
@@ -262,7 +171,6 @@ __global__ void __launch_bounds__(256, kMixed ? 6 : C::kMinBlocks) step_stream_k
 #pragma unroll
         for (int v = 0; v < 4; ++v) acc[v] = ffma2(nb[v], ww, acc[v]);
     }
-    }
 
     // the node's own state after the gather: only the gather's state is live during it
     const int g = csr.node_graph[node];
@@ -274,16 +182,11 @@ __global__ void __launch_bounds__(256, kMixed ? 6 : C::kMinBlocks) step_stream_k
     const float4 th = *reinterpret_cast<const float4*>(th_in + at);
     const float t0[4] = {th.x, th.y, th.z, th.w};
     float2 own[4];
-    if (C::kOwnFromCache) {
-        C::load4(cs_in + at, own);
-    } else {
-#pragma unroll
-        for (int v = 0; v < 4; ++v) own[v] = cos_sin_2pi_fast(t0[v]);
-    }
+    C::load4(cs_in + at, own);
     const uint4 x = draw_block(P.seed_dev ? *P.seed_dev : P.seed, (uint32_t)g, kStreamNoise, (uint32_t)i,
                                (uint32_t)t, (uint32_t)quad);
-    const float2 z01 = C::kFastMath ? box_muller_fast(x.x, x.y) : box_muller(x.x, x.y);
-    const float2 z23 = C::kFastMath ? box_muller_fast(x.z, x.w) : box_muller(x.z, x.w);
+    const float2 z01 = box_muller(x.x, x.y);
+    const float2 z23 = box_muller(x.z, x.w);
     const float z[4] = {z01.x, z01.y, z23.x, z23.y};
     const float kick = Kn * P.sqrt_dt;
     const float dtK = P.dt * K, dtKs = P.dt * Ks;
@@ -294,13 +197,152 @@ __global__ void __launch_bounds__(256, kMixed ? 6 : C::kMinBlocks) step_stream_k
         const float coup = own[v].y * acc[v].x - own[v].x * acc[v].y;
         const float shil = sin_q(P.q, own[v].x, own[v].y);
         tn[v] = wrap01(t0[v] + (dtK * coup - dtKs * shil) + kick * z[v]);
-        if (C::kFastMath)
-            ncs[v] = cos_sin_2pi_fast(tn[v]);
-        else
-            sincospif(2.0f * tn[v], &ncs[v].y, &ncs[v].x);
+        sincospif(2.0f * tn[v], &ncs[v].y, &ncs[v].x);
     }
     *reinterpret_cast<float4*>(th_out + at) = make_float4(tn[0], tn[1], tn[2], tn[3]);
     C::store4(cs_out + at, ncs);
+}
+
+// Eight 16-bit (cos, sin) pairs added to, or subtracted from, the accumulators.
+template <typename H2>
+__device__ __forceinline__ void add8(float2 (&acc)[8], const uint32_t (&v)[8]) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        if constexpr (std::is_same<H2, __half2>::value) add_f16x2(acc[k], v[k]);
+        else add_bf16x2(acc[k], v[k]);
+    }
+}
+template <typename H2>
+__device__ __forceinline__ void rsub8(float2 (&acc)[8], const uint32_t (&v)[8]) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        if constexpr (std::is_same<H2, __half2>::value) rsub_f16x2(acc[k], v[k]);
+        else rsub_bf16x2(acc[k], v[k]);
+    }
+}
+template <typename H2>
+__device__ __forceinline__ float2 h2_to_f2(uint32_t h) {
+    if constexpr (std::is_same<H2, __half2>::value) return __half22float2(*reinterpret_cast<const __half2*>(&h));
+    else return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&h));
+}
+template <typename H2>
+__device__ __forceinline__ uint32_t f2_to_h2(float2 f) {
+    if constexpr (std::is_same<H2, __half2>::value) {
+        const __half2 h = __floats2half2_rn(f.x, f.y);
+        return *reinterpret_cast<const uint32_t*>(&h);
+    } else {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(f.x, f.y);
+        return *reinterpret_cast<const uint32_t*>(&h);
+    }
+}
+
+// The 16-bit form: thread = node x octet of eight consecutive replicas.  A slot's
+// 32-byte descriptor {node, row start, first -1 entry, row end, graph, local index,
+// first two column words} arrives in one load, so the first two neighbours' pairs
+// are requested one dependent load after launch and the node's graph and Philox
+// counter need no further lookups.
+//
+// +-1 weights (kUnit): the row holds its +1 entries first.  They are added with mixed
+// f16 + f32 adds (one rounding each, as the FMA by +1 would give); the first -1 entry
+// is taken with the mixed subtract acc = x - acc, which negates the accumulator, and
+// the rest of the -1 run is added to the negated accumulator:
+// -(acc - x1 - x2) = (x1 - acc) + x2, each rounding to nearest exactly as the FMAs by -1
+// would.  The sign is folded into dt K at the end (exact).  Other weights: each pair
+// is converted to FP32 and multiply-added.
+template <typename H2, bool kUnit>
+__global__ void __launch_bounds__(256, 4) step_octet_kernel(CSRDev csr, StepParams P, float* theta,
+                                                            const H2* __restrict__ cs_in,
+                                                            H2* __restrict__ cs_out, int64_t t_fixed,
+                                                            const int32_t* __restrict__ d_t0,
+                                                            int32_t t_add, int octs_fast) {
+    const int octs = P.R_pad >> 3;
+    const int nblk = octs_fast ? blockIdx.y : blockIdx.x;
+    const int oblk = octs_fast ? blockIdx.x : blockIdx.y;
+    const int slot = nblk * blockDim.y + threadIdx.y;
+    const int oct = oblk * blockDim.x + threadIdx.x;
+    if (slot >= csr.nodes || oct >= octs) return;
+    uint32_t d[8];
+    ld256_nc(csr.sdesc + (size_t)slot * 8, d);
+    const int node = (int)d[0], e_beg = (int)d[1], e_split = (int)d[2], e_end = (int)d[3];
+    const char* cs_base = reinterpret_cast<const char*>(cs_in) + (size_t)oct * 32;
+    const size_t stride = (size_t)P.R_pad * sizeof(uint32_t);   // bytes per node row
+    float2 acc[8];
+#pragma unroll
+    for (int v = 0; v < 8; ++v) acc[v] = make_float2(0.f, 0.f);
+    float sgn = 1.0f;
+    if constexpr (kUnit) {
+        uint32_t h0[8], h1[8];
+        ld256_nc(cs_base + (size_t)(d[6] & ~kSignBit) * stride, h0);
+        ld256_nc(cs_base + (size_t)(d[7] & ~kSignBit) * stride, h1);
+        if (e_beg < e_end) {
+            if (e_beg == e_split) rsub8<H2>(acc, h0);
+            else add8<H2>(acc, h0);
+        }
+        if (e_beg + 1 < e_end) {
+            if (e_beg + 1 == e_split) rsub8<H2>(acc, h1);
+            else add8<H2>(acc, h1);
+        }
+        int e = e_beg + 2;
+        for (; e < e_split; ++e) {
+            uint32_t v[8];
+            ld256_nc(cs_base + (size_t)(__ldg(csr.col + e) & ~kSignBit) * stride, v);
+            add8<H2>(acc, v);
+        }
+        if (e == e_split && e < e_end) {
+            uint32_t v[8];
+            ld256_nc(cs_base + (size_t)(__ldg(csr.col + e) & ~kSignBit) * stride, v);
+            rsub8<H2>(acc, v);
+            ++e;
+        }
+        for (; e < e_end; ++e) {
+            uint32_t v[8];
+            ld256_nc(cs_base + (size_t)(__ldg(csr.col + e) & ~kSignBit) * stride, v);
+            add8<H2>(acc, v);
+        }
+        if (e_split < e_end) sgn = -1.0f;   // the accumulators hold -(A, B)
+    } else {
+        for (int e = e_beg; e < e_end; ++e) {
+            uint32_t v[8];
+            ld256_nc(cs_base + (size_t)__ldg(csr.col + e) * stride, v);
+            const float w = __ldg(csr.w + e);
+            const float2 ww = make_float2(w, w);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) acc[k] = ffma2(h2_to_f2<H2>(v[k]), ww, acc[k]);
+        }
+    }
+
+    const int g = (int)d[4], i = (int)d[5];
+    const int64_t t = d_t0 ? (int64_t)(*d_t0) + t_add : t_fixed;
+    const size_t sidx = (size_t)g * P.steps + t;
+    const float K = __ldg(P.K + sidx), Ks = __ldg(P.Ks + sidx), Kn = __ldg(P.Kn + sidx);
+    const size_t at = (size_t)node * P.R_pad + 8 * oct;
+    uint32_t thw[8];
+    ld256(theta + at, thw);
+    const uint64_t seed = P.seed_dev ? *P.seed_dev : P.seed;
+    uint4 xa, xb;
+    draw_block_pair(seed, (uint32_t)g, kStreamNoise, (uint32_t)i, (uint32_t)t, (uint32_t)(2 * oct), xa, xb);
+    float z[8];
+    {
+        const float2 z0 = box_muller_fast(xa.x, xa.y), z1 = box_muller_fast(xa.z, xa.w);
+        const float2 z2 = box_muller_fast(xb.x, xb.y), z3 = box_muller_fast(xb.z, xb.w);
+        z[0] = z0.x; z[1] = z0.y; z[2] = z1.x; z[3] = z1.y;
+        z[4] = z2.x; z[5] = z2.y; z[6] = z3.x; z[7] = z3.y;
+    }
+    const float kick = Kn * P.sqrt_dt;
+    const float dtK = (P.dt * K) * sgn, dtKs = P.dt * Ks;
+    uint32_t tno[8], cso[8];
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+        const float th = __uint_as_float(thw[v]);
+        const float2 own = cos_sin_2pi_fast(th);
+        const float coup = own.y * acc[v].x - own.x * acc[v].y;
+        const float shil = sin_q(P.q, own.x, own.y);
+        const float tn = wrap01(th + (dtK * coup - dtKs * shil) + kick * z[v]);
+        tno[v] = __float_as_uint(tn);
+        cso[v] = f2_to_h2<H2>(cos_sin_2pi_fast(tn));
+    }
+    st256(theta + at, tno);
+    st256(cs_out + at, cso);
 }
 
 // f = K sum_j w_ij (s_i c_j - c_i s_j) - Ks sin(2 pi q theta_i) for theta[r][n] of
@@ -441,41 +483,49 @@ cudaError_t launch_step_stream_buffers(const oim_run_s& r, int64_t t, const floa
     return cudaGetLastError();
 }
 
-template <typename C>
-static cudaError_t step_stream_as(const oim_run_s& r, int64_t t, const int32_t* d_t0, cudaStream_t s) {
+// The plain form's step t (FP32 cache).
+static cudaError_t step_plain(const oim_run_s& r, int64_t t, const int32_t* d_t0, cudaStream_t s) {
     // with d_t0 the step is *d_t0 + t (graph replay); otherwise t itself.
     const StepParams P = params_of(r);
     const StepGrid q = step_grid(r.p->nodes, r.R_pad / 4);
     const int in = (int)(t & 1);   // buffer parity follows the step index
     const int out = in ^ 1;
-    using T = typename C::T;
     const float* th_in = r.d_theta[in];
-    const T* cs_in = reinterpret_cast<const T*>(r.d_cs[in]);
+    const float2* cs_in = reinterpret_cast<const float2*>(r.d_cs[in]);
     float* th_out = r.d_theta[out];
-    T* cs_out = reinterpret_cast<T*>(r.d_cs[out]);
-    // mixed adds for 16-bit pairs on rows of 8 or more entries on average (measured: the
-    // two-graph max-cut batch, mean degree 12, 28.6 -> 26.6 us per step; the uneven
-    // batch, degrees 4-8, 170 -> 197 us)
-    const bool mixed = !C::kOwnFromCache && r.p->unit_weights && r.p->nnz >= 8 * r.p->nodes;
-    if (mixed)
-        step_stream_kernel<true, C, !C::kOwnFromCache><<<q.grid, q.block, 0, s>>>(
-            r.p->csr(), P, th_in, cs_in, th_out, cs_out, t, d_t0, (int32_t)t,
-            q.quads_fast);
-    else if (r.p->unit_weights)
-        step_stream_kernel<true, C><<<q.grid, q.block, 0, s>>>(
-            r.p->csr(), P, th_in, cs_in, th_out, cs_out, t, d_t0, (int32_t)t,
-            q.quads_fast);
+    float2* cs_out = reinterpret_cast<float2*>(r.d_cs[out]);
+    if (r.p->unit_weights)
+        step_stream_kernel<true, CacheF32><<<q.grid, q.block, 0, s>>>(
+            r.p->csr(), P, th_in, cs_in, th_out, cs_out, t, d_t0, (int32_t)t, q.quads_fast);
     else
-        step_stream_kernel<false, C><<<q.grid, q.block, 0, s>>>(
-            r.p->csr(), P, th_in, cs_in, th_out, cs_out, t, d_t0, (int32_t)t,
-            q.quads_fast);
+        step_stream_kernel<false, CacheF32><<<q.grid, q.block, 0, s>>>(
+            r.p->csr(), P, th_in, cs_in, th_out, cs_out, t, d_t0, (int32_t)t, q.quads_fast);
+    return cudaGetLastError();
+}
+
+// The 16-bit form's step t: thread = node x octet of replicas (R_pad a multiple of 8).
+template <typename H2>
+static cudaError_t step_octet(const oim_run_s& r, int64_t t, const int32_t* d_t0, cudaStream_t s) {
+    const StepParams P = params_of(r);
+    const StepGrid q = step_grid(r.p->nodes, r.R_pad / 8);
+    const int in = (int)(t & 1);
+    // phases in place (one buffer), the (cos, sin) pairs double-buffered
+    float* theta = r.d_theta[in];
+    const H2* cs_in = reinterpret_cast<const H2*>(r.d_cs[in]);
+    H2* cs_out = reinterpret_cast<H2*>(r.d_cs[in ^ 1]);
+    if (r.p->unit_weights)
+        step_octet_kernel<H2, true><<<q.grid, q.block, 0, s>>>(r.p->csr(), P, theta, cs_in, cs_out, t, d_t0,
+                                                              (int32_t)t, q.quads_fast);
+    else
+        step_octet_kernel<H2, false><<<q.grid, q.block, 0, s>>>(r.p->csr(), P, theta, cs_in, cs_out, t, d_t0,
+                                                               (int32_t)t, q.quads_fast);
     return cudaGetLastError();
 }
 
 cudaError_t launch_step_stream(const oim_run_s& r, int64_t t, const int32_t* d_t0, cudaStream_t s) {
-    if (r.prec == OIM_PREC_FP16) return step_stream_as<Cache16<__half2>>(r, t, d_t0, s);
-    if (r.prec == OIM_PREC_BF16) return step_stream_as<Cache16<__nv_bfloat162>>(r, t, d_t0, s);
-    return step_stream_as<CacheF32>(r, t, d_t0, s);
+    if (r.prec == OIM_PREC_FP16) return step_octet<__half2>(r, t, d_t0, s);
+    if (r.prec == OIM_PREC_BF16) return step_octet<__nv_bfloat162>(r, t, d_t0, s);
+    return step_plain(r, t, d_t0, s);
 }
 
 }  // namespace oim

@@ -14,6 +14,17 @@ def rad_dist(a, b):
     return np.abs(circ(np.asarray(a, np.float64) - np.asarray(b, np.float64))) * 2 * np.pi
 
 
+def coupling_bound_rad(g, K, T, dt, eps=1e-2):
+    """Largest phase deviation, in radians, that T steps of a coupling within eps of the
+    row norm can cause when the errors add up without amplification: each step moves a
+    phase by at most dt K_t eps sum_j |w_ij| cycles more than the exact coupling would.
+    A sound bound over horizons where the dynamics do not yet amplify perturbations
+    (a few steps at the benchmark couplings)."""
+    absw = np.bincount(np.repeat(np.arange(g.n), g.degrees()), weights=np.abs(g.w), minlength=g.n)
+    Kt = np.broadcast_to(np.asarray(K, np.float64), (T,)) if np.ndim(K) == 0 else np.asarray(K, np.float64)[:T]
+    return 2 * np.pi * float(np.sum(dt * Kt * eps * absw.max()))
+
+
 def require_gpu():
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():

@@ -9,7 +9,7 @@ test_gpu_statistics.py.
 import numpy as np
 import pytest
 
-from gpu_common import circ, oracle_phases, rad_dist, require_gpu
+from gpu_common import circ, coupling_bound_rad, oracle_phases, rad_dist, require_gpu
 from workloads import make_workload
 
 pytestmark = pytest.mark.gpu
@@ -65,17 +65,22 @@ def test_batched_maxcut_full_run_scores_exact(orc):
 def test_batched_maxcut_in_the_autotuned_stream_form(orc):
     # the form the autotuner picks for the benchmark workload on the GB300 (16-bit stream
     # form, mixed-add gather, CUDA-graph replay on the repeat): sampled replicas against
-    # the oracle over a short horizon (16-bit pairs: median bound), then the full 5000-step
-    # run replayed from its graph, every replica's score recounted from its own spins
+    # the oracle over a short horizon, every phase within the linear accumulation of the
+    # 1e-2 coupling bound (torus: 0.10 rad over 10 steps at K = 4; measured max 2.3e-2)
+    # and the bulk within 1e-3 rad; then the full 5000-step run replayed from its graph,
+    # every replica's score recounted from its own spins
     w = make_workload("torus_er2000")
-    T = 15
+    T = 10
     run = run_workload(w, steps=T, form="stream", precision="fp16", seed=3)
     ph = run.phases()
     for gi, g in enumerate(w.graphs):
-        for r0 in (0, 517, 1020):
-            ref = oracle_phases(orc, g, 2, w.K[gi], w.Ks[gi], w.Kn[gi], w.dt, T, 4, 3, graph=gi,
-                                replica_offset=r0, nthreads=8)
-            assert np.median(rad_dist(ph[gi][r0:r0 + 4], ref)) <= 1e-3
+        d = np.concatenate([
+            rad_dist(ph[gi][r0:r0 + 16], oracle_phases(orc, g, 2, w.K[gi], w.Ks[gi], w.Kn[gi], w.dt, T,
+                                                       16, 3, graph=gi, replica_offset=r0,
+                                                       nthreads=8)).ravel()
+            for r0 in (0, 512, 1008)])
+        assert d.max() <= coupling_bound_rad(g, w.K[gi], T, w.dt)
+        assert np.median(d) <= 1e-3
     run = run_workload(w, form="stream", precision="fp16", readout_every=50, seed=5)
     K, Ks, Kn = (np.stack(x).astype(np.float32) for x in (w.K, w.Ks, w.Kn))
     run.rerun(K, Ks, Kn, w.dt, w.steps, 6)          # the same shape again: graph replay
@@ -93,7 +98,8 @@ def test_batched_maxcut_in_the_autotuned_stream_form(orc):
 def test_dense_workload_in_the_tensor_core_form(orc):
     # the dense benchmark workload at full size in the form the autotuner picks for it
     # (BF16 tensor cores): sampled replicas against the oracle over a short horizon (the
-    # BF16 coupling is within 1e-2 of the row norm, so a median bound), then the full
+    # BF16 coupling is within 1e-2 of the row norm: every phase within the linear
+    # accumulation of that bound, the bulk within 1e-3 rad), then the full
     # 1000-step run with every replica's score recounted from its own spins
     w = make_workload("dense2000")
     g = w.graphs[0]
@@ -104,7 +110,9 @@ def test_dense_workload_in_the_tensor_core_form(orc):
     for r0 in (0, 640, 1020):
         ref = oracle_phases(orc, g, 2, w.K[0], w.Ks[0], w.Kn[0], w.dt, T, 4, 4, replica_offset=r0,
                             nthreads=8)
-        assert np.median(rad_dist(ph[r0:r0 + 4], ref)) <= 1e-3
+        d = rad_dist(ph[r0:r0 + 4], ref)
+        assert d.max() <= coupling_bound_rad(g, w.K[0], T, w.dt)   # measured max 2.3e-3
+        assert np.median(d) <= 1e-3
     run = run_workload(w, form="gemm", precision="bf16", readout_every=50, seed=6)
     out = run.readout()
     spins = orc.readout_f32(2, run.phases()[0])

@@ -8,12 +8,13 @@ Tolerances:
     dynamics amplify an FP32-ulp perturbation of the start to ~4e-6 rad) and after
     50 steps at the production coupling K = 16/mean degree (measured ~9e-5 rad);
   - spins and cut / conflict scores from the same phases: bit-exact;
-  - 16-bit (cos, sin) cache: coupling within 1e-2 of the row norm of the FP64 (A, B).
+  - 16-bit (cos, sin) cache: coupling within 1e-2 of the row norm of the FP64 (A, B);
+    its phases within the linear accumulation of that bound over a short horizon.
 """
 import numpy as np
 import pytest
 
-from gpu_common import circ, gpu_run, oracle_phases, rad_dist, require_gpu
+from gpu_common import circ, coupling_bound_rad, gpu_run, oracle_phases, rad_dist, require_gpu
 from workloads import (constant, csr_from_edges, erdos_renyi, linear_ramp, make_workload,
                        planted_partition, torus)
 
@@ -91,10 +92,15 @@ def test_stream_16bit_cache_start_noise_readout(orc, c1, precision):
     assert np.array_equal(out["spins"][0], spins)
     assert np.array_equal(out["score"][0], orc.scores(g, 2, spins))
     assert np.array_equal(out["trace"][0, -1], out["score"][0])
+    # every phase within the linear accumulation of the 1e-2 coupling bound over 20 steps
+    # (measured max: FP16 1.9e-3, BF16 1.8e-2 rad, against a bound of 0.25 rad), the bulk
+    # within 1e-3 rad
     ref = oracle_phases(orc, g, 2, c1.K[0][:20], c1.Ks[0][:20], c1.Kn[0][:20], c1.dt, 20, R, 5)
     th20 = gpu_run(g, 2, c1.K[0][:20], c1.Ks[0][:20], c1.Kn[0][:20], c1.dt, 20, R, 5, form="stream",
                    precision=precision).phases()[0]
-    assert np.median(rad_dist(th20, ref)) <= 1e-3
+    d = rad_dist(th20, ref)
+    assert d.max() <= coupling_bound_rad(g, c1.K[0], 20, c1.dt)
+    assert np.median(d) <= 1e-3
 
 
 def test_drift_matches_fp64(orc, c1):

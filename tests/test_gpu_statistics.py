@@ -77,8 +77,8 @@ def test_er800_best_cut_matches_oracle(er800_oracle, form, precision):
     w, ref = er800_oracle
     rpb = threads = 0
     if form == "autotuned":
-        o, _ = capi.oim_autotune(Problem.from_graph(w.graphs[0], 2).handle, w.replicas,
-                                 capi.OIM_PREC_AUTO, 200)
+        prob = Problem.from_graph(w.graphs[0], 2)   # kept alive while the autotuner runs
+        o, _ = capi.oim_autotune(prob.handle, w.replicas, capi.OIM_PREC_AUTO, 200)
         form, precision = o.form, o.precision
         rpb, threads = o.replicas_per_block, o.threads_per_block
     gpu = [_gpu_best(w, w.steps, s, form, precision, rpb, threads)[0][0] for s in SEEDS]
