@@ -107,6 +107,27 @@ __device__ __forceinline__ float2 cos_sin_2pi_fast(float th) {
     return make_float2(c, s);
 }
 
+// (cos, sin) of 2 pi (th + 1/2) = -(cos, sin)(2 pi th) for th in [0,1) with the
+// hardware sin / cos: the argument 2 pi th - pi lies in [-pi, pi) and takes one FMA.
+// Kernels that keep half-turn pairs for the own phase and the neighbours alike get
+// the coupling sum_j w_ij sin 2 pi (theta_i - theta_j) unchanged (it depends on phase
+// differences only) and fold the other signs into scalars.
+__device__ __forceinline__ float2 cos_sin_half_turn_fast(float th) {
+    float s, c;
+    __sincosf(__fmaf_rn(th, 6.28318530717958647f, -3.14159265358979324f), &s, &c);
+    return make_float2(c, s);
+}
+
+// Box-Muller like box_muller_fast with the angle 2 pi ub - pi: returns the negated
+// pair of normals, -(rho cos 2 pi ub, rho sin 2 pi ub).
+__device__ __forceinline__ float2 box_muller_half_turn_fast(uint32_t xa, uint32_t xb) {
+    const float ua = u01(xa);
+    const float ub = u01(xb);
+    const float rho = sqrt_approx(-1.38629436111989061f * __log2f(ua));   // -2 ln 2 log2(ua)
+    const float2 cs = cos_sin_half_turn_fast(ub);
+    return make_float2(rho * cs.x, rho * cs.y);
+}
+
 // Normals for the replica pair (r, r+1), r even: lanes (r&3, r&3 + 1).
 __device__ __forceinline__ float2 noise_pair(uint64_t seed, uint32_t graph, uint32_t i,
                                              uint32_t t, uint32_t r) {

@@ -101,8 +101,8 @@ __global__ void __launch_bounds__(256) init_stream_kernel(CSRDev csr, StepParams
     float2 v[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        if (C::kFastMath)
-            v[k] = cos_sin_2pi_fast(th[k]);
+        if (C::kFastMath)   // the 16-bit caches hold half-turn pairs (see step_octet_kernel)
+            v[k] = cos_sin_half_turn_fast(th[k]);
         else
             sincospif(2.0f * th[k], &v[k].y, &v[k].x);
     }
@@ -242,6 +242,12 @@ __device__ __forceinline__ uint32_t f2_to_h2(float2 f) {
 // are requested one dependent load after launch and the node's graph and Philox
 // counter need no further lookups.
 //
+// The 16-bit cache holds half-turn pairs (cos, sin)(2 pi (theta + 1/2)) =
+// -(cos, sin)(2 pi theta), whose argument reduction is one FMA; with the node's own
+// pair taken the same way the coupling s A - c B is unchanged, the injection
+// sin 2 pi q (theta + 1/2) = (-1)^q sin 2 pi q theta and the Box-Muller normals of the
+// shifted angle are negated, both folded into their scalar factors (exact).
+//
 // +-1 weights (kUnit): the row holds its +1 entries first.  They are added with mixed
 // f16 + f32 adds (one rounding each, as the FMA by +1 would give); the first -1 entry
 // is taken with the mixed subtract acc = x - acc, which negates the accumulator, and
@@ -249,7 +255,7 @@ __device__ __forceinline__ uint32_t f2_to_h2(float2 f) {
 // -(acc - x1 - x2) = (x1 - acc) + x2, each rounding to nearest exactly as the FMAs by -1
 // would.  The sign is folded into dt K at the end (exact).  Other weights: each pair
 // is converted to FP32 and multiply-added.
-template <typename H2, bool kUnit>
+template <typename H2, bool kUnit, int kQ>
 __global__ void __launch_bounds__(256, 4) step_octet_kernel(CSRDev csr, StepParams P, float* theta,
                                                             const H2* __restrict__ cs_in,
                                                             H2* __restrict__ cs_out, int64_t t_fixed,
@@ -321,25 +327,28 @@ __global__ void __launch_bounds__(256, 4) step_octet_kernel(CSRDev csr, StepPara
     const uint64_t seed = P.seed_dev ? *P.seed_dev : P.seed;
     uint4 xa, xb;
     draw_block_pair(seed, (uint32_t)g, kStreamNoise, (uint32_t)i, (uint32_t)t, (uint32_t)(2 * oct), xa, xb);
-    float z[8];
+    float z[8];   // the negated normals
     {
-        const float2 z0 = box_muller_fast(xa.x, xa.y), z1 = box_muller_fast(xa.z, xa.w);
-        const float2 z2 = box_muller_fast(xb.x, xb.y), z3 = box_muller_fast(xb.z, xb.w);
+        const float2 z0 = box_muller_half_turn_fast(xa.x, xa.y), z1 = box_muller_half_turn_fast(xa.z, xa.w);
+        const float2 z2 = box_muller_half_turn_fast(xb.x, xb.y), z3 = box_muller_half_turn_fast(xb.z, xb.w);
         z[0] = z0.x; z[1] = z0.y; z[2] = z1.x; z[3] = z1.y;
         z[4] = z2.x; z[5] = z2.y; z[6] = z3.x; z[7] = z3.y;
     }
-    const float kick = Kn * P.sqrt_dt;
-    const float dtK = (P.dt * K) * sgn, dtKs = P.dt * Ks;
+    const int q = kQ > 0 ? kQ : P.q;
+    const float kick = -(Kn * P.sqrt_dt);
+    const float dtK = (P.dt * K) * sgn;
+    // q = 2: sin 4 pi theta = 2 s c, the 2 taken into the factor (exact)
+    const float dtKs = (kQ == 2 ? 2.0f : 1.0f) * ((q & 1) ? -(P.dt * Ks) : P.dt * Ks);
     uint32_t tno[8], cso[8];
 #pragma unroll
     for (int v = 0; v < 8; ++v) {
         const float th = __uint_as_float(thw[v]);
-        const float2 own = cos_sin_2pi_fast(th);
+        const float2 own = cos_sin_half_turn_fast(th);
         const float coup = own.y * acc[v].x - own.x * acc[v].y;
-        const float shil = sin_q(P.q, own.x, own.y);
+        const float shil = kQ == 2 ? own.x * own.y : sin_q(q, own.x, own.y);
         const float tn = wrap01(th + (dtK * coup - dtKs * shil) + kick * z[v]);
         tno[v] = __float_as_uint(tn);
-        cso[v] = f2_to_h2<H2>(cos_sin_2pi_fast(tn));
+        cso[v] = f2_to_h2<H2>(cos_sin_half_turn_fast(tn));
     }
     st256(theta + at, tno);
     st256(cs_out + at, cso);
@@ -504,6 +513,17 @@ static cudaError_t step_plain(const oim_run_s& r, int64_t t, const int32_t* d_t0
 }
 
 // The 16-bit form's step t: thread = node x octet of replicas (R_pad a multiple of 8).
+template <typename H2, int kQ>
+static void step_octet_q(const oim_run_s& r, const StepParams& P, const StepGrid& q, float* theta,
+                         const H2* cs_in, H2* cs_out, int64_t t, const int32_t* d_t0, cudaStream_t s) {
+    if (r.p->unit_weights)
+        step_octet_kernel<H2, true, kQ><<<q.grid, q.block, 0, s>>>(r.p->csr(), P, theta, cs_in, cs_out, t,
+                                                                  d_t0, (int32_t)t, q.quads_fast);
+    else
+        step_octet_kernel<H2, false, kQ><<<q.grid, q.block, 0, s>>>(r.p->csr(), P, theta, cs_in, cs_out, t,
+                                                                   d_t0, (int32_t)t, q.quads_fast);
+}
+
 template <typename H2>
 static cudaError_t step_octet(const oim_run_s& r, int64_t t, const int32_t* d_t0, cudaStream_t s) {
     const StepParams P = params_of(r);
@@ -513,12 +533,12 @@ static cudaError_t step_octet(const oim_run_s& r, int64_t t, const int32_t* d_t0
     float* theta = r.d_theta[in];
     const H2* cs_in = reinterpret_cast<const H2*>(r.d_cs[in]);
     H2* cs_out = reinterpret_cast<H2*>(r.d_cs[in ^ 1]);
-    if (r.p->unit_weights)
-        step_octet_kernel<H2, true><<<q.grid, q.block, 0, s>>>(r.p->csr(), P, theta, cs_in, cs_out, t, d_t0,
-                                                              (int32_t)t, q.quads_fast);
+    if (P.q == 2)
+        step_octet_q<H2, 2>(r, P, q, theta, cs_in, cs_out, t, d_t0, s);
+    else if (P.q == 3)
+        step_octet_q<H2, 3>(r, P, q, theta, cs_in, cs_out, t, d_t0, s);
     else
-        step_octet_kernel<H2, false><<<q.grid, q.block, 0, s>>>(r.p->csr(), P, theta, cs_in, cs_out, t, d_t0,
-                                                               (int32_t)t, q.quads_fast);
+        step_octet_q<H2, 0>(r, P, q, theta, cs_in, cs_out, t, d_t0, s);
     return cudaGetLastError();
 }
 
