@@ -35,10 +35,13 @@ __device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
 __device__ __forceinline__ void philox10_pair(uint4& a, uint4& b, uint32_t k0, uint32_t k1) {
 #pragma unroll
     for (int round = 0; round < 10; ++round) {
-        const uint32_t alo0 = 0xD2511F53u * a.x, ahi0 = __umulhi(0xD2511F53u, a.x);
-        const uint32_t alo1 = 0xCD9E8D57u * a.z, ahi1 = __umulhi(0xCD9E8D57u, a.z);
-        const uint32_t blo0 = 0xD2511F53u * b.x, bhi0 = __umulhi(0xD2511F53u, b.x);
-        const uint32_t blo1 = 0xCD9E8D57u * b.z, bhi1 = __umulhi(0xCD9E8D57u, b.z);
+        // each 32 x 32-bit product whole (low and high words from one wide multiply)
+        const uint64_t pa0 = (uint64_t)0xD2511F53u * a.x, pa1 = (uint64_t)0xCD9E8D57u * a.z;
+        const uint64_t pb0 = (uint64_t)0xD2511F53u * b.x, pb1 = (uint64_t)0xCD9E8D57u * b.z;
+        const uint32_t alo0 = (uint32_t)pa0, ahi0 = (uint32_t)(pa0 >> 32);
+        const uint32_t alo1 = (uint32_t)pa1, ahi1 = (uint32_t)(pa1 >> 32);
+        const uint32_t blo0 = (uint32_t)pb0, bhi0 = (uint32_t)(pb0 >> 32);
+        const uint32_t blo1 = (uint32_t)pb1, bhi1 = (uint32_t)(pb1 >> 32);
         a = make_uint4(ahi1 ^ a.y ^ k0, alo1, ahi0 ^ a.w ^ k1, alo0);
         b = make_uint4(bhi1 ^ b.y ^ k0, blo1, bhi0 ^ b.w ^ k1, blo0);
         k0 += 0x9E3779B9u;
