@@ -156,12 +156,16 @@ int upload_problem(oim_problem_s* p) {
             d[5] = (uint32_t)(v - p->graphs[g].node_off);
             for (int u = 0; u < 2; ++u) {
                 const int64_t e = (int64_t)p->h_rowp[v] + u;
-                d[6 + u] = e < p->h_rowp[v + 1] ? p->h_col[(size_t)e] : (uint32_t)v;
+                d[6 + u] = e < p->h_rowp[v + 1] ? (uint32_t)p->h_col_plain[(size_t)e] : (uint32_t)v;
             }
         }
         OIM_CUDA(dev_alloc(&p->d_sdesc, sdesc.size()), "cudaMalloc(stream slot descriptors)");
         OIM_CUDA(cudaMemcpy(p->d_sdesc, sdesc.data(), sdesc.size() * sizeof(uint32_t), cudaMemcpyHostToDevice),
                  "upload stream slot descriptors");
+        OIM_CUDA(dev_alloc(&p->d_pcol, p->h_col_plain.size()), "cudaMalloc(plain columns)");
+        if (!p->h_col_plain.empty())
+            OIM_CUDA(cudaMemcpy(p->d_pcol, p->h_col_plain.data(), p->h_col_plain.size() * 4, cudaMemcpyHostToDevice),
+                     "upload plain columns");
     }
     OIM_CUDA(cudaMemcpy(p->d_shead, shead.data(), shead.size() * sizeof(uint4), cudaMemcpyHostToDevice),
              "upload stream row heads");
@@ -244,6 +248,7 @@ void free_problem(oim_problem_s* p) {
     dev_free(p->d_shead);
     dev_free(p->d_arow);
     dev_free(p->d_sdesc);
+    dev_free(p->d_pcol);
     dev_free(p->d_graphs);
     dev_free(p->d_urowp);
     dev_free(p->d_ucol);

@@ -85,9 +85,12 @@ struct CSRDev {
     // graph (the adjoint step: a warp's nodes then share a graph for its reductions)
     const int4* arow;
     // [nodes][8] the 16-bit stream form's 32-byte slot descriptors, in srow's order:
-    // {node, row start, first -1 entry, row end, graph, local index, first two packed
-    // column words (the slot's own node where the row is shorter: in bounds, never added)}
+    // {node, row start, first -1 entry, row end, graph, local index, first two column
+    // indices (the slot's own node where the row is shorter: in bounds, never added)}
     const uint32_t* sdesc;
+    // [nnz] column indices without the sign bit (the 16-bit stream form knows a +-1
+    // entry's sign from its position against the row's first -1 entry)
+    const int32_t* pcol;
 };
 
 }  // namespace oim
@@ -122,11 +125,12 @@ struct oim_problem_s {
     uint4* d_shead = nullptr;      // and the first four column words of each of those rows
     int4* d_arow = nullptr;        // adjoint row descriptors, graph by graph
     uint32_t* d_sdesc = nullptr;   // 32-byte slot descriptors of the 16-bit stream form
+    int32_t* d_pcol = nullptr;     // column indices without sign bits
     int32_t max_n = 0;             // largest graph
     oim::CSRDev csr() const {
         return oim::CSRDev{d_rowp, d_col, unit_weights ? nullptr : d_w, d_node_graph, d_split,
                            d_order, d_graphs, G, (int32_t)nodes, d_urowp, d_ucol,
-                           unit_weights ? nullptr : d_uw, d_srow, d_shead, d_arow, d_sdesc};
+                           unit_weights ? nullptr : d_uw, d_srow, d_shead, d_arow, d_sdesc, d_pcol};
     }
 };
 

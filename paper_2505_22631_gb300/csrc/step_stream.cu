@@ -238,7 +238,7 @@ __device__ __forceinline__ uint32_t f2_to_h2(float2 f) {
 
 // The 16-bit form: thread = node x octet of eight consecutive replicas.  A slot's
 // 32-byte descriptor {node, row start, first -1 entry, row end, graph, local index,
-// first two column words} arrives in one load, so the first two neighbours' pairs
+// first two column indices} arrives in one load, so the first two neighbours' pairs
 // are requested one dependent load after launch and the node's graph and Philox
 // counter need no further lookups.
 //
@@ -281,8 +281,8 @@ __global__ void __launch_bounds__(256, 5) step_octet_kernel(CSRDev csr, StepPara
     float sgn = 1.0f;
     if constexpr (kUnit) {
         uint32_t h0[8], h1[8];
-        ld256_nc(cs_base + (size_t)(d[6] & ~kSignBit) * stride, h0);
-        ld256_nc(cs_base + (size_t)(d[7] & ~kSignBit) * stride, h1);
+        ld256_nc(cs_base + (size_t)d[6] * stride, h0);
+        ld256_nc(cs_base + (size_t)d[7] * stride, h1);
         if (e_beg < e_end) {
             if (e_beg == e_split) rsub8<H2>(acc, h0);
             else add8<H2>(acc, h0);
@@ -294,25 +294,25 @@ __global__ void __launch_bounds__(256, 5) step_octet_kernel(CSRDev csr, StepPara
         int e = e_beg + 2;
         for (; e < e_split; ++e) {
             uint32_t v[8];
-            ld256_nc(cs_base + (size_t)(__ldg(csr.col + e) & ~kSignBit) * stride, v);
+            ld256_nc(cs_base + (size_t)__ldg(csr.pcol + e) * stride, v);
             add8<H2>(acc, v);
         }
         if (e == e_split && e < e_end) {
             uint32_t v[8];
-            ld256_nc(cs_base + (size_t)(__ldg(csr.col + e) & ~kSignBit) * stride, v);
+            ld256_nc(cs_base + (size_t)__ldg(csr.pcol + e) * stride, v);
             rsub8<H2>(acc, v);
             ++e;
         }
         for (; e < e_end; ++e) {
             uint32_t v[8];
-            ld256_nc(cs_base + (size_t)(__ldg(csr.col + e) & ~kSignBit) * stride, v);
+            ld256_nc(cs_base + (size_t)__ldg(csr.pcol + e) * stride, v);
             add8<H2>(acc, v);
         }
         if (e_split < e_end) sgn = -1.0f;   // the accumulators hold -(A, B)
     } else {
         for (int e = e_beg; e < e_end; ++e) {
             uint32_t v[8];
-            ld256_nc(cs_base + (size_t)__ldg(csr.col + e) * stride, v);
+            ld256_nc(cs_base + (size_t)__ldg(csr.pcol + e) * stride, v);
             const float w = __ldg(csr.w + e);
             const float2 ww = make_float2(w, w);
 #pragma unroll
