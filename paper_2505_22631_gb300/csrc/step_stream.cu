@@ -274,7 +274,9 @@ __global__ void __launch_bounds__(256, 5) step_octet_kernel(CSRDev csr, StepPara
     ld256_nc(csr.sdesc + (size_t)slot * 8, d);
     const int node = (int)d[0], e_beg = (int)d[1], e_split = (int)d[2], e_end = (int)d[3];
     const char* cs_base = reinterpret_cast<const char*>(cs_in) + (size_t)oct * 32;
-    const size_t stride = (size_t)P.R_pad * sizeof(uint32_t);   // bytes per node row
+    // bytes per node row (R_pad <= 2^20: 32 bits), so that a neighbour's address is one
+    // 32 x 32 -> 64-bit multiply-add
+    const uint32_t stride = (uint32_t)P.R_pad * (uint32_t)sizeof(uint32_t);
     float2 acc[8];
 #pragma unroll
     for (int v = 0; v < 8; ++v) acc[v] = make_float2(0.f, 0.f);
@@ -292,27 +294,29 @@ __global__ void __launch_bounds__(256, 5) step_octet_kernel(CSRDev csr, StepPara
             else add8<H2>(acc, h1);
         }
         int e = e_beg + 2;
-        for (; e < e_split; ++e) {
+        const uint32_t* cp = reinterpret_cast<const uint32_t*>(csr.pcol) + e;
+        for (; e < e_split; ++e, ++cp) {
             uint32_t v[8];
-            ld256_nc(cs_base + (size_t)__ldg(csr.pcol + e) * stride, v);
+            ld256_nc(cs_base + (size_t)__ldg(cp) * stride, v);
             add8<H2>(acc, v);
         }
         if (e == e_split && e < e_end) {
             uint32_t v[8];
-            ld256_nc(cs_base + (size_t)__ldg(csr.pcol + e) * stride, v);
+            ld256_nc(cs_base + (size_t)__ldg(cp) * stride, v);
             rsub8<H2>(acc, v);
             ++e;
+            ++cp;
         }
-        for (; e < e_end; ++e) {
+        for (; e < e_end; ++e, ++cp) {
             uint32_t v[8];
-            ld256_nc(cs_base + (size_t)__ldg(csr.pcol + e) * stride, v);
+            ld256_nc(cs_base + (size_t)__ldg(cp) * stride, v);
             add8<H2>(acc, v);
         }
         if (e_split < e_end) sgn = -1.0f;   // the accumulators hold -(A, B)
     } else {
         for (int e = e_beg; e < e_end; ++e) {
             uint32_t v[8];
-            ld256_nc(cs_base + (size_t)__ldg(csr.pcol + e) * stride, v);
+            ld256_nc(cs_base + (size_t)(uint32_t)__ldg(csr.pcol + e) * stride, v);
             const float w = __ldg(csr.w + e);
             const float2 ww = make_float2(w, w);
 #pragma unroll
