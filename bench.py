@@ -276,7 +276,7 @@ def first_hit(trace_best, target):
     return int(hit[0]) if hit.size else None
 
 
-def kernels_per_run(form, steps, readout_every):
+def kernels_per_run(form, steps, readout_every, dense_members=0):
     """Kernels of this library that one run enqueues (memsets and copies excluded)."""
     readouts = steps // readout_every if readout_every > 0 else 0
     # the per-step forms first store the run's seed on the device (one tiny kernel)
@@ -284,6 +284,9 @@ def kernels_per_run(form, steps, readout_every):
         return 1
     if form == 3:          # dense: init, a step kernel per step, relayout + spins + score per readout,
         return 1 + 1 + steps + 3 * readouts + 1   # final relayout
+    if form == 4:          # mixed: inits, the CSR step and one step per dense member each step,
+        nd = dense_members  # the dense relayouts + spins + score per readout, final relayouts
+        return 1 + (1 + nd) + (1 + nd) * steps + (2 + nd) * readouts + nd
     return 1 + 1 + steps + 2 * readouts   # stream: init, a step kernel per step, spins + score per readout
 
 
@@ -295,6 +298,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="torus_er2000")
     ap.add_argument("--form", default="auto")
+    ap.add_argument("--graph-forms", default="",
+                    help="with --form mixed: stream or gemm per graph, comma-separated")
     ap.add_argument("--precision", default="auto")
     ap.add_argument("--readout-every", type=int, default=50)
     ap.add_argument("--e2e-steps", type=int, default=3)
@@ -345,11 +350,14 @@ def main():
         policy = capi.OIM_PREC_FP32 if args.precision == "fp32" else capi.OIM_PREC_AUTO
         o, us = capi.oim_autotune(prob.handle, w.replicas, policy, 200)
         form, precision, rpb, threads = o.form, o.precision, o.replicas_per_block, o.threads_per_block
+        graph_forms = capi.graph_forms_of(o, len(w.graphs))
         tuned = {"form": o.form, "precision": o.precision, "replicas_per_block": rpb,
-                 "threads_per_block": threads, "probe_us_per_step": us}
+                 "threads_per_block": threads, "probe_us_per_step": us, "graph_forms": graph_forms}
+    else:
+        graph_forms = [capi.FORMS[f] for f in args.graph_forms.split(",")] if args.graph_forms else None
     run = Run(prob, dK, dKs, dKn, w.dt, w.steps, w.replicas, seed_base, form=form,
               precision=precision, readout_every=args.readout_every, stream=stream,
-              replicas_per_block=rpb, threads_per_block=threads)
+              replicas_per_block=rpb, threads_per_block=threads, graph_forms=graph_forms)
     info = run.info()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
@@ -392,10 +400,10 @@ def main():
     # own average launch duration comes from runs of the same steps without readouts
     # (CUDA events around each run, divided by its steps; L2 flushed between runs)
     ms_kernel_run = ms_step
-    if info["form"] in (1, 3):
+    if info["form"] in (1, 3, 4):
         bare = Run(prob, dK, dKs, dKn, w.dt, w.steps, w.replicas, seed_base + 50, form=form,
                    precision=precision, readout_every=0, stream=stream,
-                   replicas_per_block=rpb, threads_per_block=threads)
+                   replicas_per_block=rpb, threads_per_block=threads, graph_forms=graph_forms)
         bare.sync()
         kt = []
         for k in range(3):
@@ -409,8 +417,9 @@ def main():
         bare.close()
         ms_kernel_run = float(np.mean(kt))
     prec_name = {1: "fp32", 2: "bf16", 3: "fp16"}.get(info["precision"])
-    kname = {2: f"resident_quad_kernel<{prec_name}>", 1: "step_stream_kernel",
-             3: "gemm_step_kernel"}.get(info["form"], "?")
+    kname = {2: f"resident_quad_kernel<{prec_name}>",
+             1: "step_stream_kernel" if info["precision"] == 1 else "step_octet_kernel",
+             3: "gemm_step_kernel", 4: "step_octet_kernel + gemm_step_kernel"}.get(info["form"], "?")
     traffic = profiled_traffic(kname, w.name)
     if info["form"] == 3:
         n = w.graphs[0].n
@@ -429,7 +438,11 @@ def main():
                     "us_per_launch": ms_kernel_run * 1e3 / w.steps}
     else:
         node_replica_steps = w.nodes * w.replicas * w.steps
-        csr_bytes = sum(4 * g.nnz + 8 * (g.n + 1) for g in w.graphs) * w.steps
+        dense = [gi for gi, f in enumerate(graph_forms or []) if f == capi.OIM_FORM_GEMM]
+        # the CSR structure of the stream-form graphs, and for the dense members of a
+        # mixed run their BF16 coupling matrix, once per step
+        csr_bytes = sum(4 * g.nnz + 8 * (g.n + 1) for gi, g in enumerate(w.graphs) if gi not in dense) * w.steps
+        csr_bytes += sum(2 * w.graphs[gi].n ** 2 for gi in dense) * w.steps
         bytes_per_unit = 24 if info["precision"] == 1 else 16
         alg_bytes = node_replica_steps * bytes_per_unit + csr_bytes
         achieved = alg_bytes / (ms_kernel_run / 1e3) / 1e9
@@ -461,6 +474,8 @@ def main():
         + 3 * K.size * 4
     d2h = spins_h.numel() + score_h.numel() * 8 + best_h.numel() * 4
 
+    forms_arr = None if graph_forms is None else np.ascontiguousarray(graph_forms, dtype=np.int32)
+
     def e2e_step(seed):
         hs = [C.oim_create_problem(n, w.q, c.shape[0], rp, c, ww, 2) for n, rp, c, ww in host_graphs]
         hb = C.oim_create_batch(hs) if len(hs) > 1 else hs[0]
@@ -469,6 +484,8 @@ def main():
         o.precision = run.opts.precision
         o.replicas_per_block = run.opts.replicas_per_block
         o.threads_per_block = run.opts.threads_per_block
+        if forms_arr is not None:
+            o.graph_forms = forms_arr.ctypes.data
         o.readout_every = args.readout_every
         o.stream = int(stream.cuda_stream)
         hr = C.oim_run(hb, pin["K"], pin["Ks"], pin["Kn"], w.dt, w.steps, w.replicas, seed, o)
@@ -502,7 +519,9 @@ def main():
                    "nodes": [g.n for g in w.graphs], "nnz": [g.nnz for g in w.graphs],
                    "replicas": w.replicas, "euler_steps": w.steps,
                    "readout_every": args.readout_every,
-                   "form": {0: "auto", 1: "stream", 2: "resident", 3: "gemm"}[info["form"]],
+                   "form": {0: "auto", 1: "stream", 2: "resident", 3: "gemm", 4: "mixed"}[info["form"]],
+                   "graph_forms": None if graph_forms is None else
+                   [{1: "stream", 3: "gemm"}[f] for f in graph_forms],
                    "precision": {1: "fp32", 2: "bf16", 3: "fp16"}.get(info["precision"]),
                    "l2": "256 MB buffer written between timed steps (outside the events)",
                    "autotuned": tuned,
@@ -511,7 +530,9 @@ def main():
         "clocks": clocks,
         "e2e": e2e,
         "node_updates_per_s": node_updates_per_s,
-        "gpu_launches": args.steps * kernels_per_run(info["form"], w.steps, args.readout_every),
+        "gpu_launches": args.steps * kernels_per_run(
+            info["form"], w.steps, args.readout_every,
+            sum(1 for f in (graph_forms or []) if f == capi.OIM_FORM_GEMM)),
         "wall_s_timed_region": wall,
         "step_ms_all": ms,
     }
@@ -526,7 +547,7 @@ def main():
 
     if rank == 0 and not args.no_quality:
         line["quality"] = quality(w, prob, problems, args, stream, ms_step,
-                                  (form, precision, rpb, threads))
+                                  (form, precision, rpb, threads, graph_forms))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_oracle_sample(w)
     if rank == 0:
@@ -626,10 +647,11 @@ def quality(w, prob, problems, args, stream, ms_step_chosen, chosen_cfg):
     G = len(w.graphs)
     seeds = [777 + 13 * k for k in range(args.quality_seeds)]
     # best known: best score of a 4x longer run of the chosen form
-    form, precision, rpb, threads = chosen_cfg
+    form, precision, rpb, threads, graph_forms = chosen_cfg
     K4, Ks4, Kn4, T4 = stretched(w, 4)
     long = Run(prob, K4, Ks4, Kn4, w.dt, T4, w.replicas, 4242, form=form, precision=precision,
-               readout_every=re * 4, stream=stream, replicas_per_block=rpb, threads_per_block=threads)
+               readout_every=re * 4, stream=stream, replicas_per_block=rpb, threads_per_block=threads,
+               graph_forms=graph_forms)
     tr = long.readout(spins=False)["trace"]
     long.close()
     best_known = tr.max(axis=(1, 2)) if q2 else tr.min(axis=(1, 2))
@@ -663,7 +685,7 @@ def quality(w, prob, problems, args, stream, ms_step_chosen, chosen_cfg):
         plain_runs.append(pr)
     chosen_run = Run(prob, K, Ks, Kn, w.dt, w.steps, w.replicas, seeds[0], form=form,
                      precision=precision, readout_every=re, stream=stream, replicas_per_block=rpb,
-                     threads_per_block=threads)
+                     threads_per_block=threads, graph_forms=graph_forms)
     per_seed = []
     for sd in seeds:
         chosen_run.rerun(K, Ks, Kn, w.dt, w.steps, sd)

@@ -59,6 +59,10 @@ extern "C" {
                               /* replicas of one graph in shared memory           */
 #define OIM_FORM_GEMM      3  /* dense coupling on the tensor cores (BF16 W x     */
                               /* [cos|sin], FP32 accumulate), one launch per step */
+#define OIM_FORM_MIXED     4  /* a batch whose graphs take the form given per     */
+                              /* graph in oim_run_opts.graph_forms: the CSR       */
+                              /* members step together in the stream form, each   */
+                              /* dense member on the tensor cores, every step     */
 
 /* ---- storage precision of the (cos, sin) cache the coupling reads --------- */
 #define OIM_PREC_AUTO 0
@@ -92,7 +96,10 @@ typedef struct oim_run_opts {
                                 /* (256-wide tiles)                                */
     int32_t checkpoint_every;   /* keep phases every this many steps for           */
                                 /* oim_backward (0: no checkpoints)                */
-    int32_t reserved[8];
+    const int32_t* graph_forms; /* OIM_FORM_MIXED: int32[graphs], OIM_FORM_STREAM  */
+                                /* or OIM_FORM_GEMM for each graph of the batch    */
+                                /* (read by oim_run; NULL otherwise)               */
+    int32_t reserved[6];
 } oim_run_opts;
 
 /* Fill *opts with the defaults: AUTO form and precision, readout at the end,
@@ -225,6 +232,11 @@ int oim_debug_derivative(oim_problem_t p, const float* theta, int32_t replicas, 
  * per problem shape.
  *   precision_policy  OIM_PREC_AUTO (16-bit caches and BF16 allowed) or
  *                     OIM_PREC_FP32 (FP32 forms only)
+ * For a batch under OIM_PREC_AUTO the mixed form is a candidate too: members that
+ * look dense are probed on the tensor cores beside the others in the 16-bit stream
+ * form, and when the mixed form wins, best->form is OIM_FORM_MIXED and
+ * best->graph_forms points to the per-graph choice (owned by the library, valid for
+ * the life of the process).
  * Decisions are cached for the process, keyed by graph sizes, nonzeros, q,
  * replicas and policy.  Synchronous.  Errors: OIM_EINVAL, OIM_EUNSUPPORTED (no
  * candidate ran), OIM_ECUDA.

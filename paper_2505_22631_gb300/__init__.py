@@ -95,7 +95,9 @@ class Run:
 
     def __init__(self, problem: Problem, K, Ks, Kn, dt, steps, replicas, seed, form="auto",
                  precision="auto", readout_every=0, stream=None, use_graph=True,
-                 replicas_per_block=0, threads_per_block=0):
+                 replicas_per_block=0, threads_per_block=0, graph_forms=None):
+        """graph_forms (form "mixed"): one of "stream" / "gemm" (or the OIM_FORM_* values)
+        per graph of the batch."""
         self.problem = problem
         o = oim_default_opts()
         o.form = FORMS[form] if isinstance(form, str) else int(form)
@@ -105,10 +107,16 @@ class Run:
         o.use_graph = int(bool(use_graph))
         o.replicas_per_block = int(replicas_per_block)
         o.threads_per_block = int(threads_per_block)
+        forms = None
+        if graph_forms is not None:
+            forms = np.ascontiguousarray([FORMS[f] if isinstance(f, str) else int(f) for f in graph_forms],
+                                         dtype=np.int32)
+            o.graph_forms = forms.ctypes.data
         self.opts = o
         G = problem.graphs
         self._sched = [_schedule(s, G, steps) for s in (K, Ks, Kn)]
         self.handle = oim_run(problem.handle, *self._sched, dt, steps, replicas, seed, o)
+        self.opts.graph_forms = None   # read by oim_run only
         self.replicas = int(replicas)
 
     def rerun(self, K, Ks, Kn, dt, steps, seed):

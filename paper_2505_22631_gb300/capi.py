@@ -28,6 +28,7 @@ OIM_FORM_AUTO = 0
 OIM_FORM_STREAM = 1
 OIM_FORM_RESIDENT = 2
 OIM_FORM_GEMM = 3
+OIM_FORM_MIXED = 4
 
 OIM_PREC_AUTO = 0
 OIM_PREC_FP32 = 1
@@ -39,7 +40,7 @@ OIM_FLAG_DEFER_UPLOAD = 2
 OIM_NOALLOC_MAX_ACCUM = 131072
 
 FORMS = {"auto": OIM_FORM_AUTO, "stream": OIM_FORM_STREAM, "resident": OIM_FORM_RESIDENT,
-         "gemm": OIM_FORM_GEMM}
+         "gemm": OIM_FORM_GEMM, "mixed": OIM_FORM_MIXED}
 PRECISIONS = {"auto": OIM_PREC_AUTO, "fp32": OIM_PREC_FP32, "bf16": OIM_PREC_BF16,
               "fp16": OIM_PREC_FP16}
 
@@ -60,7 +61,8 @@ class oim_run_opts(ctypes.Structure):
         ("replicas_per_block", ctypes.c_int32),
         ("threads_per_block", ctypes.c_int32),
         ("checkpoint_every", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 8),
+        ("graph_forms", ctypes.c_void_p),
+        ("reserved", ctypes.c_int32 * 6),
     ]
 
 
@@ -259,6 +261,14 @@ def oim_autotune(p, replicas, precision_policy=OIM_PREC_AUTO, probe_steps=100, s
     _check(load().oim_autotune(p, int(replicas), int(precision_policy), int(probe_steps), stream,
                                ctypes.byref(o), ctypes.byref(us)))
     return o, us.value
+
+
+def graph_forms_of(opts, graphs):
+    """The per-graph forms an oim_run_opts carries (OIM_FORM_MIXED), else None."""
+    if opts.form != OIM_FORM_MIXED or not opts.graph_forms:
+        return None
+    arr = ctypes.cast(opts.graph_forms, ctypes.POINTER(ctypes.c_int32))
+    return [int(arr[g]) for g in range(graphs)]
 
 
 def oim_schedule_triangular(steps, ks_max, periods):

@@ -3,7 +3,10 @@
 // Candidates (filtered by the precision policy and by what the problem allows):
 // the resident form with a 16-bit or FP32 cache, at the planner's replicas per
 // block and at half / double that, with 1024 or 512 threads; the FP32 stream
-// form; the dense tensor-core form (one graph).  Each candidate runs a short
+// form; the dense tensor-core form (one graph); for a batch, the mixed form in which
+// the dense-looking members run on the tensor cores and the rest in the 16-bit stream
+// form (each member that looks dense is first probed alone in that role, and kept
+// there only if the batch steps faster).  Each candidate runs a short
 // probe (same graph, replicas and coupling scale as the real run, a neutral
 // schedule) twice and is timed with CUDA events on a private stream; the fastest
 // wins.  Decisions are cached for the life of the process, keyed by the graphs'
@@ -28,6 +31,7 @@ namespace {
 struct TuneResult {
     oim_run_opts opts;
     double us_per_step;
+    std::vector<int32_t> graph_forms;   // the mixed form's choice per graph (else empty)
 };
 
 std::mutex g_tune_mutex;
@@ -59,6 +63,7 @@ extern "C" int oim_autotune(oim_problem_t p, int32_t replicas, int32_t precision
         if (it != g_tune_cache.end()) {
             *best = it->second.opts;
             best->stream = stream;
+            best->graph_forms = it->second.graph_forms.empty() ? nullptr : it->second.graph_forms.data();
             if (best_us_per_step) *best_us_per_step = it->second.us_per_step;
             return OIM_OK;
         }
@@ -121,12 +126,12 @@ extern "C" int oim_autotune(oim_problem_t p, int32_t replicas, int32_t precision
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    TuneResult bestr{};
-    bestr.us_per_step = INFINITY;
-    for (auto& o : cands) {
+    // time per step of one candidate (best of two timed reruns), infinite if it cannot run
+    auto probe = [&](oim_run_opts o) -> double {
         o.stream = s;
         oim_run_t r = nullptr;
-        if (oim_run(p, K.data(), Ks.data(), Kn.data(), 0.01f, T, replicas, 12345, &o, &r) != OIM_OK) continue;
+        if (oim_run(p, K.data(), Ks.data(), Kn.data(), 0.01f, T, replicas, 12345, &o, &r) != OIM_OK)
+            return INFINITY;
         double best_ms = INFINITY;
         bool ok = oim_run_sync(r) == OIM_OK;
         for (int rep = 0; rep < 2 && ok; ++rep) {
@@ -138,10 +143,51 @@ extern "C" int oim_autotune(oim_problem_t p, int32_t replicas, int32_t precision
             if (ok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) best_ms = std::min(best_ms, (double)ms);
         }
         oim_destroy_run(r);
-        const double us = best_ms * 1e3 / (double)T;
-        if (ok && us < bestr.us_per_step) {
+        return ok ? best_ms * 1e3 / (double)T : INFINITY;
+    };
+    TuneResult bestr{};
+    bestr.us_per_step = INFINITY;
+    double us_stream16 = INFINITY;
+    for (auto& o : cands) {
+        const double us = probe(o);
+        if (o.form == OIM_FORM_STREAM && o.precision == OIM_PREC_FP16) us_stream16 = us;
+        if (us < bestr.us_per_step) {
             bestr.us_per_step = us;
             bestr.opts = o;
+        }
+    }
+    // a batch: members that look dense (mean degree >= 32 on 256 nodes or more) are tried
+    // one at a time on the tensor cores beside the rest in the 16-bit stream form; those
+    // that make the batch faster than the all-stream form are kept, and the mixed form
+    // with all of them is a candidate
+    if (precision_policy == OIM_PREC_AUTO && G > 1 && std::isfinite(us_stream16)) {
+        oim_run_opts mo;
+        oim_default_opts(&mo);
+        mo.form = OIM_FORM_MIXED;
+        mo.precision = OIM_PREC_FP16;
+        mo.use_graph = 1;
+        std::vector<int32_t> forms((size_t)G, OIM_FORM_STREAM), keep((size_t)G, OIM_FORM_STREAM);
+        int kept = 0;
+        for (int g = 0; g < G; ++g) {
+            const int64_t end = (g + 1 < G) ? p->graphs[g + 1].edge_off : p->nnz;
+            const double deg = (double)(end - p->graphs[g].edge_off) / std::max(1, p->graphs[g].n);
+            if (p->graphs[g].n < 256 || deg < 32.0) continue;
+            forms[(size_t)g] = OIM_FORM_GEMM;
+            mo.graph_forms = forms.data();
+            if (probe(mo) < 0.98 * us_stream16) {
+                keep[(size_t)g] = OIM_FORM_GEMM;
+                ++kept;
+            }
+            forms[(size_t)g] = OIM_FORM_STREAM;
+        }
+        if (kept > 0) {
+            mo.graph_forms = keep.data();
+            const double us = probe(mo);
+            if (us < bestr.us_per_step) {
+                bestr.us_per_step = us;
+                bestr.opts = mo;
+                bestr.graph_forms = keep;
+            }
         }
     }
     cudaEventDestroy(e0);
@@ -149,12 +195,15 @@ extern "C" int oim_autotune(oim_problem_t p, int32_t replicas, int32_t precision
     cudaStreamDestroy(s);
     if (!std::isfinite(bestr.us_per_step)) return fail(OIM_EUNSUPPORTED, "no candidate configuration ran");
     bestr.opts.stream = nullptr;
+    bestr.opts.graph_forms = nullptr;
+    const TuneResult* stored = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
-        g_tune_cache[key] = bestr;
+        stored = &(g_tune_cache[key] = bestr);   // map nodes stay put: graph_forms outlives the call
     }
-    *best = bestr.opts;
+    *best = stored->opts;
     best->stream = stream;
+    best->graph_forms = stored->graph_forms.empty() ? nullptr : stored->graph_forms.data();
     if (best_us_per_step) *best_us_per_step = bestr.us_per_step;
     return OIM_OK;
 }

@@ -331,10 +331,13 @@ int gemm_bn_for(const oim_run_s& r, int n) {
     return cost(112) < cost(128) ? 112 : 128;
 }
 
-// Device state of the dense form, one graph (kept in oim_run_s::gemm).
-int gemm_setup(oim_run_s& r) {
-    const GraphDev& gd = r.p->graphs[0];
-    GemmState& st = r.gemm;
+// Device state of the dense form for graph `graph` of the problem, appended to
+// oim_run_s::gemms (the dense form's one graph, or a dense member of a mixed run).
+int gemm_setup(oim_run_s& r, int graph) {
+    const GraphDev& gd = r.p->graphs[graph];
+    r.gemms.emplace_back();
+    GemmState& st = r.gemms.back();
+    st.graph = graph;
     st.n = gd.n;
     st.bn = gemm_bn_for(r, gd.n);
     st.tiles_n = (gd.n + st.bn - 1) / st.bn;
@@ -349,7 +352,7 @@ int gemm_setup(oim_run_s& r) {
     e = cudaMemset(st.w, 0, (size_t)st.n_pad * st.n_pad * sizeof(__nv_bfloat16));
     if (e == cudaSuccess) e = cudaMemset(st.x[1], 0, 2 * nth * sizeof(__nv_bfloat16));
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemset(dense form)");
-    gemm_scatter_kernel<<<(gd.n + 255) / 256, 256>>>(r.p->csr(), 0, st.n_pad,
+    gemm_scatter_kernel<<<(gd.n + 255) / 256, 256>>>(r.p->csr(), graph, st.n_pad,
                                                      reinterpret_cast<__nv_bfloat16*>(st.w));
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "dense coupling matrix");
@@ -371,47 +374,43 @@ int gemm_setup(oim_run_s& r) {
 }
 
 void gemm_free(oim_run_s& r) {
-    GemmState& st = r.gemm;
-    cudaFree(st.theta);
-    cudaFree(st.x[0]);
-    cudaFree(st.x[1]);
-    cudaFree(st.w);
-    st = GemmState{};
+    for (GemmState& st : r.gemms) {
+        cudaFree(st.theta);
+        cudaFree(st.x[0]);
+        cudaFree(st.x[1]);
+        cudaFree(st.w);
+    }
+    r.gemms.clear();
 }
 
 StepParams make_params(const oim_run_s& r);
 
-cudaError_t launch_gemm_init(const oim_run_s& r, cudaStream_t s) {
-    const GemmState& st = r.gemm;
+cudaError_t launch_gemm_init(const oim_run_s& r, int k, cudaStream_t s) {
+    const GemmState& st = r.gemms[k];
     const int64_t total = (int64_t)r.R_pad * st.n_pad;
     gemm_init_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
-        st.n, st.n_pad, r.R_pad, r.d_seed, 0, st.theta, reinterpret_cast<__nv_bfloat16*>(st.x[0]));
+        st.n, st.n_pad, r.R_pad, r.d_seed, st.graph, st.theta, reinterpret_cast<__nv_bfloat16*>(st.x[0]));
     return cudaGetLastError();
 }
 
-cudaError_t launch_gemm_step_at(const oim_run_s& r, int64_t t, const int32_t* d_t0, cudaStream_t s);
-
-cudaError_t launch_gemm_step(const oim_run_s& r, int64_t t, cudaStream_t s) {
-    return launch_gemm_step_at(r, t, nullptr, s);
-}
-
-// With d_t0 the step is *d_t0 + t (t the offset in a replayed chunk, whose parity is
-// the step's: chunks have an even length).
-cudaError_t launch_gemm_step_at(const oim_run_s& r, int64_t t, const int32_t* d_t0, cudaStream_t s) {
-    const GemmState& st = r.gemm;
+// Step t of dense state k.  With d_t0 the step is *d_t0 + t (t the offset in a replayed
+// chunk, whose parity is the step's: chunks have an even length).
+cudaError_t launch_gemm_step_at(const oim_run_s& r, int k, int64_t t, const int32_t* d_t0, cudaStream_t s) {
+    const GemmState& st = r.gemms[k];
     const StepParams P = make_params(r);
+    const size_t soff = (size_t)st.graph * P.steps;   // the graph's row of the schedules
     GemmArgs a;
     a.theta = st.theta;
     a.x_out = reinterpret_cast<__nv_bfloat16*>(st.x[(t + 1) & 1]);
-    a.K = P.K;
-    a.Ks = P.Ks;
-    a.Kn = P.Kn;
+    a.K = P.K + soff;
+    a.Ks = P.Ks + soff;
+    a.Kn = P.Kn + soff;
     a.t = t;
     a.t0 = d_t0;
     a.dt = P.dt;
     a.sqrt_dt = P.sqrt_dt;
     a.seed = r.d_seed;
-    a.graph = 0;
+    a.graph = st.graph;
     a.q = P.q;
     a.n = st.n;
     a.n_pad = st.n_pad;
@@ -429,12 +428,12 @@ cudaError_t launch_gemm_step_at(const oim_run_s& r, int64_t t, const int32_t* d_
     return cudaGetLastError();
 }
 
-// the dense form's phases into d_theta[buf] in the common layout
-cudaError_t launch_gemm_to_common(const oim_run_s& r, float* out, cudaStream_t s) {
-    const GemmState& st = r.gemm;
+// dense state k's phases into `out` in the common [node][R_pad] layout
+cudaError_t launch_gemm_to_common(const oim_run_s& r, int k, float* out, cudaStream_t s) {
+    const GemmState& st = r.gemms[k];
     const int64_t total = (int64_t)st.n * r.R_pad;
-    gemm_to_common_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(st.n, st.n_pad, r.R_pad, 0,
-                                                                         st.theta, out);
+    gemm_to_common_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
+        st.n, st.n_pad, r.R_pad, r.p->graphs[st.graph].node_off, st.theta, out);
     return cudaGetLastError();
 }
 

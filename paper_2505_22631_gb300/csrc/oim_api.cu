@@ -40,13 +40,12 @@ cudaError_t launch_cs_from_theta(const oim_run_s& r, const float* theta, float2*
 cudaError_t launch_step_stream_buffers(const oim_run_s& r, int64_t t, const float* th_in,
                                        const float2* cs_in, float* th_out, float2* cs_out,
                                        cudaStream_t s);
-int gemm_setup(oim_run_s& r);
+int gemm_setup(oim_run_s& r, int graph);
 void gemm_free(oim_run_s& r);
-cudaError_t launch_gemm_init(const oim_run_s& r, cudaStream_t s);
+cudaError_t launch_gemm_init(const oim_run_s& r, int k, cudaStream_t s);
 cudaError_t launch_set_seed(uint64_t* d_seed, uint64_t seed, cudaStream_t s);
-cudaError_t launch_gemm_step(const oim_run_s& r, int64_t t, cudaStream_t s);
-cudaError_t launch_gemm_step_at(const oim_run_s& r, int64_t t, const int32_t* d_t0, cudaStream_t s);
-cudaError_t launch_gemm_to_common(const oim_run_s& r, float* out, cudaStream_t s);
+cudaError_t launch_gemm_step_at(const oim_run_s& r, int k, int64_t t, const int32_t* d_t0, cudaStream_t s);
+cudaError_t launch_gemm_to_common(const oim_run_s& r, int k, float* out, cudaStream_t s);
 cudaError_t launch_adj_prep(const oim_run_s& r, const float* theta, const float* lam, float4* Y,
                             cudaStream_t s);
 cudaError_t launch_adj_terminal(const oim_run_s& r, const float4* Y, float* lam, double* loss,
@@ -105,6 +104,69 @@ cudaError_t fetch(std::vector<T>& out, const T* src, size_t count) {
 
 void free_problem(oim_problem_s* p);
 
+// The stream form's slot descriptors for the nodes of the graphs with take[g] set,
+// heaviest row first (a stable sort by row length, so a subset keeps the order it has
+// among all nodes): srow {node, row start, first -1 entry, row end}; shead, the first
+// four packed column words; sdesc (32 bytes) {node, row start, first -1 entry, row end,
+// graph, local index, first two column indices}.  Rows shorter than the heads are
+// padded with the slot's own node (in bounds, never added).
+struct StreamSlots {
+    std::vector<int4> srow;
+    std::vector<uint4> shead;
+    std::vector<uint32_t> sdesc;
+};
+
+StreamSlots build_stream_slots(const oim_problem_s* p, const std::vector<char>& take) {
+    std::vector<int32_t> node_g((size_t)p->nodes);
+    std::vector<int32_t> order;
+    for (int g = 0; g < p->G; ++g)
+        for (int32_t k = 0; k < p->graphs[g].n; ++k) {
+            const int32_t v = p->graphs[g].node_off + k;
+            node_g[(size_t)v] = g;
+            if (take[(size_t)g]) order.push_back(v);
+        }
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+        return p->h_rowp[a + 1] - p->h_rowp[a] > p->h_rowp[b + 1] - p->h_rowp[b];
+    });
+    StreamSlots sl;
+    sl.srow.resize(order.size());
+    sl.shead.resize(order.size());
+    sl.sdesc.resize(order.size() * 8);
+    for (size_t k = 0; k < order.size(); ++k) {
+        const int32_t v = order[k];
+        const int g = node_g[(size_t)v];
+        sl.srow[k] = make_int4(v, p->h_rowp[v], p->h_split[v], p->h_rowp[v + 1]);
+        uint32_t h[4];
+        for (int u = 0; u < 4; ++u) {
+            const int64_t e = (int64_t)p->h_rowp[v] + u;
+            h[u] = e < p->h_rowp[v + 1] ? p->h_col[(size_t)e] : (uint32_t)v;
+        }
+        sl.shead[k] = make_uint4(h[0], h[1], h[2], h[3]);
+        uint32_t* d = sl.sdesc.data() + 8 * k;
+        d[0] = (uint32_t)v;
+        d[1] = (uint32_t)p->h_rowp[v];
+        d[2] = (uint32_t)p->h_split[v];
+        d[3] = (uint32_t)p->h_rowp[v + 1];
+        d[4] = (uint32_t)g;
+        d[5] = (uint32_t)(v - p->graphs[g].node_off);
+        for (int u = 0; u < 2; ++u) {
+            const int64_t e = (int64_t)p->h_rowp[v] + u;
+            d[6 + u] = e < p->h_rowp[v + 1] ? (uint32_t)p->h_col_plain[(size_t)e] : (uint32_t)v;
+        }
+    }
+    return sl;
+}
+
+cudaError_t upload_stream_slots(const StreamSlots& sl, int4* srow, uint4* shead, uint32_t* sdesc) {
+    if (sl.srow.empty()) return cudaSuccess;
+    cudaError_t e = cudaMemcpy(srow, sl.srow.data(), sl.srow.size() * sizeof(int4), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(shead, sl.shead.data(), sl.shead.size() * sizeof(uint4), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(sdesc, sl.sdesc.data(), sl.sdesc.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    return e;
+}
+
 int upload_problem(oim_problem_s* p) {
     OIM_CUDA(dev_alloc(&p->d_rowp, p->h_rowp.size()), "cudaMalloc(row_ptr)");
     OIM_CUDA(dev_alloc(&p->d_col, p->h_col.size()), "cudaMalloc(col)");
@@ -113,62 +175,21 @@ int upload_problem(oim_problem_s* p) {
     OIM_CUDA(dev_alloc(&p->d_split, (size_t)p->nodes), "cudaMalloc(split)");
     OIM_CUDA(dev_alloc(&p->d_order, (size_t)p->nodes), "cudaMalloc(order)");
     OIM_CUDA(dev_alloc(&p->d_graphs, p->graphs.size()), "cudaMalloc(graphs)");
-    OIM_CUDA(dev_alloc(&p->d_srow, (size_t)p->nodes), "cudaMalloc(stream rows)");
     // the stream form's blocks take nodes heaviest rows first across the whole batch, so
     // the blocks that run last are the short ones (longest-processing-time-first order);
-    // each slot's row bounds travel with the node in one 16-byte descriptor
-    std::vector<int32_t> sorder((size_t)p->nodes);
-    for (int64_t i = 0; i < p->nodes; ++i) sorder[i] = (int32_t)i;
-    std::stable_sort(sorder.begin(), sorder.end(), [&](int32_t a, int32_t b) {
-        return p->h_rowp[a + 1] - p->h_rowp[a] > p->h_rowp[b + 1] - p->h_rowp[b];
-    });
-    OIM_CUDA(dev_alloc(&p->d_shead, (size_t)p->nodes), "cudaMalloc(stream row heads)");
-    std::vector<int4> srow((size_t)p->nodes);
-    std::vector<uint4> shead((size_t)p->nodes);
-    for (size_t k = 0; k < sorder.size(); ++k) {
-        const int32_t v = sorder[k];
-        srow[k] = make_int4(v, p->h_rowp[v], p->h_split[v], p->h_rowp[v + 1]);
-        uint32_t h[4];
-        for (int u = 0; u < 4; ++u) {
-            const int64_t e = (int64_t)p->h_rowp[v] + u;
-            h[u] = e < p->h_rowp[v + 1] ? p->h_col[(size_t)e] : (uint32_t)v;
-        }
-        shead[k] = make_uint4(h[0], h[1], h[2], h[3]);
-    }
-    OIM_CUDA(cudaMemcpy(p->d_srow, srow.data(), srow.size() * sizeof(int4), cudaMemcpyHostToDevice),
-             "upload stream rows");
-    // the 16-bit stream form's slot descriptors: one 32-byte load gives a slot's node, row
-    // bounds, graph, local index and first two column words
+    // each slot's row bounds travel with the node in its descriptors
     {
-        std::vector<int32_t> node_g((size_t)p->nodes);
-        for (int g = 0; g < p->G; ++g)
-            for (int32_t k = 0; k < p->graphs[g].n; ++k) node_g[(size_t)p->graphs[g].node_off + k] = g;
-        std::vector<uint32_t> sdesc((size_t)p->nodes * 8);
-        for (size_t k = 0; k < sorder.size(); ++k) {
-            const int32_t v = sorder[k];
-            const int g = node_g[(size_t)v];
-            uint32_t* d = sdesc.data() + 8 * k;
-            d[0] = (uint32_t)v;
-            d[1] = (uint32_t)p->h_rowp[v];
-            d[2] = (uint32_t)p->h_split[v];
-            d[3] = (uint32_t)p->h_rowp[v + 1];
-            d[4] = (uint32_t)g;
-            d[5] = (uint32_t)(v - p->graphs[g].node_off);
-            for (int u = 0; u < 2; ++u) {
-                const int64_t e = (int64_t)p->h_rowp[v] + u;
-                d[6 + u] = e < p->h_rowp[v + 1] ? (uint32_t)p->h_col_plain[(size_t)e] : (uint32_t)v;
-            }
-        }
-        OIM_CUDA(dev_alloc(&p->d_sdesc, sdesc.size()), "cudaMalloc(stream slot descriptors)");
-        OIM_CUDA(cudaMemcpy(p->d_sdesc, sdesc.data(), sdesc.size() * sizeof(uint32_t), cudaMemcpyHostToDevice),
-                 "upload stream slot descriptors");
+        StreamSlots sl = build_stream_slots(p, std::vector<char>((size_t)p->G, 1));
+        OIM_CUDA(dev_alloc(&p->d_srow, sl.srow.size()), "cudaMalloc(stream rows)");
+        OIM_CUDA(dev_alloc(&p->d_shead, sl.shead.size()), "cudaMalloc(stream row heads)");
+        OIM_CUDA(dev_alloc(&p->d_sdesc, sl.sdesc.size()), "cudaMalloc(stream slot descriptors)");
+        OIM_CUDA(upload_stream_slots(sl, p->d_srow, p->d_shead, p->d_sdesc), "upload stream slots");
         OIM_CUDA(dev_alloc(&p->d_pcol, p->h_col_plain.size()), "cudaMalloc(plain columns)");
         if (!p->h_col_plain.empty())
-            OIM_CUDA(cudaMemcpy(p->d_pcol, p->h_col_plain.data(), p->h_col_plain.size() * 4, cudaMemcpyHostToDevice),
+            OIM_CUDA(cudaMemcpy(p->d_pcol, p->h_col_plain.data(), p->h_col_plain.size() * 4,
+                                cudaMemcpyHostToDevice),
                      "upload plain columns");
     }
-    OIM_CUDA(cudaMemcpy(p->d_shead, shead.data(), shead.size() * sizeof(uint4), cudaMemcpyHostToDevice),
-             "upload stream row heads");
     // the adjoint's descriptors: graph by graph, each graph's rows by decreasing length
     OIM_CUDA(dev_alloc(&p->d_arow, (size_t)p->nodes), "cudaMalloc(adjoint rows)");
     std::vector<int4> arow((size_t)p->nodes);
@@ -282,6 +303,10 @@ void free_run_buffers(oim_run_s* r) {
     dev_free(r->d_t0);
     dev_free(r->d_items);
     dev_free(r->d_ckpt);
+    dev_free(r->d_srow_sub);
+    dev_free(r->d_shead_sub);
+    dev_free(r->d_sdesc_sub);
+    r->sub_slots = -1;
     gemm_free(*r);
     if (r->chunk_exec) cudaGraphExecDestroy(r->chunk_exec);
     r->chunk_exec = nullptr;
@@ -338,8 +363,31 @@ int ensure_step_buffers(oim_run_s* r, int64_t steps) {
 int choose_form(oim_run_s* r) {
     int form = r->opts.form;
     int prec = r->opts.precision;
-    if (form < OIM_FORM_AUTO || form > OIM_FORM_GEMM) return fail(OIM_EINVAL, "unknown form");
+    if (form < OIM_FORM_AUTO || form > OIM_FORM_MIXED) return fail(OIM_EINVAL, "unknown form");
     if (prec < OIM_PREC_AUTO || prec > OIM_PREC_FP16) return fail(OIM_EINVAL, "unknown precision");
+    if (form == OIM_FORM_MIXED) {
+        // graph_forms names each graph's form: the CSR members step together in the
+        // stream form with the cache precision asked for (FP16 by default), each dense
+        // member on the tensor cores (BF16 operands)
+        if (!r->opts.graph_forms) return fail(OIM_EINVAL, "OIM_FORM_MIXED needs graph_forms");
+        if (r->opts.checkpoint_every > 0)
+            return fail(OIM_EUNSUPPORTED, "checkpoints (for oim_backward) need the FP32 stream form");
+        if (r->opts.threads_per_block != 0 && r->opts.threads_per_block != 320 &&
+            r->opts.threads_per_block != 576)
+            return fail(OIM_EINVAL, "mixed form: threads_per_block is 0, 320 or 576 (the dense members' tiles)");
+        r->graph_forms.assign(r->opts.graph_forms, r->opts.graph_forms + r->p->G);
+        bool dense = false;
+        for (int32_t f : r->graph_forms) {
+            if (f != OIM_FORM_STREAM && f != OIM_FORM_GEMM)
+                return fail(OIM_EINVAL, "graph_forms entries are OIM_FORM_STREAM or OIM_FORM_GEMM");
+            dense |= f == OIM_FORM_GEMM;
+        }
+        r->form = OIM_FORM_MIXED;
+        r->prec = prec == OIM_PREC_AUTO ? OIM_PREC_FP16 : prec;
+        // X^T tiles hold 64 replicas; the 16-bit stream form moves octets
+        r->R_pad = dense ? (r->R + 63) & ~63 : (r->prec == OIM_PREC_FP32 ? (r->R + 3) & ~3 : (r->R + 7) & ~7);
+        return OIM_OK;
+    }
     if (form == OIM_FORM_GEMM) {
         if (r->p->G != 1) return fail(OIM_EUNSUPPORTED, "the dense form takes one graph per run");
         if (prec != OIM_PREC_AUTO && prec != OIM_PREC_BF16)
@@ -400,7 +448,7 @@ int allocate_run(oim_run_s* r) {
     OIM_CUDA(dev_alloc(&r->d_err, 1), "cudaMalloc(err)");
     OIM_CUDA(dev_alloc(&r->d_seed, 1), "cudaMalloc(seed)");
     OIM_CUDA(dev_alloc(&r->d_t0, 1), "cudaMalloc(t0)");
-    if (r->form == OIM_FORM_STREAM) {
+    if (r->form == OIM_FORM_STREAM || r->form == OIM_FORM_MIXED) {
         // a step reads and writes only its own node's phases, so they are updated in
         // place (one buffer under both parities); only the (cos, sin) cache, which the
         // neighbours read, needs the second buffer
@@ -411,8 +459,26 @@ int allocate_run(oim_run_s* r) {
         OIM_CUDA(cudaMalloc(&r->d_cs[1], state * pair), "cudaMalloc(cs)");
     }
     if (r->form == OIM_FORM_GEMM) {
-        int rc = gemm_setup(*r);
+        int rc = gemm_setup(*r, 0);
         if (rc != OIM_OK) return rc;
+    }
+    if (r->form == OIM_FORM_MIXED) {
+        std::vector<char> csr_member((size_t)r->p->G, 0);
+        for (int g = 0; g < r->p->G; ++g) {
+            if (r->graph_forms[(size_t)g] == OIM_FORM_GEMM) {
+                int rc = gemm_setup(*r, g);
+                if (rc != OIM_OK) return rc;
+            } else {
+                csr_member[(size_t)g] = 1;
+            }
+        }
+        // the step kernels of the CSR members take only their slots
+        StreamSlots sl = build_stream_slots(r->p, csr_member);
+        OIM_CUDA(dev_alloc(&r->d_srow_sub, sl.srow.size()), "cudaMalloc(member rows)");
+        OIM_CUDA(dev_alloc(&r->d_shead_sub, sl.shead.size()), "cudaMalloc(member row heads)");
+        OIM_CUDA(dev_alloc(&r->d_sdesc_sub, sl.sdesc.size()), "cudaMalloc(member slot descriptors)");
+        OIM_CUDA(upload_stream_slots(sl, r->d_srow_sub, r->d_shead_sub, r->d_sdesc_sub), "upload member slots");
+        r->sub_slots = (int32_t)sl.srow.size();
     }
     if (r->form == OIM_FORM_RESIDENT) {
         const auto& items = r->plan.items;
@@ -438,10 +504,45 @@ cudaError_t launch_advance_t0(int32_t* d_t0, int32_t steps, cudaStream_t s) {
 // least 32 steps; 0 where chunks do not apply (checkpointed runs, runs shorter than a
 // chunk).
 int64_t step_chunk_length(const oim_run_s& r) {
-    if ((r.form != OIM_FORM_STREAM && r.form != OIM_FORM_GEMM) || r.ckpt_every > 0) return 0;
+    if ((r.form != OIM_FORM_STREAM && r.form != OIM_FORM_GEMM && r.form != OIM_FORM_MIXED) || r.ckpt_every > 0)
+        return 0;
     int64_t L = r.readout_every > 0 ? r.readout_every : 64;
     while ((L & 1) || L < 32) L *= 2;
     return (L <= r.steps && L <= (1 << 20)) ? L : 0;
+}
+
+// The per-step forms' work, part by part: the CSR step kernel over the stream form's
+// nodes (every graph of the stream form, the CSR members of a mixed run) and the
+// tensor-core step of each dense graph (the dense form's one graph, the dense members).
+bool has_csr_part(const oim_run_s& r) {
+    return r.form == OIM_FORM_STREAM || (r.form == OIM_FORM_MIXED && r.sub_slots > 0);
+}
+
+cudaError_t init_parts(const oim_run_s& r, cudaStream_t s) {
+    cudaError_t e = has_csr_part(r) ? launch_init_stream(r, s) : cudaSuccess;
+    for (size_t k = 0; k < r.gemms.size() && e == cudaSuccess; ++k) e = launch_gemm_init(r, (int)k, s);
+    return e;
+}
+
+cudaError_t step_parts(const oim_run_s& r, int64_t t, const int32_t* d_t0, cudaStream_t s) {
+    cudaError_t e = has_csr_part(r) ? launch_step_stream(r, t, d_t0, s) : cudaSuccess;
+    for (size_t k = 0; k < r.gemms.size() && e == cudaSuccess; ++k)
+        e = launch_gemm_step_at(r, (int)k, t, d_t0, s);
+    return e;
+}
+
+// the dense graphs' phases into the common layout (readouts and the end of a run)
+cudaError_t common_parts(const oim_run_s& r, cudaStream_t s) {
+    cudaError_t e = cudaSuccess;
+    for (size_t k = 0; k < r.gemms.size() && e == cudaSuccess; ++k)
+        e = launch_gemm_to_common(r, (int)k, r.d_theta[0], s);
+    return e;
+}
+
+// The phases in the common layout after step t (the stream form alternates buffer
+// parity with the step; its two buffers alias, and the other forms keep one).
+float* readout_theta(const oim_run_s& r, int64_t t) {
+    return r.form == OIM_FORM_STREAM ? r.d_theta[(t + 1) & 1] : r.d_theta[0];
 }
 
 // A per-step form as init, steps / L replays of one captured chunk of L steps and its
@@ -450,19 +551,18 @@ int64_t step_chunk_length(const oim_run_s& r) {
 // chunk is captured once per (L, dt, readout period) and kept with the run.
 int enqueue_stream_chunks(oim_run_s* r, int64_t L) {
     cudaStream_t s = r->stream;
-    const bool dense = r->form == OIM_FORM_GEMM;
     // one step (offset t from *d_t0, or the step t itself) and, where a readout falls,
-    // its score pass (the dense form first copies its phases to the common layout)
+    // its score pass (dense graphs first copy their phases to the common layout)
     auto step = [&](int64_t t, const int32_t* d_t0, cudaStream_t q) -> cudaError_t {
-        cudaError_t x = dense ? launch_gemm_step_at(*r, t, d_t0, q) : launch_step_stream(*r, t, d_t0, q);
+        cudaError_t x = step_parts(*r, t, d_t0, q);
         if (x != cudaSuccess || r->readout_every <= 0 || (t + 1) % r->readout_every != 0) return x;
-        float* th = dense ? r->d_theta[0] : r->d_theta[(t + 1) & 1];
-        if (dense) x = launch_gemm_to_common(*r, th, q);
+        float* th = readout_theta(*r, t);
+        x = common_parts(*r, q);
         if (x != cudaSuccess) return x;
         return d_t0 ? launch_score_at(*r, th, 0, d_t0, (int32_t)(t + 1), q)
                     : launch_score(*r, th, (t + 1) / r->readout_every - 1, q);
     };
-    cudaError_t e = dense ? launch_gemm_init(*r, s) : launch_init_stream(*r, s);
+    cudaError_t e = init_parts(*r, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(r->d_t0, 0, sizeof(int32_t), s);
     if (e != cudaSuccess) return cuda_fail(e, "stream-form launch");
     if (!r->step_chunk_exec || r->step_chunk_len != L || r->step_chunk_dt != r->dt ||
@@ -494,44 +594,33 @@ int enqueue_stream_chunks(oim_run_s* r, int64_t L) {
     const int64_t chunks = r->steps / L;
     for (int64_t c = 0; c < chunks; ++c) OIM_CUDA(cudaGraphLaunch(r->step_chunk_exec, s), "chunk launch");
     for (int64_t t = chunks * L; t < r->steps && e == cudaSuccess; ++t) e = step(t, nullptr, s);
-    if (e == cudaSuccess && dense) e = launch_gemm_to_common(*r, r->d_theta[0], s);
+    if (e == cudaSuccess) e = common_parts(*r, s);
     if (e != cudaSuccess) return cuda_fail(e, "stream-form launch");
     return OIM_OK;
 }
 
-// Queue the stream form: init, then every step, with a score pass after each
-// readout step.  When capture is on, the whole sequence is recorded once into a
-// CUDA graph (kernel arguments baked in) and replayed on later identical runs.
+// Queue a per-step form: init, then every step, with a score pass after each readout
+// step.  When capture is on, the whole sequence is recorded once into a CUDA graph
+// (kernel arguments baked in) and replayed on later identical runs.
 int enqueue_stream_form(oim_run_s* r) {
     const size_t state_bytes = (size_t)r->p->nodes * r->R_pad * sizeof(float);
-    auto body_dense = [&](cudaStream_t s) -> cudaError_t {
-        cudaError_t e = launch_gemm_init(*r, s);
-        for (int64_t t = 0; t < r->steps && e == cudaSuccess; ++t) {
-            e = launch_gemm_step(*r, t, s);
-            if (e == cudaSuccess && r->readout_every > 0 && (t + 1) % r->readout_every == 0) {
-                e = launch_gemm_to_common(*r, r->d_theta[0], s);
-                if (e == cudaSuccess) e = launch_score(*r, r->d_theta[0], (t + 1) / r->readout_every - 1, s);
-            }
-        }
-        if (e == cudaSuccess) e = launch_gemm_to_common(*r, r->d_theta[0], s);
-        return e;
-    };
-    auto body_csr = [&](cudaStream_t s) -> cudaError_t {
-        cudaError_t e = launch_init_stream(*r, s);
+    auto body = [&](cudaStream_t s) -> cudaError_t {
+        cudaError_t e = init_parts(*r, s);
         if (e == cudaSuccess && r->ckpt_every > 0)
             e = cudaMemcpyAsync(r->d_ckpt, r->d_theta[0], state_bytes, cudaMemcpyDeviceToDevice, s);
         for (int64_t t = 0; t < r->steps && e == cudaSuccess; ++t) {
-            e = launch_step_stream(*r, t, nullptr, s);
-            if (e == cudaSuccess && r->readout_every > 0 && (t + 1) % r->readout_every == 0)
-                e = launch_score(*r, r->d_theta[(t + 1) & 1], (t + 1) / r->readout_every - 1, s);
+            e = step_parts(*r, t, nullptr, s);
+            if (e == cudaSuccess && r->readout_every > 0 && (t + 1) % r->readout_every == 0) {
+                e = common_parts(*r, s);
+                if (e == cudaSuccess)
+                    e = launch_score(*r, readout_theta(*r, t), (t + 1) / r->readout_every - 1, s);
+            }
             if (e == cudaSuccess && r->ckpt_every > 0 && (t + 1) % r->ckpt_every == 0)
                 e = cudaMemcpyAsync(r->d_ckpt + (size_t)((t + 1) / r->ckpt_every) * r->p->nodes * r->R_pad,
-                                    r->d_theta[(t + 1) & 1], state_bytes, cudaMemcpyDeviceToDevice, s);
+                                    readout_theta(*r, t), state_bytes, cudaMemcpyDeviceToDevice, s);
         }
+        if (e == cudaSuccess) e = common_parts(*r, s);
         return e;
-    };
-    auto body = [&](cudaStream_t s) -> cudaError_t {
-        return r->form == OIM_FORM_GEMM ? body_dense(s) : body_csr(s);
     };
     if (!r->opts.use_graph) {
         cudaError_t e = body(r->stream);

@@ -52,6 +52,7 @@ struct ResidentPlan {
 
 // Device state of the dense (tensor-core) form of one graph.
 struct GemmState {
+    int graph = 0;                     // graph of the problem (batch index)
     int n = 0, n_pad = 0, bn = 0, tiles_n = 0;   // n_pad: row length and K extent
     float* theta = nullptr;            // [R_pad][n_pad] phases, replica-major
     void* x[2] = {nullptr, nullptr};   // [2 R_pad][n_pad] bf16 (cos; sin) rows, ping-pong
@@ -160,8 +161,15 @@ struct oim_run_s {
     uint64_t* d_seed = nullptr;               // the run's seed, read by the per-step forms
     // resident-form launch plan
     oim::ResidentPlan plan;
-    // dense-form state
-    oim::GemmState gemm;
+    // dense-form state: the graph of the dense form, or the dense members of a mixed run
+    std::vector<oim::GemmState> gemms;
+    // mixed runs: the form of each graph, and the stream form's slot descriptors of the
+    // CSR members only (sub_slots of them; -1 when the step kernels take every node)
+    std::vector<int32_t> graph_forms;
+    int4* d_srow_sub = nullptr;
+    uint4* d_shead_sub = nullptr;
+    uint32_t* d_sdesc_sub = nullptr;
+    int32_t sub_slots = -1;
     int4* d_items = nullptr;                  // plan.items on the device
     // stream-form CUDA graph of a whole run, reused while its shape is unchanged
     cudaGraphExec_t chunk_exec = nullptr;
@@ -216,6 +224,19 @@ private:
 // error reporting (thread-local message)
 int fail(int code, const std::string& msg);
 int cuda_fail(cudaError_t e, const char* what);
+
+// The graph structure as the step kernels of run r see it: every node of the problem,
+// or in a mixed run only the slots of its CSR members.
+inline CSRDev step_csr(const oim_run_s& r) {
+    CSRDev c = r.p->csr();
+    if (r.sub_slots >= 0) {
+        c.srow = r.d_srow_sub;
+        c.shead = r.d_shead_sub;
+        c.sdesc = r.d_sdesc_sub;
+        c.nodes = r.sub_slots;
+    }
+    return c;
+}
 
 // launchers (return cudaError_t of the launch)
 cudaError_t launch_init_stream(const oim_run_s& r, cudaStream_t s);

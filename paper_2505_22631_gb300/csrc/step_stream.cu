@@ -512,7 +512,8 @@ cudaError_t launch_step_stream_buffers(const oim_run_s& r, int64_t t, const floa
 static cudaError_t step_plain(const oim_run_s& r, int64_t t, const int32_t* d_t0, cudaStream_t s) {
     // with d_t0 the step is *d_t0 + t (graph replay); otherwise t itself.
     const StepParams P = params_of(r);
-    const StepGrid q = step_grid(r.p->nodes, r.R_pad / 4);
+    const CSRDev csr = step_csr(r);
+    const StepGrid q = step_grid(csr.nodes, r.R_pad / 4);
     const int in = (int)(t & 1);   // buffer parity follows the step index
     const int out = in ^ 1;
     const float* th_in = r.d_theta[in];
@@ -521,40 +522,42 @@ static cudaError_t step_plain(const oim_run_s& r, int64_t t, const int32_t* d_t0
     float2* cs_out = reinterpret_cast<float2*>(r.d_cs[out]);
     if (r.p->unit_weights)
         step_stream_kernel<true, CacheF32><<<q.grid, q.block, 0, s>>>(
-            r.p->csr(), P, th_in, cs_in, th_out, cs_out, t, d_t0, (int32_t)t, q.quads_fast);
+            csr, P, th_in, cs_in, th_out, cs_out, t, d_t0, (int32_t)t, q.quads_fast);
     else
         step_stream_kernel<false, CacheF32><<<q.grid, q.block, 0, s>>>(
-            r.p->csr(), P, th_in, cs_in, th_out, cs_out, t, d_t0, (int32_t)t, q.quads_fast);
+            csr, P, th_in, cs_in, th_out, cs_out, t, d_t0, (int32_t)t, q.quads_fast);
     return cudaGetLastError();
 }
 
 // The 16-bit form's step t: thread = node x octet of replicas (R_pad a multiple of 8).
 template <typename H2, int kQ>
-static void step_octet_q(const oim_run_s& r, const StepParams& P, const StepGrid& q, float* theta,
-                         const H2* cs_in, H2* cs_out, int64_t t, const int32_t* d_t0, cudaStream_t s) {
+static void step_octet_q(const oim_run_s& r, const CSRDev& csr, const StepParams& P, const StepGrid& q,
+                         float* theta, const H2* cs_in, H2* cs_out, int64_t t, const int32_t* d_t0,
+                         cudaStream_t s) {
     if (r.p->unit_weights)
-        step_octet_kernel<H2, true, kQ><<<q.grid, q.block, 0, s>>>(r.p->csr(), P, theta, cs_in, cs_out, t,
-                                                                  d_t0, (int32_t)t, q.quads_fast);
+        step_octet_kernel<H2, true, kQ><<<q.grid, q.block, 0, s>>>(csr, P, theta, cs_in, cs_out, t, d_t0,
+                                                                  (int32_t)t, q.quads_fast);
     else
-        step_octet_kernel<H2, false, kQ><<<q.grid, q.block, 0, s>>>(r.p->csr(), P, theta, cs_in, cs_out, t,
-                                                                   d_t0, (int32_t)t, q.quads_fast);
+        step_octet_kernel<H2, false, kQ><<<q.grid, q.block, 0, s>>>(csr, P, theta, cs_in, cs_out, t, d_t0,
+                                                                   (int32_t)t, q.quads_fast);
 }
 
 template <typename H2>
 static cudaError_t step_octet(const oim_run_s& r, int64_t t, const int32_t* d_t0, cudaStream_t s) {
     const StepParams P = params_of(r);
-    const StepGrid q = step_grid(r.p->nodes, r.R_pad / 8);
+    const CSRDev csr = step_csr(r);
+    const StepGrid q = step_grid(csr.nodes, r.R_pad / 8);
     const int in = (int)(t & 1);
     // phases in place (one buffer), the (cos, sin) pairs double-buffered
     float* theta = r.d_theta[in];
     const H2* cs_in = reinterpret_cast<const H2*>(r.d_cs[in]);
     H2* cs_out = reinterpret_cast<H2*>(r.d_cs[in ^ 1]);
     if (P.q == 2)
-        step_octet_q<H2, 2>(r, P, q, theta, cs_in, cs_out, t, d_t0, s);
+        step_octet_q<H2, 2>(r, csr, P, q, theta, cs_in, cs_out, t, d_t0, s);
     else if (P.q == 3)
-        step_octet_q<H2, 3>(r, P, q, theta, cs_in, cs_out, t, d_t0, s);
+        step_octet_q<H2, 3>(r, csr, P, q, theta, cs_in, cs_out, t, d_t0, s);
     else
-        step_octet_q<H2, 0>(r, P, q, theta, cs_in, cs_out, t, d_t0, s);
+        step_octet_q<H2, 0>(r, csr, P, q, theta, cs_in, cs_out, t, d_t0, s);
     return cudaGetLastError();
 }
 

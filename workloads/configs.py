@@ -117,6 +117,16 @@ def _c4(steps=None, replicas=None):
                     BASE_SEED, "16 uneven graphs, 800-20000 nodes")
 
 
+def _c4_dense(steps=None, replicas=None):
+    """The 16-graph uneven batch plus one dense member, G(2000, 0.05) (mean degree 100):
+    the case for choosing the form per graph (the dense member on the tensor cores)."""
+    graphs = _c4(steps=1).graphs + [erdos_renyi(2000, 0.05, BASE_SEED + 4, "+1")]
+    T = steps or 5000
+    K, Ks, Kn = _schedules(graphs, T)
+    return Workload("maxcut_uneven16_dense2000_R256", graphs, 2, replicas or 256, T, 0.01, K, Ks, Kn,
+                    BASE_SEED, "16 uneven graphs and one dense graph (mean degree 100)")
+
+
 def _c5(steps=None, replicas=None, count=64):
     graphs = []
     for g in range(count):
@@ -142,6 +152,7 @@ WORKLOADS = {
     "torus_er2000": _c2,
     "planted600": _c3,
     "uneven16": _c4,
+    "uneven16_dense": _c4_dense,
     "er64": _c5,
     "dense2000": _dense,
 }
