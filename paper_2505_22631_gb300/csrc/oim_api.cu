@@ -307,6 +307,11 @@ void free_run_buffers(oim_run_s* r) {
     dev_free(r->d_shead_sub);
     dev_free(r->d_sdesc_sub);
     r->sub_slots = -1;
+    if (r->aux) cudaStreamDestroy(r->aux);
+    if (r->ev_fork) cudaEventDestroy(r->ev_fork);
+    if (r->ev_join) cudaEventDestroy(r->ev_join);
+    r->aux = nullptr;
+    r->ev_fork = r->ev_join = nullptr;
     gemm_free(*r);
     if (r->chunk_exec) cudaGraphExecDestroy(r->chunk_exec);
     r->chunk_exec = nullptr;
@@ -479,6 +484,11 @@ int allocate_run(oim_run_s* r) {
         OIM_CUDA(dev_alloc(&r->d_sdesc_sub, sl.sdesc.size()), "cudaMalloc(member slot descriptors)");
         OIM_CUDA(upload_stream_slots(sl, r->d_srow_sub, r->d_shead_sub, r->d_sdesc_sub), "upload member slots");
         r->sub_slots = (int32_t)sl.srow.size();
+        if (r->sub_slots > 0 && !r->gemms.empty()) {
+            OIM_CUDA(cudaStreamCreateWithFlags(&r->aux, cudaStreamNonBlocking), "create dense-member stream");
+            OIM_CUDA(cudaEventCreateWithFlags(&r->ev_fork, cudaEventDisableTiming), "create fork event");
+            OIM_CUDA(cudaEventCreateWithFlags(&r->ev_join, cudaEventDisableTiming), "create join event");
+        }
     }
     if (r->form == OIM_FORM_RESIDENT) {
         const auto& items = r->plan.items;
@@ -545,23 +555,47 @@ float* readout_theta(const oim_run_s& r, int64_t t) {
     return r.form == OIM_FORM_STREAM ? r.d_theta[(t + 1) & 1] : r.d_theta[0];
 }
 
+// Steps [t0, t1) (offsets from *d_t0 in a replayed chunk, which starts on a readout
+// boundary; the steps themselves otherwise) with a score pass after every readout step
+// (dense graphs first copy their phases to the common layout).  The graphs of a batch
+// never read one another's state, so a mixed run's two parts need to meet only at the
+// readouts: between them the dense members step on the run's second stream, forked
+// from q and joined back before the readout.
+cudaError_t enqueue_steps(const oim_run_s& r, int64_t t0, int64_t t1, const int32_t* d_t0, cudaStream_t q) {
+    cudaError_t e = cudaSuccess;
+    const bool fork = r.aux != nullptr;
+    for (int64_t a = t0; a < t1 && e == cudaSuccess;) {
+        const int64_t re = r.readout_every;
+        const int64_t b = re > 0 ? std::min<int64_t>(t1, (a / re + 1) * re) : t1;
+        if (fork) {
+            e = cudaEventRecord(r.ev_fork, q);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(r.aux, r.ev_fork, 0);
+            for (int64_t t = a; t < b && e == cudaSuccess; ++t) e = launch_step_stream(r, t, d_t0, q);
+            for (int64_t t = a; t < b && e == cudaSuccess; ++t)
+                for (size_t k = 0; k < r.gemms.size() && e == cudaSuccess; ++k)
+                    e = launch_gemm_step_at(r, (int)k, t, d_t0, r.aux);
+            if (e == cudaSuccess) e = cudaEventRecord(r.ev_join, r.aux);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(q, r.ev_join, 0);
+        } else {
+            for (int64_t t = a; t < b && e == cudaSuccess; ++t) e = step_parts(r, t, d_t0, q);
+        }
+        if (e == cudaSuccess && re > 0 && b % re == 0) {
+            float* th = readout_theta(r, b - 1);
+            e = common_parts(r, q);
+            if (e == cudaSuccess)
+                e = d_t0 ? launch_score_at(r, th, 0, d_t0, (int32_t)b, q) : launch_score(r, th, b / re - 1, q);
+        }
+        a = b;
+    }
+    return e;
+}
+
 // A per-step form as init, steps / L replays of one captured chunk of L steps and its
 // score passes (steps and readout slots read from the device step base, which the
 // chunk's last node moves on by L), and the remaining steps launched directly.  The
 // chunk is captured once per (L, dt, readout period) and kept with the run.
 int enqueue_stream_chunks(oim_run_s* r, int64_t L) {
     cudaStream_t s = r->stream;
-    // one step (offset t from *d_t0, or the step t itself) and, where a readout falls,
-    // its score pass (dense graphs first copy their phases to the common layout)
-    auto step = [&](int64_t t, const int32_t* d_t0, cudaStream_t q) -> cudaError_t {
-        cudaError_t x = step_parts(*r, t, d_t0, q);
-        if (x != cudaSuccess || r->readout_every <= 0 || (t + 1) % r->readout_every != 0) return x;
-        float* th = readout_theta(*r, t);
-        x = common_parts(*r, q);
-        if (x != cudaSuccess) return x;
-        return d_t0 ? launch_score_at(*r, th, 0, d_t0, (int32_t)(t + 1), q)
-                    : launch_score(*r, th, (t + 1) / r->readout_every - 1, q);
-    };
     cudaError_t e = init_parts(*r, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(r->d_t0, 0, sizeof(int32_t), s);
     if (e != cudaSuccess) return cuda_fail(e, "stream-form launch");
@@ -574,7 +608,7 @@ int enqueue_stream_chunks(oim_run_s* r, int64_t L) {
         cudaGraph_t graph = nullptr;
         e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            for (int64_t m = 0; m < L && e == cudaSuccess; ++m) e = step(m, r->d_t0, cap);
+            e = enqueue_steps(*r, 0, L, r->d_t0, cap);
             if (e == cudaSuccess) e = launch_advance_t0(r->d_t0, (int32_t)L, cap);
             cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
             if (e == cudaSuccess) e = e2;
@@ -593,7 +627,7 @@ int enqueue_stream_chunks(oim_run_s* r, int64_t L) {
     }
     const int64_t chunks = r->steps / L;
     for (int64_t c = 0; c < chunks; ++c) OIM_CUDA(cudaGraphLaunch(r->step_chunk_exec, s), "chunk launch");
-    for (int64_t t = chunks * L; t < r->steps && e == cudaSuccess; ++t) e = step(t, nullptr, s);
+    if (e == cudaSuccess) e = enqueue_steps(*r, chunks * L, r->steps, nullptr, s);
     if (e == cudaSuccess) e = common_parts(*r, s);
     if (e != cudaSuccess) return cuda_fail(e, "stream-form launch");
     return OIM_OK;
@@ -606,18 +640,18 @@ int enqueue_stream_form(oim_run_s* r) {
     const size_t state_bytes = (size_t)r->p->nodes * r->R_pad * sizeof(float);
     auto body = [&](cudaStream_t s) -> cudaError_t {
         cudaError_t e = init_parts(*r, s);
-        if (e == cudaSuccess && r->ckpt_every > 0)
-            e = cudaMemcpyAsync(r->d_ckpt, r->d_theta[0], state_bytes, cudaMemcpyDeviceToDevice, s);
-        for (int64_t t = 0; t < r->steps && e == cudaSuccess; ++t) {
-            e = step_parts(*r, t, nullptr, s);
-            if (e == cudaSuccess && r->readout_every > 0 && (t + 1) % r->readout_every == 0) {
-                e = common_parts(*r, s);
-                if (e == cudaSuccess)
-                    e = launch_score(*r, readout_theta(*r, t), (t + 1) / r->readout_every - 1, s);
+        if (r->ckpt_every <= 0) {
+            if (e == cudaSuccess) e = enqueue_steps(*r, 0, r->steps, nullptr, s);
+        } else {
+            // checkpoints (the FP32 stream form): the phases after every ckpt_every steps
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(r->d_ckpt, r->d_theta[0], state_bytes, cudaMemcpyDeviceToDevice, s);
+            for (int64_t t = 0; t < r->steps && e == cudaSuccess; ++t) {
+                e = enqueue_steps(*r, t, t + 1, nullptr, s);
+                if (e == cudaSuccess && (t + 1) % r->ckpt_every == 0)
+                    e = cudaMemcpyAsync(r->d_ckpt + (size_t)((t + 1) / r->ckpt_every) * r->p->nodes * r->R_pad,
+                                        readout_theta(*r, t), state_bytes, cudaMemcpyDeviceToDevice, s);
             }
-            if (e == cudaSuccess && r->ckpt_every > 0 && (t + 1) % r->ckpt_every == 0)
-                e = cudaMemcpyAsync(r->d_ckpt + (size_t)((t + 1) / r->ckpt_every) * r->p->nodes * r->R_pad,
-                                    readout_theta(*r, t), state_bytes, cudaMemcpyDeviceToDevice, s);
         }
         if (e == cudaSuccess) e = common_parts(*r, s);
         return e;

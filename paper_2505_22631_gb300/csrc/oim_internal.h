@@ -170,6 +170,10 @@ struct oim_run_s {
     uint4* d_shead_sub = nullptr;
     uint32_t* d_sdesc_sub = nullptr;
     int32_t sub_slots = -1;
+    // mixed runs with both parts: the dense members step on a second stream, forked
+    // from the run's stream after each readout and joined before the next one
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int4* d_items = nullptr;                  // plan.items on the device
     // stream-form CUDA graph of a whole run, reused while its shape is unchanged
     cudaGraphExec_t chunk_exec = nullptr;

@@ -88,7 +88,8 @@ def test_mixed_batch_all_dense_and_all_csr(orc):
     graphs = _batch()[:3]
     T, R = 30, 64
     K, Ks, Kn = _sched(graphs, T)
-    allcsr = gpu_run(graphs, 2, K, Ks, Kn, 0.01, T, R, 9, form="mixed", graph_forms=["stream"] * 3)
+    allcsr = gpu_run(graphs, 2, K, Ks, Kn, 0.01, T, R, 9, form="mixed", precision="fp16",
+                     graph_forms=["stream"] * 3)
     stream = gpu_run(graphs, 2, K, Ks, Kn, 0.01, T, R, 9, form="stream", precision="fp16")
     for x, y in zip(allcsr.phases(), stream.phases()):
         assert np.array_equal(x, y)

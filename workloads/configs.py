@@ -118,13 +118,15 @@ def _c4(steps=None, replicas=None):
 
 
 def _c4_dense(steps=None, replicas=None):
-    """The 16-graph uneven batch plus one dense member, G(2000, 0.05) (mean degree 100):
-    the case for choosing the form per graph (the dense member on the tensor cores)."""
-    graphs = _c4(steps=1).graphs + [erdos_renyi(2000, 0.05, BASE_SEED + 4, "+1")]
+    """The 16-graph uneven batch plus one all-to-all member, the complete graph on 2000
+    nodes with +-1 weights (the shape of the fully connected max-cut instances the
+    paper's all-to-all couplings address): the case for choosing the form per graph,
+    the dense member on the tensor cores and the rest on the CSR form."""
+    graphs = _c4(steps=1).graphs + [erdos_renyi(2000, 1.0, BASE_SEED + 5, "pm1")]
     T = steps or 5000
     K, Ks, Kn = _schedules(graphs, T)
-    return Workload("maxcut_uneven16_dense2000_R256", graphs, 2, replicas or 256, T, 0.01, K, Ks, Kn,
-                    BASE_SEED, "16 uneven graphs and one dense graph (mean degree 100)")
+    return Workload("maxcut_uneven16_k2000_R256", graphs, 2, replicas or 256, T, 0.01, K, Ks, Kn,
+                    BASE_SEED, "16 uneven graphs and a complete +-1 graph on 2000 nodes")
 
 
 def _c5(steps=None, replicas=None, count=64):
@@ -152,7 +154,7 @@ WORKLOADS = {
     "torus_er2000": _c2,
     "planted600": _c3,
     "uneven16": _c4,
-    "uneven16_dense": _c4_dense,
+    "uneven16_k2000": _c4_dense,
     "er64": _c5,
     "dense2000": _dense,
 }
