@@ -63,6 +63,9 @@ extern "C" {
                               /* graph in oim_run_opts.graph_forms: the CSR       */
                               /* members step together in the stream form, each   */
                               /* dense member on the tensor cores, every step     */
+#define OIM_FORM_PERSISTENT 5 /* the 16-bit stream form with the steps between    */
+                              /* two readouts in one cooperative launch (a grid    */
+                              /* barrier per step, bounded: OIM_ETIMEOUT)          */
 
 /* ---- storage precision of the (cos, sin) cache the coupling reads --------- */
 #define OIM_PREC_AUTO 0

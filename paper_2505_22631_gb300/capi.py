@@ -29,6 +29,7 @@ OIM_FORM_STREAM = 1
 OIM_FORM_RESIDENT = 2
 OIM_FORM_GEMM = 3
 OIM_FORM_MIXED = 4
+OIM_FORM_PERSISTENT = 5
 
 OIM_PREC_AUTO = 0
 OIM_PREC_FP32 = 1
@@ -40,7 +41,7 @@ OIM_FLAG_DEFER_UPLOAD = 2
 OIM_NOALLOC_MAX_ACCUM = 131072
 
 FORMS = {"auto": OIM_FORM_AUTO, "stream": OIM_FORM_STREAM, "resident": OIM_FORM_RESIDENT,
-         "gemm": OIM_FORM_GEMM, "mixed": OIM_FORM_MIXED}
+         "gemm": OIM_FORM_GEMM, "mixed": OIM_FORM_MIXED, "persistent": OIM_FORM_PERSISTENT}
 PRECISIONS = {"auto": OIM_PREC_AUTO, "fp32": OIM_PREC_FP32, "bf16": OIM_PREC_BF16,
               "fp16": OIM_PREC_FP16}
 

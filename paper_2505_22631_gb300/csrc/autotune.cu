@@ -111,7 +111,10 @@ extern "C" int oim_autotune(oim_problem_t p, int32_t replicas, int32_t precision
         }
     }
     add(OIM_FORM_STREAM, OIM_PREC_FP32, 0, 0);
-    if (precision_policy == OIM_PREC_AUTO) add(OIM_FORM_STREAM, OIM_PREC_FP16, 0, 0);
+    if (precision_policy == OIM_PREC_AUTO) {
+        add(OIM_FORM_STREAM, OIM_PREC_FP16, 0, 0);
+        add(OIM_FORM_PERSISTENT, OIM_PREC_FP16, 0, 0);
+    }
     if (precision_policy == OIM_PREC_AUTO && G == 1) {
         add(OIM_FORM_GEMM, OIM_PREC_BF16, 0, 320);   // 128-wide tiles
         add(OIM_FORM_GEMM, OIM_PREC_BF16, 0, 576);   // 256-wide tiles

@@ -301,6 +301,7 @@ void free_run_buffers(oim_run_s* r) {
     dev_free(r->d_err);
     dev_free(r->d_seed);
     dev_free(r->d_t0);
+    dev_free(r->d_bar);
     dev_free(r->d_items);
     dev_free(r->d_ckpt);
     dev_free(r->d_srow_sub);
@@ -368,7 +369,23 @@ int ensure_step_buffers(oim_run_s* r, int64_t steps) {
 int choose_form(oim_run_s* r) {
     int form = r->opts.form;
     int prec = r->opts.precision;
-    if (form < OIM_FORM_AUTO || form > OIM_FORM_MIXED) return fail(OIM_EINVAL, "unknown form");
+    if (form < OIM_FORM_AUTO || form > OIM_FORM_PERSISTENT) return fail(OIM_EINVAL, "unknown form");
+    if (form == OIM_FORM_PERSISTENT) {
+        if (r->opts.checkpoint_every > 0)
+            return fail(OIM_EUNSUPPORTED, "checkpoints (for oim_backward) need the FP32 stream form");
+        if (prec == OIM_PREC_FP32)
+            return fail(OIM_EUNSUPPORTED, "the persistent form keeps a 16-bit (cos, sin) cache");
+        int dev = 0, coop = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) {
+            cudaGetLastError();
+            return fail(OIM_EUNSUPPORTED, "the device does not support cooperative launches");
+        }
+        r->form = OIM_FORM_PERSISTENT;
+        r->prec = prec == OIM_PREC_AUTO ? OIM_PREC_FP16 : prec;
+        r->R_pad = (r->R + 7) & ~7;   // octets of replicas
+        return OIM_OK;
+    }
     if (prec < OIM_PREC_AUTO || prec > OIM_PREC_FP16) return fail(OIM_EINVAL, "unknown precision");
     if (form == OIM_FORM_MIXED) {
         // graph_forms names each graph's form: the CSR members step together in the
@@ -453,7 +470,8 @@ int allocate_run(oim_run_s* r) {
     OIM_CUDA(dev_alloc(&r->d_err, 1), "cudaMalloc(err)");
     OIM_CUDA(dev_alloc(&r->d_seed, 1), "cudaMalloc(seed)");
     OIM_CUDA(dev_alloc(&r->d_t0, 1), "cudaMalloc(t0)");
-    if (r->form == OIM_FORM_STREAM || r->form == OIM_FORM_MIXED) {
+    if (r->form == OIM_FORM_PERSISTENT) OIM_CUDA(dev_alloc(&r->d_bar, 2), "cudaMalloc(grid barrier)");
+    if (r->form == OIM_FORM_STREAM || r->form == OIM_FORM_MIXED || r->form == OIM_FORM_PERSISTENT) {
         // a step reads and writes only its own node's phases, so they are updated in
         // place (one buffer under both parities); only the (cos, sin) cache, which the
         // neighbours read, needs the second buffer
@@ -553,6 +571,24 @@ cudaError_t common_parts(const oim_run_s& r, cudaStream_t s) {
 // parity with the step; its two buffers alias, and the other forms keep one).
 float* readout_theta(const oim_run_s& r, int64_t t) {
     return r.form == OIM_FORM_STREAM ? r.d_theta[(t + 1) & 1] : r.d_theta[0];
+}
+
+// The persistent form: init, then the steps between two readouts in one cooperative
+// launch each, a score pass after each readout step (launched directly: a run is a few
+// launches per readout period).
+int enqueue_persistent(oim_run_s* r) {
+    cudaStream_t s = r->stream;
+    cudaError_t e = cudaMemsetAsync(r->d_bar, 0, 2 * sizeof(unsigned), s);
+    if (e == cudaSuccess) e = launch_init_stream(*r, s);
+    const int64_t re = r->readout_every;
+    for (int64_t a = 0; a < r->steps && e == cudaSuccess;) {
+        const int64_t b = re > 0 ? std::min<int64_t>(r->steps, (a / re + 1) * re) : r->steps;
+        e = launch_persistent_steps(*r, a, b, s);
+        if (e == cudaSuccess && re > 0 && b % re == 0) e = launch_score(*r, r->d_theta[0], b / re - 1, s);
+        a = b;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "persistent-form launch");
+    return OIM_OK;
 }
 
 // Steps [t0, t1) (offsets from *d_t0 in a replayed chunk, which starts on a readout
@@ -732,6 +768,10 @@ int execute(oim_run_s* r, const float* K, const float* Ks, const float* Kn) {
     if (r->form == OIM_FORM_RESIDENT) {
         cudaError_t e = launch_resident_impl(*r, r->d_items, s);
         if (e != cudaSuccess) return cuda_fail(e, "resident launch");
+        r->final_buf = 0;
+    } else if (r->form == OIM_FORM_PERSISTENT) {
+        int rc = enqueue_persistent(r);
+        if (rc != OIM_OK) return rc;
         r->final_buf = 0;
     } else {
         int rc = enqueue_stream_form(r);

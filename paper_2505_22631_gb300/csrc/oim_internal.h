@@ -159,6 +159,7 @@ struct oim_run_s {
     double* d_energy = nullptr;               // [G][R_pad]
     int32_t* d_err = nullptr;                 // device error word
     uint64_t* d_seed = nullptr;               // the run's seed, read by the per-step forms
+    unsigned* d_bar = nullptr;                // persistent form: grid barrier {count, generation}
     // resident-form launch plan
     oim::ResidentPlan plan;
     // dense-form state: the graph of the dense form, or the dense members of a mixed run
@@ -245,6 +246,7 @@ inline CSRDev step_csr(const oim_run_s& r) {
 // launchers (return cudaError_t of the launch)
 cudaError_t launch_init_stream(const oim_run_s& r, cudaStream_t s);
 cudaError_t launch_step_stream(const oim_run_s& r, int64_t t, const int32_t* d_t0, cudaStream_t s);
+cudaError_t launch_persistent_steps(const oim_run_s& r, int64_t t0, int64_t t1, cudaStream_t s);
 cudaError_t plan_resident(const oim_problem_s& p, int32_t R_pad, int32_t prec, int32_t want_k,
                           int32_t want_threads, ResidentPlan* plan);
 

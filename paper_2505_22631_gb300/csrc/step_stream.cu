@@ -23,6 +23,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <algorithm>
 #include <type_traits>
 
 #include "oim_device.cuh"
@@ -258,18 +259,19 @@ __device__ __forceinline__ uint32_t f2_to_h2(float2 f) {
 // 48 registers (five blocks of 256 per SM): 40 warps to cover the gather's latency
 // (measured on the two-graph benchmark batch: 64 registers 19.9 us, 48 registers
 // 18.6 us per step; 40 registers spill)
-template <typename H2, bool kUnit, int kQ>
-__global__ void __launch_bounds__(256, 5) step_octet_kernel(CSRDev csr, StepParams P, float* theta,
-                                                            const H2* __restrict__ cs_in,
-                                                            H2* __restrict__ cs_out, int64_t t_fixed,
-                                                            const int32_t* __restrict__ d_t0,
-                                                            int32_t t_add, int octs_fast) {
-    const int octs = P.R_pad >> 3;
-    const int nblk = octs_fast ? blockIdx.y : blockIdx.x;
-    const int oblk = octs_fast ? blockIdx.x : blockIdx.y;
-    const int slot = nblk * blockDim.y + threadIdx.y;
-    const int oct = oblk * blockDim.x + threadIdx.x;
-    if (slot >= csr.nodes || oct >= octs) return;
+// One step of one (slot, octet) work item.  kCoherent: the neighbours' pairs are read
+// through L2 only (ld.global.cg), for the persistent kernel, whose pairs were written
+// by other blocks during the same launch; the per-step kernel reads them through the
+// read-only path.
+template <typename H2, bool kUnit, int kQ, bool kCoherent>
+__device__ __forceinline__ void octet_step(const CSRDev& csr, const StepParams& P, float* theta,
+                                           const H2* __restrict__ cs_in, H2* __restrict__ cs_out,
+                                           int slot, int oct, int64_t t_fixed,
+                                           const int32_t* __restrict__ d_t0, int32_t t_add) {
+    auto ld_pairs = [](const char* p, uint32_t (&r)[8]) {
+        if constexpr (kCoherent) ld256_cg(p, r);
+        else ld256_nc(p, r);
+    };
     uint32_t d[8];
     ld256_nc(csr.sdesc + (size_t)slot * 8, d);
     const int node = (int)d[0], e_beg = (int)d[1], e_split = (int)d[2], e_end = (int)d[3];
@@ -283,8 +285,8 @@ __global__ void __launch_bounds__(256, 5) step_octet_kernel(CSRDev csr, StepPara
     float sgn = 1.0f;
     if constexpr (kUnit) {
         uint32_t h0[8], h1[8];
-        ld256_nc(cs_base + (size_t)d[6] * stride, h0);
-        ld256_nc(cs_base + (size_t)d[7] * stride, h1);
+        ld_pairs(cs_base + (size_t)d[6] * stride, h0);
+        ld_pairs(cs_base + (size_t)d[7] * stride, h1);
         if (e_beg < e_end) {
             if (e_beg == e_split) rsub8<H2>(acc, h0);
             else add8<H2>(acc, h0);
@@ -297,26 +299,26 @@ __global__ void __launch_bounds__(256, 5) step_octet_kernel(CSRDev csr, StepPara
         const uint32_t* cp = reinterpret_cast<const uint32_t*>(csr.pcol) + e;
         for (; e < e_split; ++e, ++cp) {
             uint32_t v[8];
-            ld256_nc(cs_base + (size_t)__ldg(cp) * stride, v);
+            ld_pairs(cs_base + (size_t)__ldg(cp) * stride, v);
             add8<H2>(acc, v);
         }
         if (e == e_split && e < e_end) {
             uint32_t v[8];
-            ld256_nc(cs_base + (size_t)__ldg(cp) * stride, v);
+            ld_pairs(cs_base + (size_t)__ldg(cp) * stride, v);
             rsub8<H2>(acc, v);
             ++e;
             ++cp;
         }
         for (; e < e_end; ++e, ++cp) {
             uint32_t v[8];
-            ld256_nc(cs_base + (size_t)__ldg(cp) * stride, v);
+            ld_pairs(cs_base + (size_t)__ldg(cp) * stride, v);
             add8<H2>(acc, v);
         }
         if (e_split < e_end) sgn = -1.0f;   // the accumulators hold -(A, B)
     } else {
         for (int e = e_beg; e < e_end; ++e) {
             uint32_t v[8];
-            ld256_nc(cs_base + (size_t)(uint32_t)__ldg(csr.pcol + e) * stride, v);
+            ld_pairs(cs_base + (size_t)(uint32_t)__ldg(csr.pcol + e) * stride, v);
             const float w = __ldg(csr.w + e);
             const float2 ww = make_float2(w, w);
 #pragma unroll
@@ -330,7 +332,8 @@ __global__ void __launch_bounds__(256, 5) step_octet_kernel(CSRDev csr, StepPara
     const float K = __ldg(P.K + sidx), Ks = __ldg(P.Ks + sidx), Kn = __ldg(P.Kn + sidx);
     const size_t at = (size_t)node * P.R_pad + 8 * oct;
     uint32_t thw[8];
-    ld256(theta + at, thw);
+    if constexpr (kCoherent) ld256_cg(theta + at, thw);   // ordered against the previous step's store
+    else ld256(theta + at, thw);
     const uint64_t seed = P.seed_dev ? *P.seed_dev : P.seed;
     uint4 xa, xb;
     draw_block_pair(seed, (uint32_t)g, kStreamNoise, (uint32_t)i, (uint32_t)t, (uint32_t)(2 * oct), xa, xb);
@@ -368,6 +371,89 @@ __global__ void __launch_bounds__(256, 5) step_octet_kernel(CSRDev csr, StepPara
     }
     st256(theta + at, tno);
     st256(cs_out + at, cso);
+}
+
+template <typename H2, bool kUnit, int kQ>
+__global__ void __launch_bounds__(256, 5) step_octet_kernel(CSRDev csr, StepParams P, float* theta,
+                                                            const H2* __restrict__ cs_in,
+                                                            H2* __restrict__ cs_out, int64_t t_fixed,
+                                                            const int32_t* __restrict__ d_t0,
+                                                            int32_t t_add, int octs_fast) {
+    const int octs = P.R_pad >> 3;
+    const int nblk = octs_fast ? blockIdx.y : blockIdx.x;
+    const int oblk = octs_fast ? blockIdx.x : blockIdx.y;
+    const int slot = nblk * blockDim.y + threadIdx.y;
+    const int oct = oblk * blockDim.x + threadIdx.x;
+    if (slot >= csr.nodes || oct >= octs) return;
+    octet_step<H2, kUnit, kQ, false>(csr, P, theta, cs_in, cs_out, slot, oct, t_fixed, d_t0, t_add);
+}
+
+// Nanoseconds of the GPU's global timer.
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+constexpr int32_t kErrGridBarrier = 16;           // error word: a grid barrier gave up
+constexpr uint64_t kGridBarrierNs = 2000000000ull;  // two seconds
+
+// Barrier of all blocks of a cooperative launch (co-resident by construction).  The last
+// block to arrive resets the count and moves the generation on; the others wait for the
+// generation to change for at most kGridBarrierNs, after which they record the error and
+// the kernel returns.  The fences order every write of the block before its arrival and
+// every later read after the wait (the bar.sync around them carries the block's threads).
+__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, unsigned nblocks, int32_t* err) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        volatile unsigned* vgen = gen;
+        const unsigned g0 = *vgen;
+        __threadfence();
+        if (atomicAdd(count, 1u) == nblocks - 1) {
+            atomicExch(count, 0u);
+            __threadfence();
+            atomicAdd(gen, 1u);
+            ok = 1;
+        } else {
+            ok = 1;
+            const uint64_t start = global_ns();
+            while (*vgen == g0) {
+                if (global_ns() - start > kGridBarrierNs || *reinterpret_cast<volatile int32_t*>(err) != 0) {
+                    atomicCAS(err, 0, kErrGridBarrier);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// The persistent form: steps [t0, t1) of the 16-bit stream form in one cooperative
+// launch.  Each block walks the per-step kernel's blocks (same shape, same heaviest-first
+// order) with a stride of the grid, then all blocks meet at a grid barrier before the
+// next step reads the pairs this one wrote.
+template <typename H2, bool kUnit, int kQ>
+__global__ void __launch_bounds__(256, 5) step_octet_persistent_kernel(
+    CSRDev csr, StepParams P, float* theta, H2* cs0, H2* cs1, int64_t t0, int64_t t1, int gx, int gy,
+    unsigned* bar, int32_t* err) {
+    const int octs = P.R_pad >> 3;
+    const int vblocks = gx * gy;
+    for (int64_t t = t0; t < t1; ++t) {
+        const H2* cs_in = (t & 1) ? cs1 : cs0;
+        H2* cs_out = (t & 1) ? cs0 : cs1;
+        for (int vb = blockIdx.x; vb < vblocks; vb += gridDim.x) {
+            const int oblk = vb % gx, nblk = vb / gx;   // replica blocks fastest, as octs_fast
+            const int slot = nblk * blockDim.y + threadIdx.y;
+            const int oct = oblk * blockDim.x + threadIdx.x;
+            if (slot < csr.nodes && oct < octs)
+                octet_step<H2, kUnit, kQ, true>(csr, P, theta, cs_in, cs_out, slot, oct, t, nullptr, 0);
+        }
+        if (t + 1 < t1 && !grid_barrier(bar, bar + 1, gridDim.x, err)) return;
+    }
 }
 
 // f = K sum_j w_ij (s_i c_j - c_i s_j) - Ks sin(2 pi q theta_i) for theta[r][n] of
@@ -559,6 +645,52 @@ static cudaError_t step_octet(const oim_run_s& r, int64_t t, const int32_t* d_t0
     else
         step_octet_q<H2, 0>(r, csr, P, q, theta, cs_in, cs_out, t, d_t0, s);
     return cudaGetLastError();
+}
+
+// Steps [t0, t1) of the 16-bit stream form in one cooperative launch of as many blocks
+// as fit on the GPU at once (the per-step kernel's blocks are walked with their stride).
+template <typename H2, bool kUnit, int kQ>
+static cudaError_t persistent_as(const oim_run_s& r, int64_t t0, int64_t t1, cudaStream_t s) {
+    const StepParams P = params_of(r);
+    const CSRDev csr = step_csr(r);
+    const StepGrid q = step_grid(csr.nodes, r.R_pad / 8);
+    int gx = (int)q.grid.x, gy = (int)q.grid.y;   // octet blocks, node blocks
+    if (!q.quads_fast) std::swap(gx, gy);
+    auto fn = step_octet_persistent_kernel<H2, kUnit, kQ>;
+    int per_sm = 0, dev = 0, sms = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, (int)(q.block.x * q.block.y), 0);
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int blocks = std::max(1, std::min(per_sm * sms, gx * gy));
+    H2* cs0 = reinterpret_cast<H2*>(r.d_cs[0]);
+    H2* cs1 = reinterpret_cast<H2*>(r.d_cs[1]);
+    float* theta = r.d_theta[0];
+    unsigned* bar = r.d_bar;
+    int32_t* err = r.d_err;
+    void* args[] = {const_cast<CSRDev*>(&csr), const_cast<StepParams*>(&P), &theta, &cs0, &cs1, &t0, &t1,
+                    &gx, &gy, &bar, &err};
+    return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(fn), dim3((unsigned)blocks), q.block, args,
+                                       0, s);
+}
+
+template <typename H2>
+static cudaError_t persistent_h2(const oim_run_s& r, int64_t t0, int64_t t1, cudaStream_t s) {
+    const int q = r.p->q;
+    if (r.p->unit_weights) {
+        if (q == 2) return persistent_as<H2, true, 2>(r, t0, t1, s);
+        if (q == 3) return persistent_as<H2, true, 3>(r, t0, t1, s);
+        return persistent_as<H2, true, 0>(r, t0, t1, s);
+    }
+    if (q == 2) return persistent_as<H2, false, 2>(r, t0, t1, s);
+    if (q == 3) return persistent_as<H2, false, 3>(r, t0, t1, s);
+    return persistent_as<H2, false, 0>(r, t0, t1, s);
+}
+
+cudaError_t launch_persistent_steps(const oim_run_s& r, int64_t t0, int64_t t1, cudaStream_t s) {
+    if (t1 <= t0) return cudaSuccess;
+    if (r.prec == OIM_PREC_BF16) return persistent_h2<__nv_bfloat162>(r, t0, t1, s);
+    return persistent_h2<__half2>(r, t0, t1, s);
 }
 
 cudaError_t launch_step_stream(const oim_run_s& r, int64_t t, const int32_t* d_t0, cudaStream_t s) {
