@@ -284,6 +284,8 @@ def kernels_per_run(form, steps, readout_every, dense_members=0):
         return 1
     if form == 3:          # dense: init, a step kernel per step, relayout + spins + score per readout,
         return 1 + 1 + steps + 3 * readouts + 1   # final relayout
+    if form == 5:          # persistent: init, one launch per readout period, spins + score per readout
+        return 1 + 1 + max(readouts, 1) + 2 * readouts
     if form == 4:          # mixed: inits, the CSR step and one step per dense member each step,
         nd = dense_members  # the dense relayouts + spins + score per readout, final relayouts
         return 1 + (1 + nd) + (1 + nd) * steps + (2 + nd) * readouts + nd
@@ -400,7 +402,7 @@ def main():
     # own average launch duration comes from runs of the same steps without readouts
     # (CUDA events around each run, divided by its steps; L2 flushed between runs)
     ms_kernel_run = ms_step
-    if info["form"] in (1, 3, 4):
+    if info["form"] in (1, 3, 4, 5):
         bare = Run(prob, dK, dKs, dKn, w.dt, w.steps, w.replicas, seed_base + 50, form=form,
                    precision=precision, readout_every=0, stream=stream,
                    replicas_per_block=rpb, threads_per_block=threads, graph_forms=graph_forms)
@@ -419,7 +421,8 @@ def main():
     prec_name = {1: "fp32", 2: "bf16", 3: "fp16"}.get(info["precision"])
     kname = {2: f"resident_quad_kernel<{prec_name}>",
              1: "step_stream_kernel" if info["precision"] == 1 else "step_octet_kernel",
-             3: "gemm_step_kernel", 4: "step_octet_kernel + gemm_step_kernel"}.get(info["form"], "?")
+             3: "gemm_step_kernel", 4: "step_octet_kernel + gemm_step_kernel",
+             5: "step_octet_persistent_kernel"}.get(info["form"], "?")
     traffic = profiled_traffic(kname, w.name)
     if info["form"] == 3:
         n = w.graphs[0].n
@@ -519,7 +522,8 @@ def main():
                    "nodes": [g.n for g in w.graphs], "nnz": [g.nnz for g in w.graphs],
                    "replicas": w.replicas, "euler_steps": w.steps,
                    "readout_every": args.readout_every,
-                   "form": {0: "auto", 1: "stream", 2: "resident", 3: "gemm", 4: "mixed"}[info["form"]],
+                   "form": {0: "auto", 1: "stream", 2: "resident", 3: "gemm", 4: "mixed",
+                            5: "persistent"}[info["form"]],
                    "graph_forms": None if graph_forms is None else
                    [{1: "stream", 3: "gemm"}[f] for f in graph_forms],
                    "precision": {1: "fp32", 2: "bf16", 3: "fp16"}.get(info["precision"]),
