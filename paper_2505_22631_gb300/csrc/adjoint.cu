@@ -15,8 +15,12 @@
 //   dL/dK_t = dt sum lambda_{t+1} D(theta_t),  dL/dKs_t = -dt sum lambda_{t+1} sin 2 pi q theta_t,
 //   dL/dKn_t = sqrt(dt) sum lambda_{t+1} xi_t  (pathwise: the same Philox draws as the forward).
 // Layout as the stream form: [node][R_pad], replicas contiguous, a thread per (node, quad).
-// Y holds four planes c, s, lambda c, lambda s of [node][R_pad] floats each, so a
-// neighbour gather is four 16-byte loads that a warp turns into whole 512-byte rows.
+// The forward recomputation of a segment keeps the coupling sums (A, B) of each of its
+// steps (the forward step computes them anyway), so the reverse sweep gathers only the
+// two planes lambda_{t+1} c_t and lambda_{t+1} s_t of [node][R_pad] floats (two 16-byte
+// loads per neighbour that a warp turns into whole 512-byte rows).  Each adjoint step
+// also writes the planes the next one (step t - 1) gathers, lambda_t (c, s)_{t-1}, from
+// its own lambda_t and theta_{t-1}.
 #include "oim_device.cuh"
 #include "oim_internal.h"
 
@@ -26,22 +30,22 @@ namespace {
 
 constexpr float kTwoPi = 6.28318530717958647f;
 
-// (c, s, lambda c, lambda s) of every node-replica at theta_t, as four planes.
-__global__ void __launch_bounds__(256) adj_prep_kernel(int64_t state, const float* __restrict__ theta,
-                                                       const float* __restrict__ lam, float* __restrict__ Y) {
+// (c, s) of every node-replica at theta as two planes, or (lambda c, lambda s) when lam
+// is given.
+__global__ void __launch_bounds__(256) adj_planes_kernel(int64_t state, const float* __restrict__ theta,
+                                                         const float* __restrict__ lam, float* __restrict__ Y) {
     const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= state) return;
     float s, c;
     sincospif(2.0f * theta[gid], &s, &c);
-    const float l = lam[gid];
-    Y[gid] = c;
-    Y[state + gid] = s;
-    Y[2 * state + gid] = l * c;
-    Y[3 * state + gid] = l * s;
+    const float l = lam ? lam[gid] : 1.0f;
+    Y[gid] = lam ? l * c : c;
+    Y[state + gid] = lam ? l * s : s;
 }
 
 // D(theta) * scale into lam (the terminal adjoint, scale = -2 pi / R), and the
 // per-graph FP64 sum of E = 1/2 sum_i (c_i A_i + s_i B_i) over the real replicas.
+// Y: the (c, s) planes of theta.
 __global__ void __launch_bounds__(256) adj_terminal_kernel(CSRDev csr, int R, int R_pad, float scale,
                                                            const float* __restrict__ Y,
                                                            float* __restrict__ lam,
@@ -84,12 +88,18 @@ __global__ void __launch_bounds__(256) adj_terminal_kernel(CSRDev csr, int R, in
 }
 
 // One adjoint step: lambda_out = lambda_t from lambda_in = lambda_{t+1} at theta_t,
-// and the step's gradient terms added to dK[g][t], dKs[g][t], dKn[g][t].
+// the step's gradient terms added to dK[g][t], dKs[g][t], dKn[g][t], and, when
+// theta_prev (theta_{t-1}) is given, the planes lambda_t (c, s)_{t-1} for step t - 1.
+//   AB   the forward step's coupling sums at theta_t, float2 [node][R_pad]
+//   Ylam the planes lambda_{t+1} c_t, lambda_{t+1} s_t
 // 64 registers, four blocks per SM (measured: 726 -> 699 ms for the backward pass of the
 // schedule workload against the unbounded 70 registers)
 __global__ void __launch_bounds__(256, 4) adj_step_kernel(CSRDev csr, StepParams P, int64_t t,
                                                        const float* __restrict__ theta,
-                                                       const float* __restrict__ Y,
+                                                       const float* __restrict__ theta_prev,
+                                                       const float2* __restrict__ AB,
+                                                       const float* __restrict__ Ylam,
+                                                       float* __restrict__ Ylam_out,
                                                        const float* __restrict__ lam_in,
                                                        float* __restrict__ lam_out,
                                                        double* __restrict__ dK, double* __restrict__ dKs,
@@ -111,26 +121,19 @@ __global__ void __launch_bounds__(256, 4) adj_step_kernel(CSRDev csr, StepParams
         const int node = row.x;
         const size_t at = (size_t)node * P.R_pad + 4 * quad;
         const size_t state = (size_t)csr.nodes * P.R_pad;
-        const float* Yc = Y;
-        const float* Ys = Y + state;
-        const float* Ylc = Y + 2 * state;
-        const float* Yls = Y + 3 * state;
-        float A[4] = {0, 0, 0, 0}, B[4] = {0, 0, 0, 0}, Pp[4] = {0, 0, 0, 0}, Q[4] = {0, 0, 0, 0};
+        const float* Ylc = Ylam;
+        const float* Yls = Ylam + state;
+        float Pp[4] = {0, 0, 0, 0}, Q[4] = {0, 0, 0, 0};
         for (int ei = row.y; ei < row.w; ++ei) {
             const uint32_t cw = csr.col[ei];
             const uint32_t j = csr.w ? cw : (cw & ~kSignBit);
             const float w = csr.w ? csr.w[ei] : ((cw & kSignBit) ? -1.0f : 1.0f);
             const size_t jat = (size_t)j * P.R_pad + 4 * quad;
-            const float4 c4 = *reinterpret_cast<const float4*>(Yc + jat);
-            const float4 s4 = *reinterpret_cast<const float4*>(Ys + jat);
             const float4 lc4 = *reinterpret_cast<const float4*>(Ylc + jat);
             const float4 ls4 = *reinterpret_cast<const float4*>(Yls + jat);
-            const float cj[4] = {c4.x, c4.y, c4.z, c4.w}, sj[4] = {s4.x, s4.y, s4.z, s4.w};
             const float lcj[4] = {lc4.x, lc4.y, lc4.z, lc4.w}, lsj[4] = {ls4.x, ls4.y, ls4.z, ls4.w};
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
-                A[v] = fmaf(w, cj[v], A[v]);
-                B[v] = fmaf(w, sj[v], B[v]);
                 Pp[v] = fmaf(w, lcj[v], Pp[v]);
                 Q[v] = fmaf(w, lsj[v], Q[v]);
             }
@@ -145,22 +148,38 @@ __global__ void __launch_bounds__(256, 4) adj_step_kernel(CSRDev csr, StepParams
         const float2 z01 = box_muller(x.x, x.y);
         const float2 z23 = box_muller(x.z, x.w);
         const float z[4] = {z01.x, z01.y, z23.x, z23.y};
+        const float4 ab01 = *reinterpret_cast<const float4*>(AB + at);
+        const float4 ab23 = *reinterpret_cast<const float4*>(AB + at + 2);
+        const float A[4] = {ab01.x, ab01.z, ab23.x, ab23.z}, B[4] = {ab01.y, ab01.w, ab23.y, ab23.w};
+        float lt[4];
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-            const float c = Yc[at + v], s = Ys[at + v];
+            const float th = theta[at + v];
+            float s, c;
+            sincospif(2.0f * th, &s, &c);
             const float l = lam_in[at + v];
             const float S = c * A[v] + s * B[v];
             const float Cc = c * Pp[v] + s * Q[v];
-            const float th = theta[at + v];
             float sq, cq;
             sincospif(2.0f * (float)P.q * th, &sq, &cq);
             const float diag = kTwoPi * K * S - kTwoPi * (float)P.q * Ks * cq;
-            lam_out[at + v] = l + P.dt * (l * diag - kTwoPi * K * Cc);
+            lt[v] = l + P.dt * (l * diag - kTwoPi * K * Cc);
+            lam_out[at + v] = lt[v];
             if (4 * quad + v < P.R) {
                 const float D = s * A[v] - c * B[v];
                 gK += (double)(l * D);
                 gS += (double)(l * sq);
                 gN += (double)(l * z[v]);
+            }
+        }
+        if (theta_prev) {
+            // the planes step t - 1 gathers: lambda_t (c, s) of theta_{t-1}
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                float s, c;
+                sincospif(2.0f * theta_prev[at + v], &s, &c);
+                Ylam_out[at + v] = lt[v] * c;
+                Ylam_out[state + at + v] = lt[v] * s;
             }
         }
     }
@@ -202,29 +221,26 @@ static QuadGridA quad_grid_a(int64_t nodes, int quads) {
     return q;
 }
 
-// Y (four planes of [node][R_pad] floats, in a buffer of node-replica float4s) from
-// (theta, lambda).
-cudaError_t launch_adj_prep(const oim_run_s& r, const float* theta, const float* lam, float4* Y,
-                            cudaStream_t s) {
+// Two planes of [node][R_pad] floats from theta: (c, s), or (lambda c, lambda s).
+cudaError_t launch_adj_planes(const oim_run_s& r, const float* theta, const float* lam, float* Y,
+                              cudaStream_t s) {
     const int64_t total = r.p->nodes * r.R_pad;
-    adj_prep_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(total, theta, lam,
-                                                                   reinterpret_cast<float*>(Y));
+    adj_planes_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(total, theta, lam, Y);
     return cudaGetLastError();
 }
 
-// lambda_T and the loss sums from Y(theta_T) (its lambda columns are unused).
-cudaError_t launch_adj_terminal(const oim_run_s& r, const float4* Y, float* lam, double* loss,
+// lambda_T and the loss sums from the (c, s) planes of theta_T.
+cudaError_t launch_adj_terminal(const oim_run_s& r, const float* Y, float* lam, double* loss,
                                 cudaStream_t s) {
     const float scale = -6.28318530717958647f / (float)r.R;
     const QuadGridA q = quad_grid_a(r.p->nodes, r.R_pad / 4);
-    adj_terminal_kernel<<<q.grid, q.block, 0, s>>>(
-        r.p->csr(), r.R, r.R_pad, scale, reinterpret_cast<const float*>(Y), lam, loss);
+    adj_terminal_kernel<<<q.grid, q.block, 0, s>>>(r.p->csr(), r.R, r.R_pad, scale, Y, lam, loss);
     return cudaGetLastError();
 }
 
-cudaError_t launch_adj_step(const oim_run_s& r, int64_t t, const float* theta, const float4* Y,
-                            const float* lam_in, float* lam_out, double* dK, double* dKs, double* dKn,
-                            cudaStream_t s) {
+cudaError_t launch_adj_step(const oim_run_s& r, int64_t t, const float* theta, const float* theta_prev,
+                            const float2* AB, const float* Ylam, float* Ylam_out, const float* lam_in,
+                            float* lam_out, double* dK, double* dKs, double* dKn, cudaStream_t s) {
     const StepParams P = make_params(r);
     QuadGridA q = quad_grid_a(r.p->nodes, r.R_pad / 4);
     int quads_fast = 0;
@@ -232,9 +248,8 @@ cudaError_t launch_adj_step(const oim_run_s& r, int64_t t, const float* theta, c
         q.grid = dim3(q.grid.y, q.grid.x);
         quads_fast = 1;
     }
-    adj_step_kernel<<<q.grid, q.block, 0, s>>>(
-        r.p->csr(), P, t, theta, reinterpret_cast<const float*>(Y), lam_in, lam_out, dK, dKs, dKn, r.steps,
-        quads_fast);
+    adj_step_kernel<<<q.grid, q.block, 0, s>>>(r.p->csr(), P, t, theta, theta_prev, AB, Ylam, Ylam_out, lam_in,
+                                               lam_out, dK, dKs, dKn, r.steps, quads_fast);
     return cudaGetLastError();
 }
 

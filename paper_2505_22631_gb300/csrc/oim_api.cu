@@ -38,7 +38,7 @@ cudaError_t launch_derivative(const oim_problem_s& p, const float* theta, int32_
 size_t resident_cache_bytes(int32_t prec);
 cudaError_t launch_cs_from_theta(const oim_run_s& r, const float* theta, float2* cs, cudaStream_t s);
 cudaError_t launch_step_stream_buffers(const oim_run_s& r, int64_t t, const float* th_in,
-                                       const float2* cs_in, float* th_out, float2* cs_out,
+                                       const float2* cs_in, float* th_out, float2* cs_out, float2* ab,
                                        cudaStream_t s);
 int gemm_setup(oim_run_s& r, int graph);
 void gemm_free(oim_run_s& r);
@@ -46,13 +46,12 @@ cudaError_t launch_gemm_init(const oim_run_s& r, int k, cudaStream_t s);
 cudaError_t launch_set_seed(uint64_t* d_seed, uint64_t seed, cudaStream_t s);
 cudaError_t launch_gemm_step_at(const oim_run_s& r, int k, int64_t t, const int32_t* d_t0, cudaStream_t s);
 cudaError_t launch_gemm_to_common(const oim_run_s& r, int k, float* out, cudaStream_t s);
-cudaError_t launch_adj_prep(const oim_run_s& r, const float* theta, const float* lam, float4* Y,
-                            cudaStream_t s);
-cudaError_t launch_adj_terminal(const oim_run_s& r, const float4* Y, float* lam, double* loss,
-                                cudaStream_t s);
-cudaError_t launch_adj_step(const oim_run_s& r, int64_t t, const float* theta, const float4* Y,
-                            const float* lam_in, float* lam_out, double* dK, double* dKs, double* dKn,
-                            cudaStream_t s);
+cudaError_t launch_adj_planes(const oim_run_s& r, const float* theta, const float* lam, float* Y,
+                              cudaStream_t s);
+cudaError_t launch_adj_terminal(const oim_run_s& r, const float* Y, float* lam, double* loss, cudaStream_t s);
+cudaError_t launch_adj_step(const oim_run_s& r, int64_t t, const float* theta, const float* theta_prev,
+                            const float2* AB, const float* Ylam, float* Ylam_out, const float* lam_in,
+                            float* lam_out, double* dK, double* dKs, double* dKn, cudaStream_t s);
 
 }  // namespace oim
 
@@ -1213,14 +1212,16 @@ int oim_backward(oim_run_t r, double* dK, double* dKs, double* dKn, double* loss
     const int64_t T = r->steps, C = r->ckpt_every;
     const size_t state = (size_t)r->p->nodes * r->R_pad;
     const int64_t seg_len = std::min<int64_t>(C, std::max<int64_t>(T, 1));
-    float *seg = nullptr, *lam[2] = {nullptr, nullptr};
-    float2* cs[2] = {nullptr, nullptr};
-    float4* Y = nullptr;
+    // per segment: the phases theta_t0 .. theta_t1 and the coupling sums (A, B) of its
+    // steps, recomputed from the checkpoint; lambda ping-pong; two ping-pong pairs of
+    // planes lambda_{t+1} (c, s)_t
+    float *seg = nullptr, *lam[2] = {nullptr, nullptr}, *Y[2] = {nullptr, nullptr};
+    float2 *cs[2] = {nullptr, nullptr}, *ab = nullptr;
     double *gK = nullptr, *gS = nullptr, *gN = nullptr, *gL = nullptr;
     cudaError_t e = cudaSuccess;
     auto cleanup = [&]() {
         cudaFree(seg); cudaFree(lam[0]); cudaFree(lam[1]); cudaFree(cs[0]); cudaFree(cs[1]);
-        cudaFree(Y); cudaFree(gK); cudaFree(gS); cudaFree(gN); cudaFree(gL);
+        cudaFree(Y[0]); cudaFree(Y[1]); cudaFree(ab); cudaFree(gK); cudaFree(gS); cudaFree(gN); cudaFree(gL);
     };
 #define OIM_BW(call, what)                     \
     do {                                       \
@@ -1230,12 +1231,14 @@ int oim_backward(oim_run_t r, double* dK, double* dKs, double* dKn, double* loss
             return cuda_fail(e, what);         \
         }                                      \
     } while (0)
-    OIM_BW(cudaMalloc(&seg, (size_t)seg_len * state * sizeof(float)), "cudaMalloc(segment)");
+    OIM_BW(cudaMalloc(&seg, (size_t)(seg_len + 1) * state * sizeof(float)), "cudaMalloc(segment)");
+    OIM_BW(cudaMalloc(&ab, (size_t)seg_len * state * sizeof(float2)), "cudaMalloc(coupling sums)");
     OIM_BW(cudaMalloc(&lam[0], state * sizeof(float)), "cudaMalloc(lambda)");
     OIM_BW(cudaMalloc(&lam[1], state * sizeof(float)), "cudaMalloc(lambda)");
     OIM_BW(cudaMalloc(&cs[0], state * sizeof(float2)), "cudaMalloc(cs)");
     OIM_BW(cudaMalloc(&cs[1], state * sizeof(float2)), "cudaMalloc(cs)");
-    OIM_BW(cudaMalloc(&Y, state * sizeof(float4)), "cudaMalloc(Y)");
+    OIM_BW(cudaMalloc(&Y[0], 2 * state * sizeof(float)), "cudaMalloc(planes)");
+    OIM_BW(cudaMalloc(&Y[1], 2 * state * sizeof(float)), "cudaMalloc(planes)");
     const size_t gbytes = (size_t)G * std::max<int64_t>(T, 1) * sizeof(double);
     OIM_BW(cudaMalloc(&gK, gbytes), "cudaMalloc(grad)");
     OIM_BW(cudaMalloc(&gS, gbytes), "cudaMalloc(grad)");
@@ -1245,27 +1248,33 @@ int oim_backward(oim_run_t r, double* dK, double* dKs, double* dKn, double* loss
     OIM_BW(cudaMemsetAsync(gS, 0, gbytes, s), "clear grad");
     OIM_BW(cudaMemsetAsync(gN, 0, gbytes, s), "clear grad");
     OIM_BW(cudaMemsetAsync(gL, 0, (size_t)G * sizeof(double), s), "clear loss");
-    OIM_BW(cudaMemsetAsync(lam[0], 0, state * sizeof(float), s), "clear lambda");
     // terminal adjoint and loss from the final phases
-    OIM_BW(launch_adj_prep(*r, r->d_theta[r->final_buf], lam[0], Y, s), "adjoint prep");
-    OIM_BW(launch_adj_terminal(*r, Y, lam[0], gL, s), "adjoint terminal");
-    int cur = 0;
+    OIM_BW(launch_adj_planes(*r, r->d_theta[r->final_buf], nullptr, Y[0], s), "adjoint planes");
+    OIM_BW(launch_adj_terminal(*r, Y[0], lam[0], gL, s), "adjoint terminal");
+    int cur = 0, cy = 0;
     const int64_t n_seg = (T + C - 1) / C;
     for (int64_t sg = n_seg - 1; sg >= 0; --sg) {
         const int64_t t0 = sg * C, t1 = std::min<int64_t>(t0 + C, T);
-        // recompute theta_t0 .. theta_{t1-1} from the checkpoint with the forward kernel
+        // recompute theta_t0 .. theta_t1 from the checkpoint with the forward kernel,
+        // keeping the coupling sums of steps t0 .. t1 - 1
         OIM_BW(cudaMemcpyAsync(seg, r->d_ckpt + (size_t)sg * state, state * sizeof(float),
                                cudaMemcpyDeviceToDevice, s), "load checkpoint");
         OIM_BW(launch_cs_from_theta(*r, seg, cs[0], s), "recompute cache");
-        for (int64_t m = 0; m + 1 < t1 - t0; ++m)
+        for (int64_t m = 0; m < t1 - t0; ++m)
             OIM_BW(launch_step_stream_buffers(*r, t0 + m, seg + (size_t)m * state, cs[m & 1],
-                                              seg + (size_t)(m + 1) * state, cs[(m + 1) & 1], s),
+                                              seg + (size_t)(m + 1) * state, cs[(m + 1) & 1],
+                                              ab + (size_t)m * state, s),
                    "recompute step");
+        // the planes the segment's last step gathers: lambda_t1 (c, s)_{t1 - 1}
+        OIM_BW(launch_adj_planes(*r, seg + (size_t)(t1 - 1 - t0) * state, lam[cur], Y[cy], s), "adjoint planes");
         for (int64_t t = t1 - 1; t >= t0; --t) {
             const float* th = seg + (size_t)(t - t0) * state;
-            OIM_BW(launch_adj_prep(*r, th, lam[cur], Y, s), "adjoint prep");
-            OIM_BW(launch_adj_step(*r, t, th, Y, lam[cur], lam[cur ^ 1], gK, gS, gN, s), "adjoint step");
+            const float* th_prev = t > t0 ? th - state : nullptr;
+            OIM_BW(launch_adj_step(*r, t, th, th_prev, ab + (size_t)(t - t0) * state, Y[cy], Y[cy ^ 1], lam[cur],
+                                   lam[cur ^ 1], gK, gS, gN, s),
+                   "adjoint step");
             cur ^= 1;
+            cy ^= 1;
         }
     }
     OIM_BW(cudaStreamSynchronize(s), "backward");

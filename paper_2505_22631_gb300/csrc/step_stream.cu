@@ -110,15 +110,18 @@ __global__ void __launch_bounds__(256) init_stream_kernel(CSRDev csr, StepParams
     C::store4(cs + at, v);
 }
 
-// The plain form (FP32 cache): thread = node x quad of replicas.
-template <bool kUnit, typename C>
+// The plain form (FP32 cache): thread = node x quad of replicas.  kAB: the coupling
+// sums (A, B) of the step are also stored at ab[node][R_pad] (the schedule adjoint's
+// recomputation keeps them, so its reverse sweep gathers only the lambda-weighted pairs).
+template <bool kUnit, typename C, bool kAB = false>
 __global__ void __launch_bounds__(256) step_stream_kernel(CSRDev csr, StepParams P, const float* th_in,
                                                           const typename C::T* __restrict__ cs_in,
                                                           float* th_out,
                                                           typename C::T* __restrict__ cs_out,
                                                           int64_t t_fixed,
                                                           const int32_t* __restrict__ d_t0,
-                                                          int32_t t_add, int quads_fast) {
+                                                          int32_t t_add, int quads_fast,
+                                                          float2* __restrict__ ab = nullptr) {
     // block = blockDim.x replica quads x blockDim.y nodes (no index division); the
     // blocks take their nodes in the batch's heaviest-rows-first order, and with
     // quads_fast the grid's fast dimension runs over replica blocks, so the blocks
@@ -202,6 +205,10 @@ __global__ void __launch_bounds__(256) step_stream_kernel(CSRDev csr, StepParams
     }
     *reinterpret_cast<float4*>(th_out + at) = make_float4(tn[0], tn[1], tn[2], tn[3]);
     C::store4(cs_out + at, ncs);
+    if constexpr (kAB) {
+        reinterpret_cast<float4*>(ab + at)[0] = make_float4(acc[0].x, acc[0].y, acc[1].x, acc[1].y);
+        reinterpret_cast<float4*>(ab + at)[1] = make_float4(acc[2].x, acc[2].y, acc[3].x, acc[3].y);
+    }
 }
 
 // Eight 16-bit (cos, sin) pairs added to, or subtracted from, the accumulators.
@@ -581,16 +588,16 @@ cudaError_t launch_cs_from_theta(const oim_run_s& r, const float* theta, float2*
 
 // One step t of the stream form between explicit buffers (FP32 cache: the adjoint).
 cudaError_t launch_step_stream_buffers(const oim_run_s& r, int64_t t, const float* th_in,
-                                       const float2* cs_in, float* th_out, float2* cs_out,
+                                       const float2* cs_in, float* th_out, float2* cs_out, float2* ab,
                                        cudaStream_t s) {
     const StepParams P = params_of(r);
     const StepGrid q = step_grid(r.p->nodes, r.R_pad / 4);
     if (r.p->unit_weights)
-        step_stream_kernel<true, CacheF32><<<q.grid, q.block, 0, s>>>(
-            r.p->csr(), P, th_in, cs_in, th_out, cs_out, t, nullptr, 0, q.quads_fast);
+        step_stream_kernel<true, CacheF32, true><<<q.grid, q.block, 0, s>>>(
+            r.p->csr(), P, th_in, cs_in, th_out, cs_out, t, nullptr, 0, q.quads_fast, ab);
     else
-        step_stream_kernel<false, CacheF32><<<q.grid, q.block, 0, s>>>(
-            r.p->csr(), P, th_in, cs_in, th_out, cs_out, t, nullptr, 0, q.quads_fast);
+        step_stream_kernel<false, CacheF32, true><<<q.grid, q.block, 0, s>>>(
+            r.p->csr(), P, th_in, cs_in, th_out, cs_out, t, nullptr, 0, q.quads_fast, ab);
     return cudaGetLastError();
 }
 
