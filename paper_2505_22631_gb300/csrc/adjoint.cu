@@ -37,7 +37,13 @@ __global__ void __launch_bounds__(256) adj_planes_kernel(int64_t state, const fl
     const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= state) return;
     float s, c;
-    sincospif(2.0f * theta[gid], &s, &c);
+    if (lam) {   // lambda planes, as the adjoint step writes them (hardware sin / cos)
+        const float2 cs = cos_sin_2pi_fast(theta[gid]);
+        c = cs.x;
+        s = cs.y;
+    } else {     // (c, s) of the final phases for the terminal adjoint and the loss
+        sincospif(2.0f * theta[gid], &s, &c);
+    }
     const float l = lam ? lam[gid] : 1.0f;
     Y[gid] = lam ? l * c : c;
     Y[state + gid] = lam ? l * s : s;
@@ -145,8 +151,10 @@ __global__ void __launch_bounds__(256, 4) adj_step_kernel(CSRDev csr, StepParams
         const float K = P.K[sidx], Ks = P.Ks[sidx];
         const uint4 x = draw_block(P.seed_dev ? *P.seed_dev : P.seed, (uint32_t)g, kStreamNoise, (uint32_t)i, (uint32_t)t,
                                    (uint32_t)quad);
-        const float2 z01 = box_muller(x.x, x.y);
-        const float2 z23 = box_muller(x.z, x.w);
+        // the per-step terms take the hardware sin / cos / log2 / sqrt (absolute errors
+        // ~1e-6, three orders below the adjoint's FP32 tolerance against FP64)
+        const float2 z01 = box_muller_fast(x.x, x.y);
+        const float2 z23 = box_muller_fast(x.z, x.w);
         const float z[4] = {z01.x, z01.y, z23.x, z23.y};
         const float4 ab01 = *reinterpret_cast<const float4*>(AB + at);
         const float4 ab23 = *reinterpret_cast<const float4*>(AB + at + 2);
@@ -155,13 +163,14 @@ __global__ void __launch_bounds__(256, 4) adj_step_kernel(CSRDev csr, StepParams
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
             const float th = theta[at + v];
-            float s, c;
-            sincospif(2.0f * th, &s, &c);
+            const float2 cs1 = cos_sin_2pi_fast(th);
+            const float c = cs1.x, s = cs1.y;
             const float l = lam_in[at + v];
             const float S = c * A[v] + s * B[v];
             const float Cc = c * Pp[v] + s * Q[v];
-            float sq, cq;
-            sincospif(2.0f * (float)P.q * th, &sq, &cq);
+            const float qth = (float)P.q * th;
+            const float2 csq = cos_sin_2pi_fast(qth - floorf(qth));
+            const float sq = csq.y, cq = csq.x;
             const float diag = kTwoPi * K * S - kTwoPi * (float)P.q * Ks * cq;
             lt[v] = l + P.dt * (l * diag - kTwoPi * K * Cc);
             lam_out[at + v] = lt[v];
@@ -176,10 +185,9 @@ __global__ void __launch_bounds__(256, 4) adj_step_kernel(CSRDev csr, StepParams
             // the planes step t - 1 gathers: lambda_t (c, s) of theta_{t-1}
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
-                float s, c;
-                sincospif(2.0f * theta_prev[at + v], &s, &c);
-                Ylam_out[at + v] = lt[v] * c;
-                Ylam_out[state + at + v] = lt[v] * s;
+                const float2 cs0 = cos_sin_2pi_fast(theta_prev[at + v]);
+                Ylam_out[at + v] = lt[v] * cs0.x;
+                Ylam_out[state + at + v] = lt[v] * cs0.y;
             }
         }
     }
