@@ -604,6 +604,23 @@ def run_adjoint(args, rank, world):
     ms = float(np.mean(fw) + np.mean(bw))
     ms = reduce_max(ms, world, device="cuda")
     edge_updates = w.edge_updates() * world
+    # roofline of the backward pass (the recomputation of every segment and the reverse
+    # sweep): per node-replica-step the recomputed FP32 step moves 24 B (phase read and
+    # write, (cos, sin) pair write and read) and stores its coupling sums (8 B); the
+    # adjoint step reads theta_t, theta_{t-1}, lambda_{t+1}, the sums (8 B) and its
+    # lambda-weighted planes (8 B), and writes lambda_t and the next planes (8 B): 40 B;
+    # plus the CSR once per step for each of the two
+    peaks = load_peaks()
+    nrs = w.nodes * w.replicas * T
+    csr_bytes = sum(4 * g.nnz + 8 * (g.n + 1) for g in w.graphs) * T
+    bw_bytes = nrs * (24 + 8 + 40) + 2 * csr_bytes
+    bw_achieved = bw_bytes / (float(np.mean(bw)) / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": bw_achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": bw_achieved / peaks["hbm_gbs"], "traffic": None,
+                "kernel": "backward pass (step_stream_kernel recomputation + adj_step_kernel)",
+                "peak_source": peaks["source"], "algorithmic_bytes_per_launch": bw_bytes / T,
+                "bytes_per_node_replica_step": 72,
+                "kernel_time": "CUDA events around oim_backward, divided by the steps"}
     line = {"metric": "edge-updates/s (forward + schedule adjoint)", "value": edge_updates / (ms / 1e3),
             "unit": "edge-updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms, "ms_forward": float(np.mean(fw)), "ms_backward": float(np.mean(bw)),
@@ -614,6 +631,7 @@ def run_adjoint(args, rank, world):
                        "form": "stream", "precision": "fp32",
                        "timing": "CUDA events around the forward launch sequence and around oim_backward "
                                  "(which includes its scratch allocation and the gradient copies)"},
+            "roofline": roofline, "backward_over_forward": float(np.mean(bw) / np.mean(fw)),
             "mean_loss": float(loss.mean()),
             "gradient_norms": {"dK": float(np.linalg.norm(dK)), "dKs": float(np.linalg.norm(dKs)),
                                "dKn": float(np.linalg.norm(dKn))}}
