@@ -48,6 +48,18 @@ std::string tune_key(const oim_problem_s* p, int32_t replicas, int32_t policy) {
 
 }  // namespace
 
+namespace oim {
+bool cached_choice(const oim_problem_s* p, int32_t replicas, oim_run_opts* out) {
+    const std::string key = tune_key(p, replicas, OIM_PREC_AUTO);
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tune_cache.find(key);
+    if (it == g_tune_cache.end()) return false;
+    *out = it->second.opts;
+    out->graph_forms = it->second.graph_forms.empty() ? nullptr : it->second.graph_forms.data();
+    return true;
+}
+}  // namespace oim
+
 extern "C" int oim_autotune(oim_problem_t p, int32_t replicas, int32_t precision_policy,
                             int64_t probe_steps, void* stream, oim_run_opts* best,
                             double* best_us_per_step) {
@@ -56,6 +68,7 @@ extern "C" int oim_autotune(oim_problem_t p, int32_t replicas, int32_t precision
     if (precision_policy != OIM_PREC_AUTO && precision_policy != OIM_PREC_FP32)
         return fail(OIM_EINVAL, "precision policy must be OIM_PREC_AUTO or OIM_PREC_FP32");
     if (probe_steps < 4) probe_steps = 4;
+    NvtxRange range("oim_autotune");
     const std::string key = tune_key(p, replicas, precision_policy);
     {
         std::lock_guard<std::mutex> lock(g_tune_mutex);

@@ -436,6 +436,19 @@ int choose_form(oim_run_s* r) {
     // the replicas per block of FP32, coupling error ~1e-4 relative); the stream
     // form defaults to FP32 (the plain form) and takes FP16 / BF16 when asked.
     if (prec == OIM_PREC_AUTO) prec = (form == OIM_FORM_STREAM) ? OIM_PREC_FP32 : OIM_PREC_FP16;
+    if (form == OIM_FORM_AUTO && r->opts.precision == OIM_PREC_AUTO && r->opts.checkpoint_every == 0 &&
+        r->opts.replicas_per_block == 0 && r->opts.threads_per_block == 0) {
+        // a shape the autotuner has timed in this process takes its choice
+        oim_run_opts tuned;
+        if (cached_choice(r->p, r->R, &tuned)) {
+            r->opts.form = tuned.form;
+            r->opts.precision = tuned.precision;
+            r->opts.replicas_per_block = tuned.replicas_per_block;
+            r->opts.threads_per_block = tuned.threads_per_block;
+            r->opts.graph_forms = tuned.graph_forms;
+            return choose_form(r);
+        }
+    }
     if (form == OIM_FORM_AUTO) {
         ResidentPlan tmp;
         form = plan_resident(*r->p, r->R_pad, prec, r->opts.replicas_per_block,
@@ -998,6 +1011,7 @@ void oim_destroy_problem(oim_problem_t p) {
 int oim_run(oim_problem_t p, const float* K, const float* Ks, const float* Kn, float dt,
             int64_t steps, int32_t replicas, uint64_t seed, const oim_run_opts* opts,
             oim_run_t* out) {
+    NvtxRange range("oim_run");
     g_last_error.clear();
     if (!out) return fail(OIM_EINVAL, "out is NULL");
     *out = nullptr;
@@ -1043,6 +1057,7 @@ int oim_run(oim_problem_t p, const float* K, const float* Ks, const float* Kn, f
 
 int oim_rerun(oim_run_t r, const float* K, const float* Ks, const float* Kn, float dt, int64_t steps,
               uint64_t seed) {
+    NvtxRange range("oim_rerun");
     g_last_error.clear();
     if (!r) return fail(OIM_EINVAL, "NULL run");
     int rc = validate_schedule_args(dt, steps);
@@ -1082,6 +1097,7 @@ int oim_run_info(oim_run_t r, int64_t* steps, int32_t* replicas, int64_t* n_read
 
 int oim_readout(oim_run_t r, int8_t* spins, double* score, int32_t* best_replica, double* trace,
                 double* energy) {
+    NvtxRange range("oim_readout");
     g_last_error.clear();
     if (!r) return fail(OIM_EINVAL, "NULL run");
     if (!r->ran) return fail(OIM_ESTATE, "run has not executed");
@@ -1199,6 +1215,7 @@ int oim_debug_derivative(oim_problem_t p, const float* theta, int32_t replicas, 
 }
 
 int oim_backward(oim_run_t r, double* dK, double* dKs, double* dKn, double* loss) {
+    NvtxRange range("oim_backward");
     g_last_error.clear();
     if (!r) return fail(OIM_EINVAL, "NULL run");
     if (!r->ran) return fail(OIM_ESTATE, "run has not executed");

@@ -3,6 +3,7 @@
 
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstdint>
 #include <string>
@@ -225,6 +226,19 @@ private:
     int prev_ = -1;
     bool switched_ = false;
 };
+
+// A named range on the profiler's timeline for the lifetime of the object (NVTX; a no-op
+// unless a tool is attached).
+class NvtxRange {
+public:
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
+// the autotuner's cached choice for a problem shape and replica count (false if none)
+bool cached_choice(const oim_problem_s* p, int32_t replicas, oim_run_opts* out);
 
 // error reporting (thread-local message)
 int fail(int code, const std::string& msg);
