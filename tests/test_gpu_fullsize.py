@@ -197,3 +197,60 @@ def test_adjoint_at_schedule_workload_sizes_matches_oracle(orc):
         assert abs(L[gi] - rL) <= 1e-5 * np.abs(g.w).sum()
         for got, ref in ((dK[gi], rK), (dKs[gi], rKs), (dKn[gi], rKn)):
             assert np.max(np.abs(got - ref)) <= 2e-3 * np.max(np.abs(ref)) + 1e-6
+
+
+def test_uneven_batch_in_the_persistent_form(orc):
+    # the form the autotuner picks for the 16-graph uneven batch on the GB300: the 16-bit
+    # stream steps between readouts in one cooperative launch; a full-size 400-step run with
+    # readouts, bit for bit the per-step 16-bit stream form, and every sampled replica's
+    # score recounted from its own spins
+    w = make_workload("uneven16", steps=400)
+    a = run_workload(w, form="persistent", precision="fp16", readout_every=100, seed=9)
+    b = run_workload(w, form="stream", precision="fp16", readout_every=100, seed=9)
+    assert a.info()["form"] == 5
+    pa, pb = a.phases(), b.phases()
+    oa = a.readout()
+    assert np.array_equal(oa["trace"], b.readout()["trace"])
+    for gi in (0, 7, 8, 15):
+        assert np.array_equal(pa[gi], pb[gi])
+        g = w.graphs[gi]
+        spins = orc.readout_f32(2, pa[gi][:16])
+        assert np.array_equal(oa["spins"][gi][:16], spins)
+        assert np.array_equal(oa["score"][gi][:16], orc.scores(g, 2, spins))
+
+
+def test_uneven_batch_with_a_complete_graph_in_the_mixed_form(orc):
+    # 16 uneven graphs and a complete +-1 graph on 2000 nodes, 256 replicas: the mixed form
+    # (the complete graph on the tensor cores, the rest in the 16-bit stream form, on two
+    # streams between readouts).  Over a short horizon the complete graph's sampled
+    # replicas lie within the linear accumulation of the BF16 coupling bound of the oracle
+    # and a CSR member matches the stream form of the whole batch bit for bit; then a
+    # 300-step run with readouts, every sampled score recounted from its own spins
+    w = make_workload("uneven16_k2000", steps=300)
+    G = len(w.graphs)
+    forms = ["stream"] * (G - 1) + ["gemm"]
+    T = 10
+    from paper_2505_22631_gb300 import Problem, Run
+    probs = [Problem.from_graph(g, 2) for g in w.graphs]
+    prob = Problem.batch(probs)
+    K, Ks, Kn = (np.stack(x)[:, :T].copy() for x in (w.K, w.Ks, w.Kn))
+    short = Run(prob, K, Ks, Kn, w.dt, T, w.replicas, 3, form="mixed", precision="fp16", graph_forms=forms)
+    plain = Run(prob, K, Ks, Kn, w.dt, T, w.replicas, 3, form="stream", precision="fp16")
+    ps, pp = short.phases(), plain.phases()
+    assert np.array_equal(ps[8], pp[8])
+    g = w.graphs[-1]
+    d = np.concatenate([rad_dist(ps[-1][r0:r0 + 4], oracle_phases(orc, g, 2, w.K[-1], w.Ks[-1], w.Kn[-1], w.dt,
+                                                                  T, 4, 3, graph=G - 1, replica_offset=r0,
+                                                                  nthreads=16)).ravel()
+                        for r0 in (0, 128, 252)])
+    assert d.max() <= coupling_bound_rad(g, w.K[-1], T, w.dt)
+    assert np.median(d) <= 1e-3
+    full = Run(prob, *(np.stack(x).copy() for x in (w.K, w.Ks, w.Kn)), w.dt, w.steps, w.replicas, 5,
+               form="mixed", precision="fp16", readout_every=100, graph_forms=forms)
+    out = full.readout()
+    ph = full.phases()
+    for gi in (0, 15, G - 1):
+        spins = orc.readout_f32(2, ph[gi][:8])
+        assert np.array_equal(out["spins"][gi][:8], spins)
+        assert np.array_equal(out["score"][gi][:8], orc.scores(w.graphs[gi], 2, spins))
+        assert np.array_equal(out["trace"][gi, -1], out["score"][gi])
