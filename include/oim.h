@@ -102,7 +102,12 @@ typedef struct oim_run_opts {
     const int32_t* graph_forms; /* OIM_FORM_MIXED: int32[graphs], OIM_FORM_STREAM  */
                                 /* or OIM_FORM_GEMM for each graph of the batch    */
                                 /* (read by oim_run; NULL otherwise)               */
-    int32_t reserved[6];
+    int32_t csr_scores;         /* nonzero: every readout scores every graph with  */
+                                /* the CSR pass.  0: a dense-form graph (dense     */
+                                /* form, dense member of a mixed run) with q = 2   */
+                                /* and integer |w_ij| <= 256 is scored on the      */
+                                /* tensor cores, (sum w + s^T W s) / 4, exact      */
+    int32_t reserved[5];
 } oim_run_opts;
 
 /* Fill *opts with the defaults: AUTO form and precision, readout at the end,

@@ -95,9 +95,11 @@ class Run:
 
     def __init__(self, problem: Problem, K, Ks, Kn, dt, steps, replicas, seed, form="auto",
                  precision="auto", readout_every=0, stream=None, use_graph=True,
-                 replicas_per_block=0, threads_per_block=0, graph_forms=None):
+                 replicas_per_block=0, threads_per_block=0, graph_forms=None, csr_scores=False):
         """graph_forms (form "mixed"): one of "stream" / "gemm" (or the OIM_FORM_* values)
-        per graph of the batch."""
+        per graph of the batch.  csr_scores: score every graph with the CSR pass (by
+        default dense-form graphs with q = 2 and small integer weights are scored on the
+        tensor cores)."""
         self.problem = problem
         o = oim_default_opts()
         o.form = FORMS[form] if isinstance(form, str) else int(form)
@@ -107,6 +109,7 @@ class Run:
         o.use_graph = int(bool(use_graph))
         o.replicas_per_block = int(replicas_per_block)
         o.threads_per_block = int(threads_per_block)
+        o.csr_scores = int(bool(csr_scores))
         forms = None
         if graph_forms is not None:
             forms = np.ascontiguousarray([FORMS[f] if isinstance(f, str) else int(f) for f in graph_forms],

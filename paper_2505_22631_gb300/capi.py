@@ -63,7 +63,8 @@ class oim_run_opts(ctypes.Structure):
         ("threads_per_block", ctypes.c_int32),
         ("checkpoint_every", ctypes.c_int32),
         ("graph_forms", ctypes.c_void_p),
-        ("reserved", ctypes.c_int32 * 6),
+        ("csr_scores", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 5),
     ]
 
 

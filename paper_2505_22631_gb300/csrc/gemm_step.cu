@@ -15,6 +15,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <algorithm>
+#include <cmath>
 #include <string>
 
 #include "oim_device.cuh"
@@ -303,6 +305,135 @@ __global__ void gemm_to_common_kernel(int n, int n_pad, int R_pad, int node_off,
     out[(size_t)(node_off + i) * R_pad + r] = theta[(size_t)r * n_pad + i];
 }
 
+// ---------------------------------------------------------------- readout on tensor cores
+// X^T rows 2r and 2r + 1 = the spins s_r = +-1 of replica r (BF16, exact), 0 beyond n.
+__global__ void gemm_spins_kernel(int n, int n_pad, int R_pad, const float* __restrict__ theta,
+                                  __nv_bfloat16* __restrict__ x) {
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= (int64_t)R_pad * n_pad) return;
+    const int r = (int)(gid / n_pad), i = (int)(gid - (int64_t)r * n_pad);
+    const float sgn = i < n ? (spin_of(theta[gid], 2) ? -1.0f : 1.0f) : 0.0f;
+    x[(size_t)(2 * r) * n_pad + i] = __float2bfloat16_rn(sgn);
+    x[(size_t)(2 * r + 1) * n_pad + i] = __float2bfloat16_rn(sgn);
+}
+
+// The agreeing weight of every replica of one dense graph from P^T = X^T W with the spin
+// rows above: a 128 x 128 tile of P^T (64 replicas x 128 nodes) per block, one thread
+// streaming the K blocks with TMA and issuing tcgen05.mma into TMEM, then each thread of
+// an even X^T row (replica r) sums s_{r,c} P[r][c] over the tile's 128 columns (integers,
+// exact in FP32) and adds a quarter of it, FP64, to agree[r]; the block of the first
+// column tile also adds a quarter of sum_ij w_ij.  sum_{i<j} w_ij [s_i == s_j] =
+// (sum_ij w_ij + s^T W s) / 4.  Bounded waits as in the step kernel.
+struct ScoreArgs {
+    const float* theta;      // [R_pad][n_pad] phases (the spins' source, for s_{r,c})
+    double* agree;           // [G][row_stride][R_pad]
+    int64_t row_stride, k;   // readout slot k, or from the device step base
+    const int32_t* t0;
+    int32_t t_add, every;
+    int32_t graph, n_pad, R, R_pad;
+    double wsum4;            // sum_ij w_ij / 4
+    int32_t* err;
+};
+
+__global__ void __launch_bounds__(128, 1)
+    gemm_score_kernel(const __grid_constant__ CUtensorMap mX, const __grid_constant__ CUtensorMap mW, ScoreArgs a) {
+    using namespace tc;
+    constexpr int S = 4, kBN = 128, kBBytes = kBN * 128;
+    constexpr uint32_t kCols = 128;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* base =
+        reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    unsigned char* sA = base;
+    unsigned char* sB = base + S * kABytes;
+    __shared__ __align__(8) uint64_t full[S], empty[S], done;
+    __shared__ uint32_t tmem_slot;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * kBN;
+    const int KB = a.n_pad / kBK;
+    if (threadIdx.x == 0) {
+        prefetch_map(&mX);
+        prefetch_map(&mW);
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(&done, 1);
+        fence_barrier_init();
+    }
+    if (warp == 0) tmem_alloc(&tmem_slot, kCols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+    if (threadIdx.x == 0) {
+        const uint32_t idesc = idesc_bf16_f32(kBM, kBN);
+        int pending[S];
+        auto load = [&](int kb) {
+            const int s = kb % S;
+            mbar_arrive_expect_tx(&full[s], kABytes + kBBytes);
+            tma_load_2d(sA + s * kABytes, &mX, kb * kBK, m0, &full[s]);
+            tma_load_2d(sB + s * kBBytes, &mW, kb * kBK, n0, &full[s]);
+            pending[s] = kb;
+        };
+        for (int s = 0; s < S; ++s) pending[s] = -1;
+        for (int kb = 0; kb < KB && kb < S; ++kb) load(kb);
+        for (int kb = 0; kb < KB; ++kb) {
+            const int s = kb % S;
+            if (!mbar_wait(&full[s], (kb / S) & 1, a.err, kErrFullWait)) break;
+            pending[s] = -1;
+            tc_fence_after();
+            const uint32_t a0 = smem_u32(sA + s * kABytes), b0 = smem_u32(sB + s * kBBytes);
+#pragma unroll
+            for (int k = 0; k < kBK / 16; ++k)
+                umma_bf16(tmem, sdesc_kmajor_sw128(a0 + 32 * k), sdesc_kmajor_sw128(b0 + 32 * k), idesc,
+                          (kb | k) != 0);
+            umma_commit(&empty[s]);
+            if (kb + S < KB) {
+                if (!mbar_wait(&empty[s], (kb / S) & 1, a.err, kErrEmptyWait)) break;
+                load(kb + S);
+            }
+        }
+        // loads still in flight after a wait that gave up land before the block exits
+        for (int s = 0; s < S; ++s)
+            if (pending[s] >= 0) mbar_wait(&full[s], (pending[s] / S) & 1, a.err, kErrFullWait);
+        umma_commit(&done);
+    }
+    __syncwarp();
+    const bool have = __all_sync(0xffffffffu, mbar_wait(&done, 0, a.err, kErrDoneWait));
+    tc_fence_after();
+    if (have) {
+        const int row = m0 + warp * 32 + lane;   // X^T row; even rows carry replica row / 2
+        const int r = row >> 1;
+        const float* th = a.theta + (size_t)r * a.n_pad + n0;
+        float p = 0.0f;
+#pragma unroll 1
+        for (int c = 0; c < kBN; c += 16) {
+            if (n0 + c >= a.n_pad) break;   // the last tile may reach past n_pad (a multiple of 64)
+            uint32_t v[16];
+            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
+#pragma unroll
+            for (int j = 0; j < 16; j += 4) {
+                const float4 t4 = *reinterpret_cast<const float4*>(th + c + j);
+                const float tt[4] = {t4.x, t4.y, t4.z, t4.w};
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    // columns beyond n hold spin 0 in X^T and zero rows of W: P is 0 there
+                    const float sg = spin_of(tt[u], 2) ? -1.0f : 1.0f;
+                    p = __fmaf_rn(sg, __uint_as_float(v[j + u]), p);
+                }
+            }
+        }
+        if ((row & 1) == 0 && r < a.R) {
+            const int64_t k = a.t0 ? ((int64_t)(*a.t0) + a.t_add) / a.every - 1 : a.k;
+            double* dst = a.agree + ((int64_t)a.graph * a.row_stride + k) * a.R_pad + r;
+            atomicAdd(dst, 0.25 * (double)p + (blockIdx.x == 0 ? a.wsum4 : 0.0));
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, kCols);
+}
+
 }  // namespace
 
 // 128-wide tiles with three stages use 97 KB of shared memory and 256 TMEM columns,
@@ -331,6 +462,8 @@ int gemm_bn_for(const oim_run_s& r, int n) {
     return cost(112) < cost(128) ? 112 : 128;
 }
 
+constexpr size_t kScoreSmem = 4 * (size_t)(kABytes + 128 * 128) + 1024;
+
 // Device state of the dense form for graph `graph` of the problem, appended to
 // oim_run_s::gemms (the dense form's one graph, or a dense member of a mixed run).
 int gemm_setup(oim_run_s& r, int graph) {
@@ -357,6 +490,20 @@ int gemm_setup(oim_run_s& r, int graph) {
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "dense coupling matrix");
     int rc = make_map_bf16(&st.map_w, st.w, st.n_pad, st.n_pad, (uint64_t)st.n_pad * 2, st.bn);
+    if (rc == OIM_OK) rc = make_map_bf16(&st.map_w128, st.w, st.n_pad, st.n_pad, (uint64_t)st.n_pad * 2, 128);
+    // readouts on the tensor cores when every weight of the graph is exact in BF16
+    // (and every partial sum an integer below 2^24: 128 columns of row sums below 2^17)
+    st.score_tc = r.p->q == 2;
+    for (int32_t i = 0; i < gd.n && st.score_tc; ++i) {
+        const int32_t v = gd.node_off + i;
+        double row = 0.0;
+        for (int64_t e = r.p->h_rowp[(size_t)v]; e < r.p->h_rowp[(size_t)v + 1]; ++e) {
+            const float x = r.p->h_w[(size_t)e];
+            if (x != std::floor(x) || std::fabs(x) > 256.0f) st.score_tc = false;
+            row += std::fabs((double)x);
+        }
+        if (row >= 131072.0) st.score_tc = false;
+    }
     for (int b = 0; b < 2 && rc == OIM_OK; ++b)
         rc = make_map_bf16(&st.map_x[b], st.x[b], st.n_pad, 2 * (uint64_t)r.R_pad, (uint64_t)st.n_pad * 2, 128);
     if (rc != OIM_OK) return rc;
@@ -369,6 +516,8 @@ int gemm_setup(oim_run_s& r, int graph) {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(gemm_step_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)TileShape<256>::kSmemBytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(gemm_score_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScoreSmem);
     if (e != cudaSuccess) return cuda_fail(e, "dense form shared memory");
     return OIM_OK;
 }
@@ -425,6 +574,36 @@ cudaError_t launch_gemm_step_at(const oim_run_s& r, int k, int64_t t, const int3
     else
         gemm_step_kernel<128><<<grid, TileShape<128>::kThreads, TileShape<128>::kSmemBytes, s>>>(
             st.map_x[t & 1], st.map_w, a);
+    return cudaGetLastError();
+}
+
+// The agreeing weight of dense state k's replicas into readout slot k_slot (or the slot
+// of the device step base), on the tensor cores: the spins into X^T buffer xbuf (the one
+// the next step does not read), then P^T = X^T W.  Requires st.score_tc.
+cudaError_t launch_gemm_score(const oim_run_s& r, int k, int64_t k_slot, const int32_t* d_t0, int32_t t_add,
+                              int xbuf, cudaStream_t s) {
+    const GemmState& st = r.gemms[k];
+    const int64_t total = (int64_t)r.R_pad * st.n_pad;
+    gemm_spins_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(
+        st.n, st.n_pad, r.R_pad, st.theta, reinterpret_cast<__nv_bfloat16*>(st.x[xbuf]));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    ScoreArgs a;
+    a.theta = st.theta;
+    a.agree = r.d_trace;
+    a.row_stride = r.readouts_cap;
+    a.k = k_slot;
+    a.t0 = d_t0;
+    a.t_add = t_add;
+    a.every = (int32_t)std::max<int64_t>(1, r.readout_every);
+    a.graph = st.graph;
+    a.n_pad = st.n_pad;
+    a.R = r.R;
+    a.R_pad = r.R_pad;
+    a.wsum4 = 0.5 * r.p->graphs[st.graph].wtot;   // sum_ij w_ij / 4 = 2 wtot / 4
+    a.err = r.d_err;
+    const dim3 grid((unsigned)((st.n_pad + 127) / 128), (unsigned)((2 * r.R_pad) / kBM));
+    gemm_score_kernel<<<grid, 128, kScoreSmem, s>>>(st.map_x[xbuf], st.map_w128, a);
     return cudaGetLastError();
 }
 

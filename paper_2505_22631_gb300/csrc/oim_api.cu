@@ -46,6 +46,11 @@ cudaError_t launch_gemm_init(const oim_run_s& r, int k, cudaStream_t s);
 cudaError_t launch_set_seed(uint64_t* d_seed, uint64_t seed, cudaStream_t s);
 cudaError_t launch_gemm_step_at(const oim_run_s& r, int k, int64_t t, const int32_t* d_t0, cudaStream_t s);
 cudaError_t launch_gemm_to_common(const oim_run_s& r, int k, float* out, cudaStream_t s);
+cudaError_t launch_gemm_score(const oim_run_s& r, int k, int64_t k_slot, const int32_t* d_t0, int32_t t_add,
+                              int xbuf, cudaStream_t s);
+
+// dense state k is scored on the tensor cores at readouts
+inline bool tc_scored(const oim_run_s& r, int k) { return r.score_split && r.gemms[(size_t)k].score_tc; }
 cudaError_t launch_adj_planes(const oim_run_s& r, const float* theta, const float* lam, float* Y,
                               cudaStream_t s);
 cudaError_t launch_adj_terminal(const oim_run_s& r, const float* Y, float* lam, double* loss, cudaStream_t s);
@@ -307,6 +312,8 @@ void free_run_buffers(oim_run_s* r) {
     dev_free(r->d_shead_sub);
     dev_free(r->d_sdesc_sub);
     r->sub_slots = -1;
+    r->score_ranges.clear();
+    r->score_split = false;
     if (r->aux) cudaStreamDestroy(r->aux);
     if (r->ev_fork) cudaEventDestroy(r->ev_fork);
     if (r->ev_join) cudaEventDestroy(r->ev_join);
@@ -520,6 +527,25 @@ int allocate_run(oim_run_s* r) {
             OIM_CUDA(cudaEventCreateWithFlags(&r->ev_join, cudaEventDisableTiming), "create join event");
         }
     }
+    // graphs scored on the tensor cores leave the CSR score pass
+    r->score_ranges.clear();
+    r->score_split = false;
+    if (!r->opts.csr_scores) {
+        std::vector<int2> tc;
+        for (const GemmState& st : r->gemms)
+            if (st.score_tc) {
+                const GraphDev& gd = r->p->graphs[(size_t)st.graph];
+                tc.push_back(make_int2(gd.node_off, gd.node_off + gd.n));
+            }
+        std::sort(tc.begin(), tc.end(), [](int2 a, int2 b) { return a.x < b.x; });
+        int lo = 0;
+        for (const int2& c : tc) {
+            if (c.x > lo) r->score_ranges.push_back(make_int2(lo, c.x));
+            lo = c.y;
+        }
+        if (lo < r->p->nodes) r->score_ranges.push_back(make_int2(lo, (int)r->p->nodes));
+        r->score_split = !tc.empty();
+    }
     if (r->form == OIM_FORM_RESIDENT) {
         const auto& items = r->plan.items;
         OIM_CUDA(dev_alloc(&r->d_items, items.size()), "cudaMalloc(items)");
@@ -571,11 +597,26 @@ cudaError_t step_parts(const oim_run_s& r, int64_t t, const int32_t* d_t0, cudaS
     return e;
 }
 
-// the dense graphs' phases into the common layout (readouts and the end of a run)
-cudaError_t common_parts(const oim_run_s& r, cudaStream_t s) {
+// the dense graphs' phases into the common layout (readouts and the end of a run); at
+// readouts (scored_only) only those of the graphs that the CSR score pass scores
+cudaError_t common_parts(const oim_run_s& r, cudaStream_t s, bool scored_only = false) {
     cudaError_t e = cudaSuccess;
     for (size_t k = 0; k < r.gemms.size() && e == cudaSuccess; ++k)
-        e = launch_gemm_to_common(r, (int)k, r.d_theta[0], s);
+        if (!(scored_only && tc_scored(r, (int)k))) e = launch_gemm_to_common(r, (int)k, r.d_theta[0], s);
+    return e;
+}
+
+// The readout after `b` steps (an offset from *d_t0 in a replayed chunk) into slot
+// `slot`: the graphs scored on the tensor cores from their spins in the X^T buffer that
+// step b - 1 read (the next step writes it again), the others by the CSR score pass.
+cudaError_t score_parts(const oim_run_s& r, const float* th, int64_t slot, const int32_t* d_t0, int64_t b,
+                        cudaStream_t s) {
+    cudaError_t e = cudaSuccess;
+    for (size_t k = 0; k < r.gemms.size() && e == cudaSuccess; ++k)
+        if (tc_scored(r, (int)k))
+            e = launch_gemm_score(r, (int)k, slot, d_t0, (int32_t)b, (int)((b - 1) & 1), s);
+    if (e == cudaSuccess && !(r.score_split && r.score_ranges.empty()))
+        e = d_t0 ? launch_score_at(r, th, 0, d_t0, (int32_t)b, s) : launch_score(r, th, slot, s);
     return e;
 }
 
@@ -629,9 +670,8 @@ cudaError_t enqueue_steps(const oim_run_s& r, int64_t t0, int64_t t1, const int3
         }
         if (e == cudaSuccess && re > 0 && b % re == 0) {
             float* th = readout_theta(r, b - 1);
-            e = common_parts(r, q);
-            if (e == cudaSuccess)
-                e = d_t0 ? launch_score_at(r, th, 0, d_t0, (int32_t)b, q) : launch_score(r, th, b / re - 1, q);
+            e = common_parts(r, q, true);
+            if (e == cudaSuccess) e = score_parts(r, th, b / re - 1, d_t0, b, q);
         }
         a = b;
     }
@@ -1113,7 +1153,7 @@ int oim_readout(oim_run_t r, int8_t* spins, double* score, int32_t* best_replica
             OIM_CUDA(cudaMemsetAsync(r->d_trace + ((size_t)g * r->readouts_cap + k_final) * r->R_pad, 0,
                                      (size_t)r->R_pad * sizeof(double), s),
                      "clear final row");
-        OIM_CUDA(launch_score(*r, theta, k_final, s), "score launch");
+        OIM_CUDA(score_parts(*r, theta, k_final, nullptr, r->steps, s), "score launch");
         OIM_CUDA(launch_finalize(*r, k_final, r->d_score, s), "finalize launch");
     }
     if (energy) {

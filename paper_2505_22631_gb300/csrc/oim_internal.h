@@ -60,6 +60,10 @@ struct GemmState {
     void* w = nullptr;                 // [n_pad][n_pad] bf16 coupling matrix
     CUtensorMap map_x[2];
     CUtensorMap map_w;
+    // readouts on the tensor cores (q = 2, every weight an integer of magnitude <= 256,
+    // exact in BF16): the agreeing weight as (sum_ij w_ij + s^T W s) / 4 for spins s = +-1
+    bool score_tc = false;
+    CUtensorMap map_w128;              // W in 128-row boxes for the score product
 };
 
 struct CSRDev {
@@ -172,6 +176,10 @@ struct oim_run_s {
     uint4* d_shead_sub = nullptr;
     uint32_t* d_sdesc_sub = nullptr;
     int32_t sub_slots = -1;
+    // with score_split: the node ranges [x, y) whose scores the CSR score pass computes
+    // (the graphs not scored on the tensor cores), in node order; otherwise every node
+    std::vector<int2> score_ranges;
+    bool score_split = false;
     // mixed runs with both parts: the dense members step on a second stream, forked
     // from the run's stream after each readout and joined before the next one
     cudaStream_t aux = nullptr;

@@ -40,15 +40,16 @@ constexpr int kScoreQuads = 32, kScoreLanes = 8;
 
 __global__ void __launch_bounds__(kScoreQuads * kScoreLanes) score_kernel(
     CSRDev csr, const int8_t* __restrict__ spins, int R_pad, double* __restrict__ agree, int64_t row_stride,
-    int64_t k_fixed, int npt, const int32_t* __restrict__ d_t0, int32_t t_add, int32_t every) {
+    int64_t k_fixed, int npt, const int32_t* __restrict__ d_t0, int32_t t_add, int32_t every, int node_lo,
+    int node_hi) {
     __shared__ double red[kScoreLanes][kScoreQuads][4];
     // readout slot: fixed, or (in a replayed chunk of steps) from the device step base
     const int64_t k = d_t0 ? ((int64_t)(*d_t0) + t_add) / every - 1 : k_fixed;
     const int quads = R_pad >> 2;
     const int quad = blockIdx.x * kScoreQuads + threadIdx.x;
     const bool valid = quad < quads;      // no early exit: the block synchronises below
-    const int chunk0 = blockIdx.y * kScoreLanes * npt;
-    const int chunk1 = min(chunk0 + kScoreLanes * npt, csr.nodes);
+    const int chunk0 = node_lo + blockIdx.y * kScoreLanes * npt;
+    const int chunk1 = min(chunk0 + kScoreLanes * npt, node_hi);
     const bool one_graph = csr.node_graph[chunk0] == csr.node_graph[chunk1 - 1];
     const char4* sp = reinterpret_cast<const char4*>(spins) + (valid ? quad : 0);
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
@@ -229,10 +230,20 @@ cudaError_t launch_score_at(const oim_run_s& r, const float* theta, int64_t k, c
     const int npt = nodes_per_thread(r);
     const int chunk = kScoreLanes * npt;
     dim3 block(kScoreQuads, kScoreLanes);
-    dim3 grid((quads + kScoreQuads - 1) / kScoreQuads, (unsigned)((r.p->nodes + chunk - 1) / chunk));
-    score_kernel<<<grid, block, 0, s>>>(r.p->csr(), r.d_spins, r.R_pad, r.d_trace, r.readouts_cap, k, npt,
-                                        d_t0, t_add, (int32_t)std::max<int64_t>(1, r.readout_every));
-    return cudaGetLastError();
+    // the node ranges whose graphs are not scored on the tensor cores (all nodes by default)
+    const int2 all = make_int2(0, (int)r.p->nodes);
+    const int2* rg = r.score_split ? r.score_ranges.data() : &all;
+    const size_t nr = r.score_split ? r.score_ranges.size() : 1;
+    for (size_t q = 0; q < nr; ++q) {
+        if (rg[q].y <= rg[q].x) continue;
+        dim3 grid((quads + kScoreQuads - 1) / kScoreQuads, (unsigned)((rg[q].y - rg[q].x + chunk - 1) / chunk));
+        score_kernel<<<grid, block, 0, s>>>(r.p->csr(), r.d_spins, r.R_pad, r.d_trace, r.readouts_cap, k, npt,
+                                            d_t0, t_add, (int32_t)std::max<int64_t>(1, r.readout_every), rg[q].x,
+                                            rg[q].y);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_finalize(const oim_run_s& r, int64_t k, double* score, cudaStream_t s) {

@@ -49,11 +49,12 @@ def test_opts_struct_layout_matches_header(capi):
     #include <stddef.h>
     #include "oim.h"
     int main(void) {
-        printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(oim_run_opts),
+        printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(oim_run_opts),
                offsetof(oim_run_opts, readout_every), offsetof(oim_run_opts, stream),
                offsetof(oim_run_opts, use_graph), offsetof(oim_run_opts, replicas_per_block),
                offsetof(oim_run_opts, threads_per_block), offsetof(oim_run_opts, checkpoint_every),
-               offsetof(oim_run_opts, graph_forms), offsetof(oim_run_opts, reserved));
+               offsetof(oim_run_opts, graph_forms), offsetof(oim_run_opts, csr_scores),
+               offsetof(oim_run_opts, reserved));
         return 0;
     }
     """
@@ -67,7 +68,7 @@ def test_opts_struct_layout_matches_header(capi):
     S = capi.oim_run_opts
     got = [ctypes.sizeof(S), S.readout_every.offset, S.stream.offset, S.use_graph.offset,
            S.replicas_per_block.offset, S.threads_per_block.offset, S.checkpoint_every.offset,
-           S.graph_forms.offset, S.reserved.offset]
+           S.graph_forms.offset, S.csr_scores.offset, S.reserved.offset]
     assert got == vals
 
 
