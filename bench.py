@@ -313,7 +313,9 @@ def main():
     ap.add_argument("--replicas", type=int, default=0, help="override the workload's replicas")
     ap.add_argument("--adjoint", action="store_true",
                     help="time the checkpointed forward run plus oim_backward (schedule gradients)")
-    ap.add_argument("--checkpoint-every", type=int, default=100)
+    ap.add_argument("--checkpoint-every", type=int, default=0,
+                    help="adjoint: checkpoint period (0: every step, with each step's coupling sums, "
+                         "when that fits in device memory, else 100)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -562,8 +564,9 @@ def main():
 
 
 def run_adjoint(args, rank, world):
-    """Schedule-gradient pass: FP32 stream forward with a checkpoint every C steps,
-    then oim_backward (recompute each segment, reverse sweep).  Reported as edge-updates
+    """Schedule-gradient pass: FP32 stream forward keeping the whole trajectory (or a
+    checkpoint every C steps), then oim_backward (the reverse sweep, after recomputing each
+    segment when only checkpoints were kept).  Reported as edge-updates
     of the forward trajectory per second of forward + backward."""
     import torch
     from paper_2505_22631_gb300 import Problem, build, capi  # noqa: F401
@@ -577,49 +580,67 @@ def run_adjoint(args, rank, world):
     dK, dKs, dKn = (np.zeros((G, T)) for _ in range(3))
     loss = np.zeros(G)
 
+    # checkpoint period: every step with its coupling sums (12 B per node-replica-step:
+    # the library keeps the sums when they fit with a tenth of the device to spare), else
+    # a checkpoint every 100 steps and a recomputation of each segment
+    C = args.checkpoint_every
+    if C <= 0:
+        free_b, total_b = torch.cuda.mem_get_info()
+        need = 12 * w.nodes * (w.replicas + 3) * T
+        C = 1 if need + max(total_b // 10, 2 << 30) + (4 << 30) <= free_b else 100
+    o = capi.oim_default_opts()
+    o.form = capi.OIM_FORM_STREAM
+    o.precision = capi.OIM_PREC_FP32
+    o.checkpoint_every = C
+    o.use_graph = 1
+    o.stream = int(stream.cuda_stream)
+    # the run is made once and re-run per seed (buffers kept, the whole run replayed from
+    # a CUDA graph once its shape comes back)
+    free0 = torch.cuda.mem_get_info()[0]
+    run = capi.oim_run(prob.handle, K, Ks, Kn, w.dt, T, w.replicas, 11, o)
+    # the library kept every step's coupling sums if the run holds them (8 B per
+    # node-replica-step on top of the phases)
+    whole = C == 1 and free0 - torch.cuda.mem_get_info()[0] >= 12 * w.nodes * w.replicas * T
+    capi.oim_backward(run, dK, dKs, dKn, loss)
+
     def step(seed):
-        o = capi.oim_default_opts()
-        o.form = capi.OIM_FORM_STREAM
-        o.precision = capi.OIM_PREC_FP32
-        o.checkpoint_every = args.checkpoint_every
-        o.use_graph = 1
-        o.stream = int(stream.cuda_stream)
         e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         e0.record(stream)
-        r = capi.oim_run(prob.handle, K, Ks, Kn, w.dt, T, w.replicas, seed, o)
+        capi.oim_rerun(run, K, Ks, Kn, w.dt, T, seed)
         e1.record(stream)
-        capi.oim_backward(r, dK, dKs, dKn, loss)   # synchronous
+        capi.oim_backward(run, dK, dKs, dKn, loss)   # synchronous
         e2.record(stream)
         torch.cuda.synchronize()
-        capi.oim_destroy_run(r)
         return e0.elapsed_time(e1), e1.elapsed_time(e2)
 
     for k in range(args.warmup):
-        step(seed=11 + k)
+        step(seed=12 + k)
     fw, bw = [], []
     for k in range(args.steps):
         a, b = step(seed=101 + k)
         fw.append(a)
         bw.append(b)
+    capi.oim_destroy_run(run)
     ms = float(np.mean(fw) + np.mean(bw))
     ms = reduce_max(ms, world, device="cuda")
     edge_updates = w.edge_updates() * world
-    # roofline of the backward pass (the recomputation of every segment and the reverse
-    # sweep): per node-replica-step the recomputed FP32 step moves 24 B (phase read and
-    # write, (cos, sin) pair write and read) and stores its coupling sums (8 B); the
-    # adjoint step reads theta_t, theta_{t-1}, lambda_{t+1}, the sums (8 B) and its
-    # lambda-weighted planes (8 B), and writes lambda_t and the next planes (8 B): 40 B;
-    # plus the CSR once per step for each of the two
+    # roofline of the backward pass: per node-replica-step the adjoint step reads theta_t,
+    # theta_{t-1}, lambda_{t+1}, the coupling sums (8 B) and its lambda-weighted planes
+    # (8 B), and writes lambda_t and the next planes (8 B): 40 B, plus the CSR once per
+    # step.  With a recomputation the recomputed FP32 step adds 24 B (phase read and write,
+    # (cos, sin) pair write and read), the stored sums 8 B and the CSR once more.
     peaks = load_peaks()
     nrs = w.nodes * w.replicas * T
     csr_bytes = sum(4 * g.nnz + 8 * (g.n + 1) for g in w.graphs) * T
-    bw_bytes = nrs * (24 + 8 + 40) + 2 * csr_bytes
+    per_nrs = 40 if whole else 72
+    bw_bytes = nrs * per_nrs + (1 if whole else 2) * csr_bytes
     bw_achieved = bw_bytes / (float(np.mean(bw)) / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": bw_achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": bw_achieved / peaks["hbm_gbs"], "traffic": None,
-                "kernel": "backward pass (step_stream_kernel recomputation + adj_step_kernel)",
+                "kernel": "backward pass (adj_step_kernel" + (")" if whole else
+                                                              " + step_stream_kernel recomputation)"),
                 "peak_source": peaks["source"], "algorithmic_bytes_per_launch": bw_bytes / T,
-                "bytes_per_node_replica_step": 72,
+                "bytes_per_node_replica_step": per_nrs,
                 "kernel_time": "CUDA events around oim_backward, divided by the steps"}
     line = {"metric": "edge-updates/s (forward + schedule adjoint)", "value": edge_updates / (ms / 1e3),
             "unit": "edge-updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -627,7 +648,9 @@ def run_adjoint(args, rank, world):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (f64 gradient sums)",
             "data": "synthetic",
             "config": {"workload": w.name, "graphs": len(w.graphs), "nodes": w.nodes, "replicas": w.replicas,
-                       "euler_steps": T, "checkpoint_every": args.checkpoint_every,
+                       "euler_steps": T, "checkpoint_every": C,
+                       "trajectory": "whole (phases and coupling sums of every step kept)" if whole
+                       else "checkpoints, each segment recomputed",
                        "form": "stream", "precision": "fp32",
                        "timing": "CUDA events around the forward launch sequence and around oim_backward "
                                  "(which includes its scratch allocation and the gradient copies)"},

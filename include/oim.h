@@ -98,7 +98,8 @@ typedef struct oim_run_opts {
                                 /* size; dense form: 320 (128-wide tiles) or 576  */
                                 /* (256-wide tiles)                                */
     int32_t checkpoint_every;   /* keep phases every this many steps for           */
-                                /* oim_backward (0: no checkpoints)                */
+                                /* oim_backward (0: no checkpoints; 1: every step, */
+                                /* with its coupling sums when they fit)           */
     const int32_t* graph_forms; /* OIM_FORM_MIXED: int32[graphs], OIM_FORM_STREAM  */
                                 /* or OIM_FORM_GEMM for each graph of the batch    */
                                 /* (read by oim_run; NULL otherwise)               */
@@ -260,7 +261,11 @@ int oim_autotune(oim_problem_t p, int32_t replicas, int32_t precision_policy, in
  * paper tunes K, Ks, Kn by hand, Sec. IV-B).  The noise enters pathwise: the
  * gradient is that of the trajectory with the run's own Philox draws.
  * The run must use the stream form in FP32 with checkpoint_every > 0; phases are
- * recomputed between checkpoints, so memory is checkpoint_every x state.
+ * recomputed between checkpoints, so memory is checkpoint_every x state.  With
+ * checkpoint_every = 1 the forward pass also keeps every step's coupling sums
+ * (8 B per node-replica-step, on top of the 4 B of its phases) when they fit in
+ * device memory with a tenth of it (at least 2 GiB) to spare, and the backward pass
+ * then recomputes nothing; otherwise it recomputes each step from its phases.
  *   dK, dKs, dKn  double[graphs][steps] each (host or device, may be NULL)
  *   loss          double[graphs] (host or device, may be NULL): L_g
  * Synchronous.  Errors: OIM_ESTATE (no checkpoints, wrong form), OIM_ENOMEM, OIM_ECUDA.

@@ -308,6 +308,8 @@ void free_run_buffers(oim_run_s* r) {
     dev_free(r->d_bar);
     dev_free(r->d_items);
     dev_free(r->d_ckpt);
+    dev_free(r->d_ab);
+    r->ab_cap = 0;
     dev_free(r->d_srow_sub);
     dev_free(r->d_shead_sub);
     dev_free(r->d_sdesc_sub);
@@ -361,6 +363,21 @@ int ensure_step_buffers(oim_run_s* r, int64_t steps) {
             r->ckpt_cap = need;
             OIM_CUDA(dev_alloc(&r->d_ckpt, (size_t)need * r->p->nodes * r->R_pad), "cudaMalloc(checkpoints)");
         }
+    }
+    if (r->ckpt_every == 1 && steps > r->ab_cap) {
+        // the whole trajectory's coupling sums, 8 B per node-replica-step, when they fit
+        // with a tenth of the device (at least 2 GiB) left over; otherwise the backward
+        // pass recomputes them step by step
+        drop_graphs(r);
+        dev_free(r->d_ab);
+        r->ab_cap = steps;
+        const size_t bytes = (size_t)steps * r->p->nodes * r->R_pad * sizeof(float2);
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess &&
+            bytes + std::max<size_t>(total_b / 10, (size_t)2 << 30) <= free_b) {
+            if (cudaMalloc(&r->d_ab, bytes) != cudaSuccess) r->d_ab = nullptr;
+        }
+        cudaGetLastError();
     }
     const int64_t ro_need = n_ro + 1;   // one extra row for the final scores
     if (ro_need > r->readouts_cap || !r->d_trace) {
@@ -730,6 +747,25 @@ int enqueue_stream_form(oim_run_s* r) {
         cudaError_t e = init_parts(*r, s);
         if (r->ckpt_every <= 0) {
             if (e == cudaSuccess) e = enqueue_steps(*r, 0, r->steps, nullptr, s);
+        } else if (r->d_ab) {
+            // the whole trajectory: each step reads its phases from slot t and writes slot
+            // t + 1 of the checkpoints, and keeps its coupling sums
+            const size_t st = (size_t)r->p->nodes * r->R_pad;
+            float* ck = r->d_ckpt;
+            float2* cs0 = reinterpret_cast<float2*>(r->d_cs[0]);
+            float2* cs1 = reinterpret_cast<float2*>(r->d_cs[1]);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(ck, r->d_theta[0], state_bytes, cudaMemcpyDeviceToDevice, s);
+            const int64_t re = r->readout_every;
+            for (int64_t t = 0; t < r->steps && e == cudaSuccess; ++t) {
+                e = launch_step_stream_buffers(*r, t, ck + (size_t)t * st, (t & 1) ? cs1 : cs0,
+                                               ck + (size_t)(t + 1) * st, (t & 1) ? cs0 : cs1,
+                                               r->d_ab + (size_t)t * st, s);
+                if (e == cudaSuccess && re > 0 && (t + 1) % re == 0)
+                    e = launch_score(*r, ck + (size_t)(t + 1) * st, (t + 1) / re - 1, s);
+            }
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(r->d_theta[0], ck + (size_t)r->steps * st, state_bytes,
+                                    cudaMemcpyDeviceToDevice, s);
         } else {
             // checkpoints (the FP32 stream form): the phases after every ckpt_every steps
             if (e == cudaSuccess)
@@ -1269,6 +1305,9 @@ int oim_backward(oim_run_t r, double* dK, double* dKs, double* dKn, double* loss
     const int64_t T = r->steps, C = r->ckpt_every;
     const size_t state = (size_t)r->p->nodes * r->R_pad;
     const int64_t seg_len = std::min<int64_t>(C, std::max<int64_t>(T, 1));
+    // the whole trajectory kept by the forward pass (phases and coupling sums of every
+    // step): one segment over all steps, nothing recomputed
+    const bool whole = C == 1 && r->d_ab != nullptr;
     // per segment: the phases theta_t0 .. theta_t1 and the coupling sums (A, B) of its
     // steps, recomputed from the checkpoint; lambda ping-pong; two ping-pong pairs of
     // planes lambda_{t+1} (c, s)_t
@@ -1288,8 +1327,10 @@ int oim_backward(oim_run_t r, double* dK, double* dKs, double* dKn, double* loss
             return cuda_fail(e, what);         \
         }                                      \
     } while (0)
-    OIM_BW(cudaMalloc(&seg, (size_t)(seg_len + 1) * state * sizeof(float)), "cudaMalloc(segment)");
-    OIM_BW(cudaMalloc(&ab, (size_t)seg_len * state * sizeof(float2)), "cudaMalloc(coupling sums)");
+    if (!whole) {
+        OIM_BW(cudaMalloc(&seg, (size_t)(seg_len + 1) * state * sizeof(float)), "cudaMalloc(segment)");
+        OIM_BW(cudaMalloc(&ab, (size_t)seg_len * state * sizeof(float2)), "cudaMalloc(coupling sums)");
+    }
     OIM_BW(cudaMalloc(&lam[0], state * sizeof(float)), "cudaMalloc(lambda)");
     OIM_BW(cudaMalloc(&lam[1], state * sizeof(float)), "cudaMalloc(lambda)");
     OIM_BW(cudaMalloc(&cs[0], state * sizeof(float2)), "cudaMalloc(cs)");
@@ -1309,7 +1350,19 @@ int oim_backward(oim_run_t r, double* dK, double* dKs, double* dKn, double* loss
     OIM_BW(launch_adj_planes(*r, r->d_theta[r->final_buf], nullptr, Y[0], s), "adjoint planes");
     OIM_BW(launch_adj_terminal(*r, Y[0], lam[0], gL, s), "adjoint terminal");
     int cur = 0, cy = 0;
-    const int64_t n_seg = (T + C - 1) / C;
+    const int64_t n_seg = whole ? 0 : (T + C - 1) / C;
+    if (whole && T > 0) {
+        const float* ck = r->d_ckpt;
+        OIM_BW(launch_adj_planes(*r, ck + (size_t)(T - 1) * state, lam[cur], Y[cy], s), "adjoint planes");
+        for (int64_t t = T - 1; t >= 0; --t) {
+            const float* th = ck + (size_t)t * state;
+            OIM_BW(launch_adj_step(*r, t, th, t > 0 ? th - state : nullptr, r->d_ab + (size_t)t * state, Y[cy],
+                                   Y[cy ^ 1], lam[cur], lam[cur ^ 1], gK, gS, gN, s),
+                   "adjoint step");
+            cur ^= 1;
+            cy ^= 1;
+        }
+    }
     for (int64_t sg = n_seg - 1; sg >= 0; --sg) {
         const int64_t t0 = sg * C, t1 = std::min<int64_t>(t0 + C, T);
         // recompute theta_t0 .. theta_t1 from the checkpoint with the forward kernel,

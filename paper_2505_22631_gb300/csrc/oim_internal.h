@@ -201,6 +201,10 @@ struct oim_run_s {
     int32_t ckpt_every = 0;
     int64_t ckpt_cap = 0;
     float* d_ckpt = nullptr;
+    // ckpt_every 1, when it fits in device memory: the coupling sums (A, B) of every
+    // step as well ([steps][nodes][R_pad]), so the backward pass recomputes nothing
+    float2* d_ab = nullptr;
+    int64_t ab_cap = 0;                       // steps the buffer was sized (or tried) for
     bool ran = false;
 };
 

@@ -36,7 +36,7 @@ def gpu_grads(graphs, q, K, Ks, Kn, dt, T, R, seed, C):
 
 
 @pytest.mark.parametrize("q", [2, 3])
-@pytest.mark.parametrize("C", [16, 1000])
+@pytest.mark.parametrize("C", [1, 16, 1000])
 def test_adjoint_matches_oracle(orc, q, C):
     g0 = erdos_renyi(40, 0.15, 3, "pm1")
     g1 = planted_partition(30, 3, 3.0, 4) if q == 3 else torus(5, 6, 5, "pm1")
@@ -88,3 +88,41 @@ def test_backward_requires_checkpoints():
     with pytest.raises(OimError) as ei:
         capi.oim_backward(run.handle, np.zeros((1, 10)), None, None, None)
     assert ei.value.code == capi.OIM_ESTATE
+
+
+def test_whole_trajectory_mode_equals_recomputation():
+    # checkpoint_every = 1 keeps every step's phases and coupling sums, so the backward
+    # pass recomputes nothing: the same FP32 arithmetic as the recomputing pass (only the
+    # order of the FP64 gradient sums differs), and a forward pass whose phases, scores
+    # and trace are those of a run without checkpoints
+    from paper_2505_22631_gb300 import Problem, capi
+    graphs = [erdos_renyi(300, 0.05, 11, "pm1"), torus(12, 10, 12, "pm1")]
+    prob = Problem.batch([Problem.from_graph(g, 2) for g in graphs])
+    T, R, dt, seed = 120, 12, 0.01, 5
+    rng = np.random.default_rng(7)
+    K = (0.1 + 0.1 * rng.random((2, T))).astype(np.float32)
+    Ks = np.stack([linear_ramp(T, 0, 1.5)] * 2)
+    Kn = (0.05 + 0.05 * rng.random((2, T))).astype(np.float32)
+    out = {}
+    for C in (0, 1, 16):
+        o = capi.oim_default_opts()
+        o.form = capi.OIM_FORM_STREAM
+        o.precision = capi.OIM_PREC_FP32
+        o.checkpoint_every = C
+        o.readout_every = 20
+        r = capi.oim_run(prob.handle, K, Ks, Kn, dt, T, R, seed, o)
+        th = np.zeros(prob.nodes * R, np.float32)
+        capi.oim_get_phases(r, th)
+        score, trace = np.zeros((2, R)), np.zeros((2, T // 20, R))
+        capi.oim_readout(r, None, score, None, trace, None)
+        grads = [np.zeros((2, T)) for _ in range(3)] + [np.zeros(2)]
+        if C:
+            capi.oim_backward(r, *grads)
+        capi.oim_destroy_run(r)
+        out[C] = (th, score, trace, grads)
+    for C in (1, 16):
+        assert np.array_equal(out[C][0], out[0][0])
+        assert np.array_equal(out[C][1], out[0][1])
+        assert np.array_equal(out[C][2], out[0][2])
+    for a, b in zip(out[1][3], out[16][3]):
+        assert np.allclose(a, b, rtol=1e-9, atol=1e-12 * max(1.0, np.abs(b).max()))
