@@ -71,6 +71,8 @@ struct ResidentArgs {
     double* agree;          // [G][row_stride][R_pad]
     int64_t row_stride;
     int64_t readout_every;
+    int64_t T;              // steps to run (P.steps is the schedules' row stride, which a
+                            // re-run with fewer steps leaves larger)
     int32_t integer_weights;   // scores accumulate exactly in 32-bit integers
 };
 
@@ -173,7 +175,7 @@ __global__ void __launch_bounds__(1024, 1) resident_kernel(ResidentArgs a) {
     const float sdt = P.sqrt_dt;
     const size_t sbase = (size_t)g * P.steps;
     int64_t next_readout = a.readout_every > 0 ? a.readout_every : -1;
-    for (int64_t t = 0; t < P.steps; ++t) {
+    for (int64_t t = 0; t < a.T; ++t) {
         const float K = __ldg(P.K + sbase + t), Ks = __ldg(P.Ks + sbase + t);
         const float Kn = __ldg(P.Kn + sbase + t);
         const float dtK = P.dt * K, dtKs = P.dt * Ks, kick = Kn * sdt;
@@ -427,7 +429,7 @@ __global__ void __launch_bounds__(1024, 1) resident_quad_kernel(ResidentArgs a) 
     const float sdt = P.sqrt_dt;
     const size_t sbase = (size_t)g * P.steps;
     int64_t next_readout = a.readout_every > 0 ? a.readout_every : -1;
-    for (int64_t t = 0; t < P.steps; ++t) {
+    for (int64_t t = 0; t < a.T; ++t) {
         const float K = __ldg(P.K + sbase + t), Ks = __ldg(P.Ks + sbase + t);
         const float Kn = __ldg(P.Kn + sbase + t);
         const float dtK = P.dt * K, dtKs = P.dt * Ks, kick = Kn * sdt;
@@ -733,6 +735,7 @@ cudaError_t launch_resident_impl(const oim_run_s& r, const int4* d_items, cudaSt
     a.agree = r.d_trace;
     a.row_stride = r.readouts_cap;
     a.readout_every = r.readout_every;
+    a.T = r.steps;
     a.integer_weights = r.p->integer_weights ? 1 : 0;
     const ResidentPlan& pl = r.plan;
     const int blocks = (int)pl.items.size();

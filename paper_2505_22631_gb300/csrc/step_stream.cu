@@ -386,6 +386,12 @@ __global__ void __launch_bounds__(256, 5) step_octet_kernel(CSRDev csr, StepPara
                                                             H2* __restrict__ cs_out, int64_t t_fixed,
                                                             const int32_t* __restrict__ d_t0,
                                                             int32_t t_add, int octs_fast) {
+    // launched as a programmatic dependent of the previous kernel in the stream: the
+    // next step may be scheduled as soon as every block of this one has started, and
+    // every block waits here for the previous grid's completion (and its memory)
+    // before it reads anything a kernel writes (a no-op under a plain launch)
+    asm volatile("griddepcontrol.launch_dependents;");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const int octs = P.R_pad >> 3;
     const int nblk = octs_fast ? blockIdx.y : blockIdx.x;
     const int oblk = octs_fast ? blockIdx.x : blockIdx.y;
@@ -623,16 +629,29 @@ static cudaError_t step_plain(const oim_run_s& r, int64_t t, const int32_t* d_t0
 }
 
 // The 16-bit form's step t: thread = node x octet of replicas (R_pad a multiple of 8).
+// (launched with programmatic stream serialization: consecutive steps overlap the next
+// launch with the tail of the previous one; in a captured graph the edge is programmatic)
 template <typename H2, int kQ>
-static void step_octet_q(const oim_run_s& r, const CSRDev& csr, const StepParams& P, const StepGrid& q,
-                         float* theta, const H2* cs_in, H2* cs_out, int64_t t, const int32_t* d_t0,
-                         cudaStream_t s) {
+static cudaError_t step_octet_q(const oim_run_s& r, const CSRDev& csr, const StepParams& P, const StepGrid& q,
+                                float* theta, const H2* cs_in, H2* cs_out, int64_t t, const int32_t* d_t0,
+                                cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = q.grid;
+    cfg.blockDim = q.block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const int32_t t_add = (int32_t)t;
+    const int octs_fast = q.quads_fast;
     if (r.p->unit_weights)
-        step_octet_kernel<H2, true, kQ><<<q.grid, q.block, 0, s>>>(csr, P, theta, cs_in, cs_out, t, d_t0,
-                                                                  (int32_t)t, q.quads_fast);
-    else
-        step_octet_kernel<H2, false, kQ><<<q.grid, q.block, 0, s>>>(csr, P, theta, cs_in, cs_out, t, d_t0,
-                                                                   (int32_t)t, q.quads_fast);
+        return cudaLaunchKernelEx(&cfg, step_octet_kernel<H2, true, kQ>, csr, P, theta, cs_in, cs_out, t, d_t0,
+                                  t_add, octs_fast);
+    return cudaLaunchKernelEx(&cfg, step_octet_kernel<H2, false, kQ>, csr, P, theta, cs_in, cs_out, t, d_t0,
+                              t_add, octs_fast);
 }
 
 template <typename H2>
@@ -645,13 +664,9 @@ static cudaError_t step_octet(const oim_run_s& r, int64_t t, const int32_t* d_t0
     float* theta = r.d_theta[in];
     const H2* cs_in = reinterpret_cast<const H2*>(r.d_cs[in]);
     H2* cs_out = reinterpret_cast<H2*>(r.d_cs[in ^ 1]);
-    if (P.q == 2)
-        step_octet_q<H2, 2>(r, csr, P, q, theta, cs_in, cs_out, t, d_t0, s);
-    else if (P.q == 3)
-        step_octet_q<H2, 3>(r, csr, P, q, theta, cs_in, cs_out, t, d_t0, s);
-    else
-        step_octet_q<H2, 0>(r, csr, P, q, theta, cs_in, cs_out, t, d_t0, s);
-    return cudaGetLastError();
+    if (P.q == 2) return step_octet_q<H2, 2>(r, csr, P, q, theta, cs_in, cs_out, t, d_t0, s);
+    if (P.q == 3) return step_octet_q<H2, 3>(r, csr, P, q, theta, cs_in, cs_out, t, d_t0, s);
+    return step_octet_q<H2, 0>(r, csr, P, q, theta, cs_in, cs_out, t, d_t0, s);
 }
 
 // Steps [t0, t1) of the 16-bit stream form in one cooperative launch of as many blocks

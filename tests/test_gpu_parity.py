@@ -431,3 +431,27 @@ def test_stream_launch_shapes_agree_bitwise():
     b = gpu_run(*args, 16, 7, form="stream", precision="fp16", readout_every=10)
     assert np.array_equal(a.phases()[0][:16], b.phases()[0])
     assert np.array_equal(a.readout()["trace"][:, :, :16], b.readout()["trace"])
+
+
+@pytest.mark.parametrize("form,precision,R", [("resident", "fp32", 8), ("resident", "fp16", 8),
+                                              ("stream", "fp32", 8), ("stream", "fp16", 8),
+                                              ("gemm", "bf16", 64)])
+def test_rerun_with_fewer_steps_runs_only_those(orc, c1, form, precision, R):
+    # a run's schedule buffer keeps the stride of its longest run, so a shorter re-run must
+    # take its step count from the call, not from that stride: it equals a fresh run of the
+    # same steps (trace included), and a re-run of zero steps gives the initial phases
+    from paper_2505_22631_gb300 import Problem, Run
+    g = c1.graphs[0]
+    prob = Problem.from_graph(g, 2)
+    kw = dict(form=form, precision=precision, readout_every=10)
+    T0, T1 = 40, 20
+    run = Run(prob, c1.K[0][:T0], c1.Ks[0][:T0], c1.Kn[0][:T0], c1.dt, T0, R, 5, **kw)
+    run.rerun(c1.K[0][:T1], c1.Ks[0][:T1], c1.Kn[0][:T1], c1.dt, T1, 9)
+    short = run.phases()[0]
+    trace = run.readout()["trace"]
+    fresh = Run(prob, c1.K[0][:T1], c1.Ks[0][:T1], c1.Kn[0][:T1], c1.dt, T1, R, 9, **kw)
+    assert np.array_equal(short, fresh.phases()[0])
+    assert np.array_equal(trace, fresh.readout()["trace"])
+    z = np.zeros(0, np.float32)
+    run.rerun(z, z, z, c1.dt, 0, 77)
+    assert np.array_equal(run.phases()[0], orc.init_phases(g.n, R, 77).astype(np.float32))
