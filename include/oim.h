@@ -50,6 +50,9 @@ extern "C" {
 #define OIM_ETIMEOUT     -4   /* a device-side wait gave up (error word set)     */
 #define OIM_EUNSUPPORTED -5   /* valid request this build or GPU cannot serve   */
 #define OIM_ESTATE       -6   /* handle in the wrong state for this call         */
+#define OIM_EINDEX       -7   /* checked builds (-DOIM_CHECKS): a kernel met a    */
+                              /* column index outside its row's graph and       */
+                              /* skipped it (reported by oim_run_sync)          */
 
 /* ---- integration forms ---------------------------------------------------- */
 #define OIM_FORM_AUTO      0  /* chosen per graph by the autotuner               */
@@ -218,6 +221,23 @@ int oim_run_info(oim_run_t r, int64_t* steps, int32_t* replicas, int64_t* n_read
  * [0,1), to host or device memory.  Synchronises.  Errors: OIM_ESTATE, OIM_ECUDA.
  */
 int oim_get_phases(oim_run_t r, float* theta);
+
+/*
+ * oim_debug_set_column -- overwrite the column index of CSR entry `entry` in the
+ * problem's device arrays (the host copy and the derived arrays keep the old
+ * value), for testing the index checks of a checked build: with a column outside
+ * the row's graph, the step, adjoint and readout kernels of a build made with
+ * -DOIM_CHECKS skip the entry and oim_run_sync returns OIM_EINDEX; other builds
+ * read the named node (in bounds: 0 <= column < nodes) as if it were a neighbour.
+ *   entry   0 <= entry < nnz, not among the first four entries of its row (the
+ *           stream form's slot descriptors also hold those)
+ *   column  global node index, 0 <= column < nodes
+ *   previous  host int32 (may be NULL): the entry's column before the call (rows
+ *           are stored with their +1 entries first, so entry k of a row is not
+ *           necessarily the caller's k-th column)
+ * Synchronous.  Errors: OIM_EINVAL, OIM_ECUDA.
+ */
+int oim_debug_set_column(oim_problem_t p, int64_t entry, int32_t column, int32_t* previous);
 
 /*
  * oim_debug_derivative -- the drift of Eq. 5 for given phases of one graph,

@@ -15,6 +15,9 @@ import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "liboim.so")
+# the same library built with -DOIM_CHECKS (build(checks=True)): kernels test every
+# column index against its row's graph and report OIM_EINDEX instead of reading it
+CHECKS_LIB_PATH = os.path.join(_PKG, "liboim_checks.so")
 
 OIM_OK = 0
 OIM_EINVAL = -1
@@ -23,6 +26,7 @@ OIM_ECUDA = -3
 OIM_ETIMEOUT = -4
 OIM_EUNSUPPORTED = -5
 OIM_ESTATE = -6
+OIM_EINDEX = -7
 
 OIM_FORM_AUTO = 0
 OIM_FORM_STREAM = 1
@@ -89,6 +93,7 @@ SIGNATURES = {
     "oim_run_info": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
     "oim_get_phases": (ctypes.c_int, [_vp, _vp]),
     "oim_debug_derivative": (ctypes.c_int, [_vp, _vp, _i32, _f32, _f32, _vp]),
+    "oim_debug_set_column": (ctypes.c_int, [_vp, _i64, _i32, _vp]),
     "oim_backward": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "oim_autotune": (ctypes.c_int, [_vp, _i32, _i32, _i64, _vp, ctypes.POINTER(oim_run_opts),
                                     ctypes.POINTER(ctypes.c_double)]),
@@ -236,6 +241,13 @@ def oim_get_phases(r, theta):
 def oim_debug_derivative(p, theta, replicas, K, Ks, f_out):
     _check(load().oim_debug_derivative(p, ptr(theta, np.float32), int(replicas), float(K),
                                        float(Ks), ptr(f_out, np.float32)))
+
+
+def oim_debug_set_column(p, entry, column) -> int:
+    """Overwrite a device column index (index-check tests); returns the previous one."""
+    prev = ctypes.c_int32(0)
+    _check(load().oim_debug_set_column(p, int(entry), int(column), ctypes.byref(prev)))
+    return int(prev.value)
 
 
 def oim_backward(r, dK=None, dKs=None, dKn=None, loss=None):

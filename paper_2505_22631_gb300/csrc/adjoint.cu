@@ -21,6 +21,7 @@
 // loads per neighbour that a warp turns into whole 512-byte rows).  Each adjoint step
 // also writes the planes the next one (step t - 1) gathers, lambda_t (c, s)_{t-1}, from
 // its own lambda_t and theta_{t-1}.
+#include "oim_checks.cuh"
 #include "oim_device.cuh"
 #include "oim_internal.h"
 
@@ -70,7 +71,7 @@ __global__ void __launch_bounds__(256) adj_terminal_kernel(CSRDev csr, int R, in
         float A[4] = {0, 0, 0, 0}, B[4] = {0, 0, 0, 0};
         for (int ei = csr.rowp[node]; ei < csr.rowp[node + 1]; ++ei) {
             const uint32_t cw = csr.col[ei];
-            const uint32_t j = csr.w ? cw : (cw & ~kSignBit);
+            const uint32_t j = checked_node_of_row(csr, node, csr.w ? cw : (cw & ~kSignBit));
             const float w = csr.w ? csr.w[ei] : ((cw & kSignBit) ? -1.0f : 1.0f);
             const size_t jat = (size_t)j * R_pad + 4 * quad;
             const float4 c4 = *reinterpret_cast<const float4*>(Yc + jat);
@@ -132,7 +133,7 @@ __global__ void __launch_bounds__(256, 4) adj_step_kernel(CSRDev csr, StepParams
         float Pp[4] = {0, 0, 0, 0}, Q[4] = {0, 0, 0, 0};
         for (int ei = row.y; ei < row.w; ++ei) {
             const uint32_t cw = csr.col[ei];
-            const uint32_t j = csr.w ? cw : (cw & ~kSignBit);
+            const uint32_t j = checked_node_of_row(csr, node, csr.w ? cw : (cw & ~kSignBit));
             const float w = csr.w ? csr.w[ei] : ((cw & kSignBit) ? -1.0f : 1.0f);
             const size_t jat = (size_t)j * P.R_pad + 4 * quad;
             const float4 lc4 = *reinterpret_cast<const float4*>(Ylc + jat);

@@ -19,6 +19,7 @@
 #include <cmath>
 #include <string>
 
+#include "oim_checks.cuh"
 #include "oim_device.cuh"
 #include "oim_internal.h"
 #include "tc_common.cuh"
@@ -290,7 +291,7 @@ __global__ void gemm_scatter_kernel(CSRDev csr, int g, int n_pad, __nv_bfloat16*
     const int node = gd.node_off + i;
     for (int e = csr.rowp[node]; e < csr.rowp[node + 1]; ++e) {
         const uint32_t cw = csr.col[e];
-        const int j = (int)(csr.w ? cw : (cw & ~kSignBit)) - gd.node_off;
+        const int j = (int)checked_node(csr, g, csr.w ? cw : (cw & ~kSignBit), (uint32_t)node) - gd.node_off;
         const float w = csr.w ? csr.w[e] : ((cw & kSignBit) ? -1.0f : 1.0f);
         W[(size_t)i * n_pad + j] = __float2bfloat16_rn(w);
     }

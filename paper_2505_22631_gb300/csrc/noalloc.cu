@@ -6,6 +6,7 @@
 #include <mutex>
 #include <string>
 
+#include "oim_checks.cuh"
 #include "oim_device.cuh"
 #include "oim_internal.h"
 
@@ -63,7 +64,7 @@ __global__ void __launch_bounds__(256) noalloc_agree_kernel(CSRDev csr, const fl
         float f0 = 0.f, f1 = 0.f, f2 = 0.f, f3 = 0.f;
         for (int e = csr.rowp[node]; e < csr.rowp[node + 1]; ++e) {
             const uint32_t cw = csr.col[e];
-            const uint32_t j = csr.w ? cw : (cw & ~kSignBit);
+            const uint32_t j = checked_node_of_row(csr, node, csr.w ? cw : (cw & ~kSignBit));
             if ((int)j <= node) continue;
             const float w = csr.w ? csr.w[e] : ((cw & kSignBit) ? -1.0f : 1.0f);
             const float4 tj = *reinterpret_cast<const float4*>(theta + (size_t)j * ld + 4 * quad);

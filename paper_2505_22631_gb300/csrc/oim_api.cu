@@ -250,6 +250,8 @@ int upload_problem(oim_problem_s* p) {
                  "upload upper col");
     if (!uw.empty())
         OIM_CUDA(cudaMemcpy(p->d_uw, uw.data(), uw.size() * 4, cudaMemcpyHostToDevice), "upload upper w");
+    OIM_CUDA(dev_alloc(&p->d_check, 1), "cudaMalloc(check word)");
+    OIM_CUDA(cudaMemset(p->d_check, 0, sizeof(int32_t)), "clear check word");
     p->uploaded = true;
     return OIM_OK;
 }
@@ -278,6 +280,7 @@ void free_problem(oim_problem_s* p) {
     dev_free(p->d_urowp);
     dev_free(p->d_ucol);
     dev_free(p->d_uw);
+    dev_free(p->d_check);
 }
 
 // Pack columns: global node index, and for +-1 weights the sign in bit 31.
@@ -876,6 +879,23 @@ int set_device_of(const oim_problem_s* p, DeviceScope& scope) {
     return OIM_OK;
 }
 
+// Checked builds: OIM_EINDEX (and the word cleared) when a kernel recorded a column
+// index outside its row's graph since the last check; other builds never record one.
+int take_check_word(oim_problem_s* p) {
+#ifdef OIM_CHECKS
+    if (!p || !p->d_check) return OIM_OK;
+    int32_t w = 0;
+    OIM_CUDA(cudaMemcpy(&w, p->d_check, sizeof(w), cudaMemcpyDeviceToHost), "read check word");
+    if (w != 0) {
+        OIM_CUDA(cudaMemset(p->d_check, 0, sizeof(w)), "clear check word");
+        return fail(OIM_EINDEX, "a column index outside its row's graph was skipped (checked build)");
+    }
+#else
+    (void)p;
+#endif
+    return OIM_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1157,7 +1177,7 @@ int oim_run_sync(oim_run_t r) {
     int32_t err = 0;
     OIM_CUDA(cudaMemcpy(&err, r->d_err, sizeof(err), cudaMemcpyDeviceToHost), "read error word");
     if (err != 0) return fail(OIM_ETIMEOUT, "a device-side wait gave up (error word " + std::to_string(err) + ")");
-    return OIM_OK;
+    return take_check_word(r->p);
 }
 
 int oim_run_info(oim_run_t r, int64_t* steps, int32_t* replicas, int64_t* n_readouts, int32_t* form,
@@ -1290,6 +1310,33 @@ int oim_debug_derivative(oim_problem_t p, const float* theta, int32_t replicas, 
     return OIM_OK;
 }
 
+int oim_debug_set_column(oim_problem_t p, int64_t entry, int32_t column, int32_t* previous) {
+    g_last_error.clear();
+    if (!p) return fail(OIM_EINVAL, "NULL problem");
+    if (entry < 0 || entry >= p->nnz) return fail(OIM_EINVAL, "entry out of range");
+    if (column < 0 || column >= p->nodes) return fail(OIM_EINVAL, "column out of range");
+    {
+        // the first four entries of a row are also held by the slot descriptors
+        const auto it = std::upper_bound(p->h_rowp.begin(), p->h_rowp.end(), (int32_t)entry);
+        const int64_t row_start = *(it - 1);
+        if (entry - row_start < 4) return fail(OIM_EINVAL, "entry among the first four of its row");
+    }
+    DeviceScope scope;
+    int rc = set_device_of(p, scope);
+    if (rc == OIM_OK) rc = ensure_uploaded(p);
+    if (rc != OIM_OK) return rc;
+    const uint32_t packed = (uint32_t)column | (p->h_col[(size_t)entry] & kSignBit);
+    const int32_t plain = column;
+    if (previous) {
+        uint32_t old = 0;
+        OIM_CUDA(cudaMemcpy(&old, p->d_col + entry, sizeof(old), cudaMemcpyDeviceToHost), "read column");
+        *previous = (int32_t)(old & ~kSignBit);
+    }
+    OIM_CUDA(cudaMemcpy(p->d_col + entry, &packed, sizeof(packed), cudaMemcpyHostToDevice), "write column");
+    OIM_CUDA(cudaMemcpy(p->d_pcol + entry, &plain, sizeof(plain), cudaMemcpyHostToDevice), "write column");
+    return OIM_OK;
+}
+
 int oim_backward(oim_run_t r, double* dK, double* dKs, double* dKn, double* loss) {
     NvtxRange range("oim_backward");
     g_last_error.clear();
@@ -1388,6 +1435,11 @@ int oim_backward(oim_run_t r, double* dK, double* dKs, double* dKn, double* loss
         }
     }
     OIM_BW(cudaStreamSynchronize(s), "backward");
+    rc = take_check_word(r->p);
+    if (rc != OIM_OK) {
+        cleanup();
+        return rc;
+    }
     const size_t gcount = (size_t)G * T;
     if (dK && T > 0) OIM_BW(cudaMemcpy(dK, gK, gcount * sizeof(double), cudaMemcpyDefault), "write dK");
     if (dKs && T > 0) OIM_BW(cudaMemcpy(dKs, gS, gcount * sizeof(double), cudaMemcpyDefault), "write dKs");

@@ -97,6 +97,9 @@ struct CSRDev {
     // [nnz] column indices without the sign bit (the 16-bit stream form knows a +-1
     // entry's sign from its position against the row's first -1 entry)
     const int32_t* pcol;
+    // checked builds (OIM_CHECKS): the word in which the kernels record a column index
+    // outside its row's graph (oim_checks.cuh); unused otherwise
+    int32_t* check;
 };
 
 }  // namespace oim
@@ -132,11 +135,13 @@ struct oim_problem_s {
     int4* d_arow = nullptr;        // adjoint row descriptors, graph by graph
     uint32_t* d_sdesc = nullptr;   // 32-byte slot descriptors of the 16-bit stream form
     int32_t* d_pcol = nullptr;     // column indices without sign bits
+    int32_t* d_check = nullptr;    // checked builds: index-check word (0: no failure)
     int32_t max_n = 0;             // largest graph
     oim::CSRDev csr() const {
         return oim::CSRDev{d_rowp, d_col, unit_weights ? nullptr : d_w, d_node_graph, d_split,
                            d_order, d_graphs, G, (int32_t)nodes, d_urowp, d_ucol,
-                           unit_weights ? nullptr : d_uw, d_srow, d_shead, d_arow, d_sdesc, d_pcol};
+                           unit_weights ? nullptr : d_uw, d_srow, d_shead, d_arow, d_sdesc, d_pcol,
+                           d_check};
     }
 };
 

@@ -9,6 +9,7 @@
 // whatever the order of the additions.
 #include <algorithm>
 
+#include "oim_checks.cuh"
 #include "oim_device.cuh"
 #include "oim_internal.h"
 
@@ -80,7 +81,9 @@ __global__ void __launch_bounds__(kScoreQuads * kScoreLanes) score_kernel(
             f2 += (si.z == sj.z) ? w : 0.f;
             f3 += (si.w == sj.w) ? w : 0.f;
         };
-        auto row_of = [&](uint32_t cw) { return sp[(size_t)(csr.uw ? cw : (cw & ~kSignBit)) * quads]; };
+        auto row_of = [&](uint32_t cw) {
+            return sp[(size_t)checked_node_of_row(csr, node, csr.uw ? cw : (cw & ~kSignBit)) * quads];
+        };
         const int e_end = csr.urowp[node + 1];
         int e = csr.urowp[node];
         for (; e + 4 <= e_end; e += 4) {
@@ -146,7 +149,7 @@ __global__ void __launch_bounds__(256) energy_kernel(CSRDev csr, const float* __
         const int e_end = csr.rowp[node + 1];
         for (int e = csr.rowp[node]; e < e_end; ++e) {
             const uint32_t cw = csr.col[e];
-            const uint32_t j = csr.w ? cw : (cw & ~kSignBit);
+            const uint32_t j = checked_node(csr, g, csr.w ? cw : (cw & ~kSignBit), (uint32_t)node);
             if ((int)j <= node) continue;
             const float w = csr.w ? csr.w[e] : ((cw & kSignBit) ? -1.0f : 1.0f);
             const float4 tj = *reinterpret_cast<const float4*>(theta + (size_t)j * R_pad + 4 * quad);

@@ -25,6 +25,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include "oim_checks.cuh"
 #include "oim_device.cuh"
 #include "oim_internal.h"
 
@@ -200,6 +201,7 @@ __global__ void __launch_bounds__(1024, 1) resident_kernel(ResidentArgs a) {
                     jj = (int)cw - noff;
                     w = __ldg(a.csr.w + e);
                 }
+                jj = checked_local(a.csr, n, jj, i);
                 const UT nb = cache[jj * units + u];
                 const float2 ww = make_float2(w, w);
 #pragma unroll
@@ -249,7 +251,7 @@ __global__ void __launch_bounds__(1024, 1) resident_kernel(ResidentArgs a) {
                 const int e_end = a.csr.rowp[node + 1];
                 for (int e = a.csr.rowp[node]; e < e_end; ++e) {
                     const uint32_t cw = a.csr.col[e];
-                    const int jn = kUnit ? (int)(cw & ~kSignBit) : (int)cw;
+                    const int jn = noff + checked_local(a.csr, n, (kUnit ? (int)(cw & ~kSignBit) : (int)cw) - noff, i);
                     if (jn <= node) continue;
                     const float w = kUnit ? ((cw & kSignBit) ? -1.0f : 1.0f) : a.csr.w[e];
 #pragma unroll
@@ -414,7 +416,9 @@ __global__ void __launch_bounds__(1024, 1) resident_quad_kernel(ResidentArgs a) 
         const int nnz_g = a.csr.rowp[noff + n] - e0;
         for (int e = threadIdx.x; e < nnz_g; e += blockDim.x) {
             const uint32_t cw = a.csr.col[e0 + e];
-            s_col[e] = (uint16_t)(((cw & ~kSignBit) - (uint32_t)noff) | ((cw & kSignBit) ? kLocalSign : 0u));
+            // (checked builds: a column outside the graph becomes its first node)
+            const uint32_t jl = (uint32_t)checked_local(a.csr, n, (int)((cw & ~kSignBit) - (uint32_t)noff), 0);
+            s_col[e] = (uint16_t)(jl | ((cw & kSignBit) ? kLocalSign : 0u));
         }
     }
     for (int i = i_begin; i < n; i += NS) {
@@ -481,6 +485,7 @@ __global__ void __launch_bounds__(1024, 1) resident_quad_kernel(ResidentArgs a) 
                         jj = (int)cw - noff;
                         w = __ldg(a.csr.w + e);
                     }
+                    jj = checked_local(a.csr, n, jj, i);
                     float2 nb[4];
                     Quad::unpack(cache[jj * units + u], nb);
                     const float2 ww = make_float2(w, w);
@@ -544,7 +549,7 @@ __global__ void __launch_bounds__(1024, 1) resident_quad_kernel(ResidentArgs a) 
                         w = (c & kLocalSign) ? -1.0f : 1.0f;
                     } else {
                         const uint32_t cw = a.csr.col[e0 + e];
-                        jl = (int)(kUnit ? (cw & ~kSignBit) : cw) - noff;
+                        jl = checked_local(a.csr, n, (int)(kUnit ? (cw & ~kSignBit) : cw) - noff, i);
                         w = kUnit ? ((cw & kSignBit) ? -1.0f : 1.0f) : a.csr.w[e0 + e];
                     }
                     if (jl <= i) continue;

@@ -26,6 +26,7 @@
 #include <algorithm>
 #include <type_traits>
 
+#include "oim_checks.cuh"
 #include "oim_device.cuh"
 #include "oim_internal.h"
 
@@ -147,7 +148,9 @@ __global__ void __launch_bounds__(256) step_stream_kernel(CSRDev csr, StepParams
         float2 hv[kH][4];
 #pragma unroll
         for (int u = 0; u < kH; ++u)
-            C::load4(cs_in + (size_t)(kUnit ? (hc[u] & ~kSignBit) : hc[u]) * P.R_pad + 4 * quad, hv[u]);
+            C::load4(cs_in + (size_t)checked_node_of_row(csr, node, kUnit ? (hc[u] & ~kSignBit) : hc[u]) * P.R_pad +
+                         4 * quad,
+                     hv[u]);
 #pragma unroll
         for (int u = 0; u < kH; ++u) {
             if (e_beg + u < e_end) {
@@ -169,6 +172,7 @@ __global__ void __launch_bounds__(256) step_stream_kernel(CSRDev csr, StepParams
             j = cw;
             w = __ldg(csr.w + e);
         }
+        j = checked_node_of_row(csr, node, j);
         float2 nb[4];
         C::load4(cs_in + (size_t)j * P.R_pad + 4 * quad, nb);
         const float2 ww = make_float2(w, w);
@@ -282,6 +286,8 @@ __device__ __forceinline__ void octet_step(const CSRDev& csr, const StepParams& 
     uint32_t d[8];
     ld256_nc(csr.sdesc + (size_t)slot * 8, d);
     const int node = (int)d[0], e_beg = (int)d[1], e_split = (int)d[2], e_end = (int)d[3];
+    // (checked builds: every column a node of the row's graph d[4])
+    auto col = [&](uint32_t j) { return checked_node(csr, (int)d[4], j, (uint32_t)node); };
     const char* cs_base = reinterpret_cast<const char*>(cs_in) + (size_t)oct * 32;
     // bytes per node row (R_pad <= 2^20: 32 bits), so that a neighbour's address is one
     // 32 x 32 -> 64-bit multiply-add
@@ -292,8 +298,8 @@ __device__ __forceinline__ void octet_step(const CSRDev& csr, const StepParams& 
     float sgn = 1.0f;
     if constexpr (kUnit) {
         uint32_t h0[8], h1[8];
-        ld_pairs(cs_base + (size_t)d[6] * stride, h0);
-        ld_pairs(cs_base + (size_t)d[7] * stride, h1);
+        ld_pairs(cs_base + (size_t)col(d[6]) * stride, h0);
+        ld_pairs(cs_base + (size_t)col(d[7]) * stride, h1);
         if (e_beg < e_end) {
             if (e_beg == e_split) rsub8<H2>(acc, h0);
             else add8<H2>(acc, h0);
@@ -306,26 +312,26 @@ __device__ __forceinline__ void octet_step(const CSRDev& csr, const StepParams& 
         const uint32_t* cp = reinterpret_cast<const uint32_t*>(csr.pcol) + e;
         for (; e < e_split; ++e, ++cp) {
             uint32_t v[8];
-            ld_pairs(cs_base + (size_t)__ldg(cp) * stride, v);
+            ld_pairs(cs_base + (size_t)col(__ldg(cp)) * stride, v);
             add8<H2>(acc, v);
         }
         if (e == e_split && e < e_end) {
             uint32_t v[8];
-            ld_pairs(cs_base + (size_t)__ldg(cp) * stride, v);
+            ld_pairs(cs_base + (size_t)col(__ldg(cp)) * stride, v);
             rsub8<H2>(acc, v);
             ++e;
             ++cp;
         }
         for (; e < e_end; ++e, ++cp) {
             uint32_t v[8];
-            ld_pairs(cs_base + (size_t)__ldg(cp) * stride, v);
+            ld_pairs(cs_base + (size_t)col(__ldg(cp)) * stride, v);
             add8<H2>(acc, v);
         }
         if (e_split < e_end) sgn = -1.0f;   // the accumulators hold -(A, B)
     } else {
         for (int e = e_beg; e < e_end; ++e) {
             uint32_t v[8];
-            ld_pairs(cs_base + (size_t)(uint32_t)__ldg(csr.pcol + e) * stride, v);
+            ld_pairs(cs_base + (size_t)col((uint32_t)__ldg(csr.pcol + e)) * stride, v);
             const float w = __ldg(csr.w + e);
             const float2 ww = make_float2(w, w);
 #pragma unroll
@@ -482,7 +488,7 @@ __global__ void derivative_kernel(CSRDev csr, int q, int R, const float* __restr
     float2 acc = make_float2(0.f, 0.f);
     for (int e = csr.rowp[i]; e < csr.rowp[i + 1]; ++e) {
         const uint32_t cw = csr.col[e];
-        const uint32_t j = csr.w ? cw : (cw & ~kSignBit);
+        const uint32_t j = checked_local(csr, n, (int)(csr.w ? cw : (cw & ~kSignBit)), i);
         const float w = csr.w ? csr.w[e] : ((cw & kSignBit) ? -1.0f : 1.0f);
         float sj, cj;
         sincospif(2.0f * theta[(int64_t)r * n + j], &sj, &cj);
