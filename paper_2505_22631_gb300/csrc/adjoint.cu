@@ -11,7 +11,9 @@
 //   S_j = sum_k w_jk cos 2 pi (theta_j - theta_k) = c_j A_j + s_j B_j
 //   C_j = sum_k w_jk lambda_{t+1,k} cos 2 pi (theta_k - theta_j) = c_j P_j + s_j Q_j
 // where (A, B, P, Q)_j = sum_k w_jk (c_k, s_k, lambda_k c_k, lambda_k s_k), all at theta_t.
-// Schedule gradients, summed over nodes and replicas of each graph in FP64:
+// Schedule gradients, summed over nodes and replicas of each graph (the terms of a warp,
+// at most 128, in FP32 -- a relative error of ~1e-5 of their absolute sum, far inside the
+// adjoint's FP32 tolerance -- and the warps' sums in FP64):
 //   dL/dK_t = dt sum lambda_{t+1} D(theta_t),  dL/dKs_t = -dt sum lambda_{t+1} sin 2 pi q theta_t,
 //   dL/dKn_t = sqrt(dt) sum lambda_{t+1} xi_t  (pathwise: the same Philox draws as the forward).
 // Layout as the stream form: [node][R_pad], replicas contiguous, a thread per (node, quad).
@@ -122,7 +124,8 @@ __global__ void __launch_bounds__(256, 4) adj_step_kernel(CSRDev csr, StepParams
     const int quad = qblk * blockDim.x + threadIdx.x;
     const bool valid = slot < csr.nodes && quad < quads;   // no early exit: the warp shuffles below
     int g = -1;
-    double gK = 0.0, gS = 0.0, gN = 0.0;
+    // gradient terms: a warp's (at most 128) in FP32, the warps' sums in FP64 atomics
+    float gK = 0.f, gS = 0.f, gN = 0.f;
     if (valid) {
         const int4 row = __ldg(csr.arow + slot);   // {node, row start, first -1 entry, row end}
         const int node = row.x;
@@ -177,9 +180,9 @@ __global__ void __launch_bounds__(256, 4) adj_step_kernel(CSRDev csr, StepParams
             lam_out[at + v] = lt[v];
             if (4 * quad + v < P.R) {
                 const float D = s * A[v] - c * B[v];
-                gK += (double)(l * D);
-                gS += (double)(l * sq);
-                gN += (double)(l * z[v]);
+                gK = fmaf(l, D, gK);
+                gS = fmaf(l, sq, gS);
+                gN = fmaf(l, z[v], gN);
             }
         }
         if (theta_prev) {
@@ -206,9 +209,9 @@ __global__ void __launch_bounds__(256, 4) adj_step_kernel(CSRDev csr, StepParams
     } else if (g < 0) {
         return;
     }
-    atomicAdd(dK + (size_t)g * T + t, (double)P.dt * gK);
-    atomicAdd(dKs + (size_t)g * T + t, -(double)P.dt * gS);
-    atomicAdd(dKn + (size_t)g * T + t, (double)P.sqrt_dt * gN);
+    atomicAdd(dK + (size_t)g * T + t, (double)P.dt * (double)gK);
+    atomicAdd(dKs + (size_t)g * T + t, -(double)P.dt * (double)gS);
+    atomicAdd(dKn + (size_t)g * T + t, (double)P.sqrt_dt * (double)gN);
 }
 
 }  // namespace
