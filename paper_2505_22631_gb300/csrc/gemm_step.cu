@@ -64,8 +64,10 @@ struct GemmArgs {
 // Tile shapes: 128 columns (10 warps, 3 stages, 97 KB of shared memory, 256 TMEM
 // columns: two blocks per SM), 112 columns (the same, with a short second part: more
 // tiles, so that the tiles spread over more SMs when 128-wide ones leave SMs with a
-// single tile) and 256 columns (18 warps, 4 stages, 193 KB, all 512 TMEM columns: one
-// block per SM, half the X^T re-reads from L2).
+// single tile), 256 columns (18 warps, 4 stages, 193 KB, all 512 TMEM columns: one
+// block per SM, half the X^T re-reads from L2) and 224 columns (the same block with a
+// short last part, 177 KB: nine tile columns of a 2000-node graph fill 144 SMs where
+// 256-wide ones fill 128).
 template <int BN>
 struct TileShape {
     static constexpr int kParts = (BN + 63) / 64;                // 64-column parts (the last may be short)
@@ -439,14 +441,14 @@ __global__ void __launch_bounds__(128, 1)
 
 // 128-wide tiles with three stages use 97 KB of shared memory and 256 TMEM columns,
 // so two blocks share an SM (and its 512 TMEM columns).
-// Tile width of the dense form.  threads_per_block 576 asks for 256-wide tiles; 320
-// for 112- or 128-wide ones; 0 takes 256-wide tiles for graphs of 3000 nodes or more
-// (measured: 4-5 % faster at n = 4000, slower at n <= 2000 with 4096 replicas; the
-// autotuner times both).  Between 112 and 128 the one whose busiest SM (two blocks
-// per SM) carries the fewest tile columns wins, 128 on a tie (fewer X^T re-reads).
+// Tile width of the dense form.  threads_per_block 576 asks for one block per SM with
+// 224- or 256-wide tiles; 320 for two blocks per SM with 112- or 128-wide ones; 0 takes
+// the wide tiles for graphs of 3000 nodes or more (measured: 4-5 % faster at n = 4000;
+// at n = 2000, 224-wide tiles 19.9 against 20.4 us/step with 1024 replicas and equal
+// with 4096; the autotuner times both block sizes).  Within each pair the width whose
+// busiest SM carries the fewest tile columns wins, the wider on a tie (fewer X^T
+// re-reads).
 int gemm_bn_for(const oim_run_s& r, int n) {
-    if (r.opts.threads_per_block == TileShape<256>::kThreads) return 256;
-    if (r.opts.threads_per_block == 0 && n >= 3000) return 256;
     static int sms = 0;
     if (sms == 0) {
         int dev = 0, v = 0;
@@ -456,11 +458,14 @@ int gemm_bn_for(const oim_run_s& r, int n) {
                   : 152;
     }
     const int64_t mt = (2 * (int64_t)r.R_pad) / kBM;
-    auto cost = [&](int bn) {
+    // tile columns on the busiest SM with `per_sm` blocks an SM
+    auto cost = [&](int bn, int per_sm) {
         const int64_t tiles = (int64_t)((n + bn - 1) / bn) * mt;
-        return ((tiles + sms - 1) / sms) * bn;
+        return ((tiles + (int64_t)sms * per_sm - 1) / ((int64_t)sms * per_sm)) * per_sm * bn;
     };
-    return cost(112) < cost(128) ? 112 : 128;
+    if (r.opts.threads_per_block == TileShape<256>::kThreads || (r.opts.threads_per_block == 0 && n >= 3000))
+        return cost(224, 1) < cost(256, 1) ? 224 : 256;
+    return cost(112, 2) < cost(128, 2) ? 112 : 128;
 }
 
 constexpr size_t kScoreSmem = 4 * (size_t)(kABytes + 128 * 128) + 1024;
@@ -518,6 +523,9 @@ int gemm_setup(oim_run_s& r, int graph) {
         e = cudaFuncSetAttribute(gemm_step_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)TileShape<256>::kSmemBytes);
     if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(gemm_step_kernel<224>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)TileShape<224>::kSmemBytes);
+    if (e == cudaSuccess)
         e = cudaFuncSetAttribute(gemm_score_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScoreSmem);
     if (e != cudaSuccess) return cuda_fail(e, "dense form shared memory");
     return OIM_OK;
@@ -568,6 +576,9 @@ cudaError_t launch_gemm_step_at(const oim_run_s& r, int k, int64_t t, const int3
     const dim3 grid(st.tiles_n, (2 * r.R_pad) / kBM);
     if (st.bn == 256)
         gemm_step_kernel<256><<<grid, TileShape<256>::kThreads, TileShape<256>::kSmemBytes, s>>>(
+            st.map_x[t & 1], st.map_w, a);
+    else if (st.bn == 224)
+        gemm_step_kernel<224><<<grid, TileShape<224>::kThreads, TileShape<224>::kSmemBytes, s>>>(
             st.map_x[t & 1], st.map_w, a);
     else if (st.bn == 112)
         gemm_step_kernel<112><<<grid, TileShape<112>::kThreads, TileShape<112>::kSmemBytes, s>>>(
