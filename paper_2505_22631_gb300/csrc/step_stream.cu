@@ -274,11 +274,12 @@ __device__ __forceinline__ uint32_t f2_to_h2(float2 f) {
 // through L2 only (ld.global.cg), for the persistent kernel, whose pairs were written
 // by other blocks during the same launch; the per-step kernel reads them through the
 // read-only path.
-template <typename H2, bool kUnit, int kQ, bool kCoherent>
+template <typename H2, bool kUnit, int kQ, bool kCoherent, bool kPre = false>
 __device__ __forceinline__ void octet_step(const CSRDev& csr, const StepParams& P, float* theta,
                                            const H2* __restrict__ cs_in, H2* __restrict__ cs_out,
                                            int slot, int oct, int64_t t_fixed,
-                                           const int32_t* __restrict__ d_t0, int32_t t_add) {
+                                           const int32_t* __restrict__ d_t0, int32_t t_add,
+                                           uint4 xa_pre = uint4{}, uint4 xb_pre = uint4{}) {
     auto ld_pairs = [](const char* p, uint32_t (&r)[8]) {
         if constexpr (kCoherent) ld256_cg(p, r);
         else ld256_nc(p, r);
@@ -347,9 +348,11 @@ __device__ __forceinline__ void octet_step(const CSRDev& csr, const StepParams& 
     uint32_t thw[8];
     if constexpr (kCoherent) ld256_cg(theta + at, thw);   // ordered against the previous step's store
     else ld256(theta + at, thw);
-    const uint64_t seed = P.seed_dev ? *P.seed_dev : P.seed;
-    uint4 xa, xb;
-    draw_block_pair(seed, (uint32_t)g, kStreamNoise, (uint32_t)i, (uint32_t)t, (uint32_t)(2 * oct), xa, xb);
+    uint4 xa = xa_pre, xb = xb_pre;   // kPre: drawn by the caller
+    if constexpr (!kPre) {
+        const uint64_t seed = P.seed_dev ? *P.seed_dev : P.seed;
+        draw_block_pair(seed, (uint32_t)g, kStreamNoise, (uint32_t)i, (uint32_t)t, (uint32_t)(2 * oct), xa, xb);
+    }
     float z[8];   // the negated normals
     {
         const float2 z0 = box_muller_half_turn_fast(xa.x, xa.y), z1 = box_muller_half_turn_fast(xa.z, xa.w);
@@ -394,17 +397,31 @@ __global__ void __launch_bounds__(256, 5) step_octet_kernel(CSRDev csr, StepPara
                                                             int32_t t_add, int octs_fast) {
     // launched as a programmatic dependent of the previous kernel in the stream: the
     // next step may be scheduled as soon as every block of this one has started, and
-    // every block waits here for the previous grid's completion (and its memory)
-    // before it reads anything a kernel writes (a no-op under a plain launch)
+    // every block waits (griddepcontrol.wait) for the previous grid's completion (and
+    // its memory) before it reads anything a kernel writes (a no-op under a plain launch)
     asm volatile("griddepcontrol.launch_dependents;");
-    asm volatile("griddepcontrol.wait;" ::: "memory");
     const int octs = P.R_pad >> 3;
     const int nblk = octs_fast ? blockIdx.y : blockIdx.x;
     const int oblk = octs_fast ? blockIdx.x : blockIdx.y;
     const int slot = nblk * blockDim.y + threadIdx.y;
     const int oct = oblk * blockDim.x + threadIdx.x;
     if (slot >= csr.nodes || oct >= octs) return;
-    octet_step<H2, kUnit, kQ, false>(csr, P, theta, cs_in, cs_out, slot, oct, t_fixed, d_t0, t_add);
+    if (d_t0 == nullptr) {
+        // the step is known: the noise depends on no kernel's output (the descriptors,
+        // the seed and the schedules are written before the run), so it is drawn while
+        // the previous step may still be running
+        const uint32_t* dsc = csr.sdesc + (size_t)slot * 8;
+        const uint64_t seed = P.seed_dev ? *P.seed_dev : P.seed;
+        uint4 xa, xb;
+        draw_block_pair(seed, __ldg(dsc + 4), kStreamNoise, __ldg(dsc + 5), (uint32_t)t_fixed, (uint32_t)(2 * oct),
+                        xa, xb);
+        asm volatile("griddepcontrol.wait;" ::: "memory");
+        octet_step<H2, kUnit, kQ, false, true>(csr, P, theta, cs_in, cs_out, slot, oct, t_fixed, d_t0, t_add, xa,
+                                               xb);
+    } else {
+        asm volatile("griddepcontrol.wait;" ::: "memory");
+        octet_step<H2, kUnit, kQ, false>(csr, P, theta, cs_in, cs_out, slot, oct, t_fixed, d_t0, t_add);
+    }
 }
 
 // Nanoseconds of the GPU's global timer.
