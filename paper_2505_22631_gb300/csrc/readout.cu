@@ -8,6 +8,7 @@
 // weights every partial sum is an integer below 2^53, so the result is exact
 // whatever the order of the additions.
 #include <algorithm>
+#include <type_traits>
 
 #include "oim_checks.cuh"
 #include "oim_device.cuh"
@@ -39,6 +40,10 @@ __global__ void __launch_bounds__(256) spin_kernel(const float* __restrict__ the
 // that straddles graphs flushes per thread at each graph change.
 constexpr int kScoreQuads = 32, kScoreLanes = 8;
 
+// kF32: the thread's running sums in FP32 (launched for +-1 weights when npt x the
+// largest row length stays below 2^24, so every partial sum is an integer exact in FP32;
+// FP64 arithmetic is slow on this part), else in FP64.
+template <bool kF32>
 __global__ void __launch_bounds__(kScoreQuads * kScoreLanes) score_kernel(
     CSRDev csr, const int8_t* __restrict__ spins, int R_pad, double* __restrict__ agree, int64_t row_stride,
     int64_t k_fixed, int npt, const int32_t* __restrict__ d_t0, int32_t t_add, int32_t every, int node_lo,
@@ -53,16 +58,17 @@ __global__ void __launch_bounds__(kScoreQuads * kScoreLanes) score_kernel(
     const int chunk1 = min(chunk0 + kScoreLanes * npt, node_hi);
     const bool one_graph = csr.node_graph[chunk0] == csr.node_graph[chunk1 - 1];
     const char4* sp = reinterpret_cast<const char4*>(spins) + (valid ? quad : 0);
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    using Acc = typename std::conditional<kF32, float, double>::type;
+    Acc acc[4] = {0, 0, 0, 0};
     int g_cur = -1;
     auto flush = [&]() {
         if (g_cur < 0) return;
         double* dst = agree + ((int64_t)g_cur * row_stride + k) * R_pad + 4 * quad;
 #pragma unroll
         for (int c = 0; c < 4; ++c)
-            if (acc[c] != 0.0) atomicAdd(dst + c, acc[c]);
+            if (acc[c] != 0) atomicAdd(dst + c, (double)acc[c]);
 #pragma unroll
-        for (int c = 0; c < 4; ++c) acc[c] = 0.0;
+        for (int c = 0; c < 4; ++c) acc[c] = 0;
     };
     for (int node = chunk0 + threadIdx.y; valid && node < chunk1; node += kScoreLanes) {
         const int g = csr.node_graph[node];
@@ -105,7 +111,7 @@ __global__ void __launch_bounds__(kScoreQuads * kScoreLanes) score_kernel(
         return;   // uniform across the block: every thread took this branch
     }
 #pragma unroll
-    for (int c = 0; c < 4; ++c) red[threadIdx.y][threadIdx.x][c] = acc[c];
+    for (int c = 0; c < 4; ++c) red[threadIdx.y][threadIdx.x][c] = (double)acc[c];
     __syncthreads();
     if (threadIdx.y == 0 && valid) {
         const int g = csr.node_graph[chunk0];
@@ -233,6 +239,9 @@ cudaError_t launch_score_at(const oim_run_s& r, const float* theta, int64_t k, c
     const int npt = nodes_per_thread(r);
     const int chunk = kScoreLanes * npt;
     dim3 block(kScoreQuads, kScoreLanes);
+    int max_deg = 0;
+    for (const GraphDev& gd : r.p->graphs) max_deg = std::max(max_deg, gd.max_deg);
+    const bool f32_sums = r.p->unit_weights && (int64_t)npt * max_deg < (int64_t)1 << 24;
     // the node ranges whose graphs are not scored on the tensor cores (all nodes by default)
     const int2 all = make_int2(0, (int)r.p->nodes);
     const int2* rg = r.score_split ? r.score_ranges.data() : &all;
@@ -240,9 +249,9 @@ cudaError_t launch_score_at(const oim_run_s& r, const float* theta, int64_t k, c
     for (size_t q = 0; q < nr; ++q) {
         if (rg[q].y <= rg[q].x) continue;
         dim3 grid((quads + kScoreQuads - 1) / kScoreQuads, (unsigned)((rg[q].y - rg[q].x + chunk - 1) / chunk));
-        score_kernel<<<grid, block, 0, s>>>(r.p->csr(), r.d_spins, r.R_pad, r.d_trace, r.readouts_cap, k, npt,
-                                            d_t0, t_add, (int32_t)std::max<int64_t>(1, r.readout_every), rg[q].x,
-                                            rg[q].y);
+        const auto fn = f32_sums ? score_kernel<true> : score_kernel<false>;
+        fn<<<grid, block, 0, s>>>(r.p->csr(), r.d_spins, r.R_pad, r.d_trace, r.readouts_cap, k, npt, d_t0, t_add,
+                                  (int32_t)std::max<int64_t>(1, r.readout_every), rg[q].x, rg[q].y);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
