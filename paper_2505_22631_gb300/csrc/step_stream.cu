@@ -274,6 +274,13 @@ __device__ __forceinline__ uint32_t f2_to_h2(float2 f) {
 // through L2 only (ld.global.cg), for the persistent kernel, whose pairs were written
 // by other blocks during the same launch; the per-step kernel reads them through the
 // read-only path.
+// A 32-byte load through L2 only (not kept in L1).
+__device__ __forceinline__ void ld256_l2(const void* p, uint32_t (&r)[8]) {
+    asm("ld.global.cg.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+        : "l"(p));
+}
+
 template <typename H2, bool kUnit, int kQ, bool kCoherent, bool kPre = false>
 __device__ __forceinline__ void octet_step(const CSRDev& csr, const StepParams& P, float* theta,
                                            const H2* __restrict__ cs_in, H2* __restrict__ cs_out,
@@ -345,9 +352,13 @@ __device__ __forceinline__ void octet_step(const CSRDev& csr, const StepParams& 
     const size_t sidx = (size_t)g * P.steps + t;
     const float K = __ldg(P.K + sidx), Ks = __ldg(P.Ks + sidx), Kn = __ldg(P.Kn + sidx);
     const size_t at = (size_t)node * P.R_pad + 8 * oct;
+    // own phases through L2 (they are read once): another block's store of the previous
+    // step to the same 128-byte line (fewer than 32 replicas a node) can then never be
+    // met in a stale L1 copy, also when this step's blocks start while the previous
+    // step still runs (programmatic dependent launch)
     uint32_t thw[8];
     if constexpr (kCoherent) ld256_cg(theta + at, thw);   // ordered against the previous step's store
-    else ld256(theta + at, thw);
+    else ld256_l2(theta + at, thw);
     uint4 xa = xa_pre, xb = xb_pre;   // kPre: drawn by the caller
     if constexpr (!kPre) {
         const uint64_t seed = P.seed_dev ? *P.seed_dev : P.seed;
@@ -389,6 +400,16 @@ __device__ __forceinline__ void octet_step(const CSRDev& csr, const StepParams& 
     st256(cs_out + at, cso);
 }
 
+// After griddepcontrol.wait: the state pointers pass through a volatile move, so that
+// no load through them (the 256-bit loads are plain asm, which the compiler may move
+// across other asm) can be scheduled before the wait.
+template <typename T>
+__device__ __forceinline__ T* after_wait(T* p) {
+    uint64_t v = reinterpret_cast<uint64_t>(p);
+    asm volatile("mov.b64 %0, %0;" : "+l"(v));
+    return reinterpret_cast<T*>(v);
+}
+
 template <typename H2, bool kUnit, int kQ>
 __global__ void __launch_bounds__(256, 5) step_octet_kernel(CSRDev csr, StepParams P, float* theta,
                                                             const H2* __restrict__ cs_in,
@@ -416,11 +437,12 @@ __global__ void __launch_bounds__(256, 5) step_octet_kernel(CSRDev csr, StepPara
         draw_block_pair(seed, __ldg(dsc + 4), kStreamNoise, __ldg(dsc + 5), (uint32_t)t_fixed, (uint32_t)(2 * oct),
                         xa, xb);
         asm volatile("griddepcontrol.wait;" ::: "memory");
-        octet_step<H2, kUnit, kQ, false, true>(csr, P, theta, cs_in, cs_out, slot, oct, t_fixed, d_t0, t_add, xa,
-                                               xb);
+        octet_step<H2, kUnit, kQ, false, true>(csr, P, after_wait(theta), after_wait(cs_in), cs_out, slot, oct,
+                                               t_fixed, d_t0, t_add, xa, xb);
     } else {
         asm volatile("griddepcontrol.wait;" ::: "memory");
-        octet_step<H2, kUnit, kQ, false>(csr, P, theta, cs_in, cs_out, slot, oct, t_fixed, d_t0, t_add);
+        octet_step<H2, kUnit, kQ, false>(csr, P, after_wait(theta), after_wait(cs_in), cs_out, slot, oct, t_fixed,
+                                         after_wait(d_t0), t_add);
     }
 }
 
