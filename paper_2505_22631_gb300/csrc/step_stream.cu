@@ -416,11 +416,12 @@ __global__ void __launch_bounds__(256, 5) step_octet_kernel(CSRDev csr, StepPara
                                                             H2* __restrict__ cs_out, int64_t t_fixed,
                                                             const int32_t* __restrict__ d_t0,
                                                             int32_t t_add, int octs_fast) {
-    // launched as a programmatic dependent of the previous kernel in the stream: the
-    // next step may be scheduled as soon as every block of this one has started, and
-    // every block waits (griddepcontrol.wait) for the previous grid's completion (and
-    // its memory) before it reads anything a kernel writes (a no-op under a plain launch)
-    asm volatile("griddepcontrol.launch_dependents;");
+    // launched as a programmatic dependent of the previous kernel in the stream: every
+    // block waits (griddepcontrol.wait) for the previous grid's completion (and its
+    // memory) before it reads anything a kernel writes (a no-op under a plain launch),
+    // and only then lets the next step be scheduled (griddepcontrol.launch_dependents),
+    // so that no step is launched before the step two back has finished reading the
+    // (cos, sin) buffer the next one will read
     const int octs = P.R_pad >> 3;
     const int nblk = octs_fast ? blockIdx.y : blockIdx.x;
     const int oblk = octs_fast ? blockIdx.x : blockIdx.y;
@@ -437,10 +438,12 @@ __global__ void __launch_bounds__(256, 5) step_octet_kernel(CSRDev csr, StepPara
         draw_block_pair(seed, __ldg(dsc + 4), kStreamNoise, __ldg(dsc + 5), (uint32_t)t_fixed, (uint32_t)(2 * oct),
                         xa, xb);
         asm volatile("griddepcontrol.wait;" ::: "memory");
+        asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
         octet_step<H2, kUnit, kQ, false, true>(csr, P, after_wait(theta), after_wait(cs_in), cs_out, slot, oct,
                                                t_fixed, d_t0, t_add, xa, xb);
     } else {
         asm volatile("griddepcontrol.wait;" ::: "memory");
+        asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
         octet_step<H2, kUnit, kQ, false>(csr, P, after_wait(theta), after_wait(cs_in), cs_out, slot, oct, t_fixed,
                                          after_wait(d_t0), t_add);
     }
