@@ -45,6 +45,7 @@ struct StepParams {
 struct ResidentPlan {
     int unit = 4;                  // replicas per thread item: 4 (quad kernel), 2 or 1
     bool csr_smem = false;         // graph structure staged in shared memory
+    bool double_buffer = false;    // quad kernel: two (cos, sin) caches, one barrier a step
     int threads = 0;
     size_t smem = 0;
     std::vector<int> k_of_graph;   // replicas per block, per graph

@@ -74,6 +74,7 @@ struct ResidentArgs {
     int64_t readout_every;
     int64_t T;              // steps to run (P.steps is the schedules' row stride, which a
                             // re-run with fewer steps leaves larger)
+    int32_t double_buffer;  // quad kernel: ping-pong (cos, sin) caches in shared memory
     int32_t integer_weights;   // scores accumulate exactly in 32-bit integers
 };
 
@@ -399,8 +400,13 @@ __global__ void __launch_bounds__(1024, 1) resident_quad_kernel(ResidentArgs a) 
     const int R_pad = P.R_pad;
     float* theta = a.theta + r0 + 4 * u;
 
-    T* cache = reinterpret_cast<T*>(smem_raw);                  // [n][units]
-    int32_t* s_rowp = reinterpret_cast<int32_t*>(smem_raw + align16((size_t)n * units * sizeof(T)));
+    // [n][units] (cos, sin) cache; with double buffering a second one follows, the
+    // steps read one and write the other, and one barrier a step separates them
+    const bool db = a.double_buffer != 0;
+    const size_t cache_bytes = align16((size_t)n * units * sizeof(T));
+    T* cache = reinterpret_cast<T*>(smem_raw);
+    T* cache_next = db ? reinterpret_cast<T*>(smem_raw + cache_bytes) : cache;
+    int32_t* s_rowp = reinterpret_cast<int32_t*>(smem_raw + (db ? 2 : 1) * cache_bytes);
     int32_t* s_split = reinterpret_cast<int32_t*>(reinterpret_cast<unsigned char*>(s_rowp) +
                                                   align16((size_t)(n + 1) * 4));
     uint16_t* s_order = reinterpret_cast<uint16_t*>(reinterpret_cast<unsigned char*>(s_split) +
@@ -433,15 +439,25 @@ __global__ void __launch_bounds__(1024, 1) resident_quad_kernel(ResidentArgs a) 
     const float sdt = P.sqrt_dt;
     const size_t sbase = (size_t)g * P.steps;
     int64_t next_readout = a.readout_every > 0 ? a.readout_every : -1;
+    // with double buffering and at most one node a thread, the thread keeps its node's
+    // phases in registers and stores them only where a readout or the end reads them
+    const bool own1 = db && n <= NS;
+    float4 th_keep = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (own1 && i_begin < n) {
+        const int i0 = kSmemCSR ? (int)s_order[i_begin] : a.csr.order[noff + i_begin];
+        th_keep = *reinterpret_cast<const float4*>(theta + (size_t)(noff + i0) * R_pad);
+    }
     for (int64_t t = 0; t < a.T; ++t) {
         const float K = __ldg(P.K + sbase + t), Ks = __ldg(P.Ks + sbase + t);
         const float Kn = __ldg(P.Kn + sbase + t);
         const float dtK = P.dt * K, dtKs = P.dt * Ks, kick = Kn * sdt;
+        const bool store_theta = !own1 || t + 1 == next_readout || t + 1 == a.T;
         // nodes in order of degree, so the lanes of a warp run rows of equal length;
         // the next node's phases are loaded while the current one is processed
         int i_cur = i_begin < n ? (kSmemCSR ? (int)s_order[i_begin] : a.csr.order[noff + i_begin]) : 0;
-        float4 th_cur = i_begin < n ? *reinterpret_cast<const float4*>(theta + (size_t)(noff + i_cur) * R_pad)
-                                    : make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 th_cur = own1 ? th_keep
+                             : (i_begin < n ? *reinterpret_cast<const float4*>(theta + (size_t)(noff + i_cur) * R_pad)
+                                            : make_float4(0.f, 0.f, 0.f, 0.f));
         for (int slot_i = i_begin; slot_i < n; slot_i += NS) {
             const int i = i_cur;
             const float4 th = th_cur;
@@ -505,10 +521,21 @@ __global__ void __launch_bounds__(1024, 1) resident_quad_kernel(ResidentArgs a) 
                 const float d = own[v].y * acc[v].x - own[v].x * acc[v].y;
                 tn[v] = wrap01(t0[v] + (dtK * d - dtKs * sin_q(P.q, own[v].x, own[v].y)) + kick * z[v]);
             }
-            *reinterpret_cast<float4*>(theta + (size_t)node * R_pad) = make_float4(tn[0], tn[1], tn[2], tn[3]);
+            if (store_theta)
+                *reinterpret_cast<float4*>(theta + (size_t)node * R_pad) = make_float4(tn[0], tn[1], tn[2], tn[3]);
+            if (db) {
+                // the next step's cache, written while this one is still read
+                const float2 cs[4] = {M::cs(tn[0]), M::cs(tn[1]), M::cs(tn[2]), M::cs(tn[3])};
+                cache_next[i * units + u] = Quad::pack(cs);
+            }
+            if (own1) th_keep = make_float4(tn[0], tn[1], tn[2], tn[3]);
         }
         __syncthreads();
-        {
+        if (db) {
+            T* tmp = cache;
+            cache = cache_next;
+            cache_next = tmp;
+        } else {
             float4 th_n = i_begin < n ? *reinterpret_cast<const float4*>(theta + (size_t)(noff + i_begin) * R_pad)
                                       : make_float4(0.f, 0.f, 0.f, 0.f);
             for (int i = i_begin; i < n; i += NS) {
@@ -517,8 +544,8 @@ __global__ void __launch_bounds__(1024, 1) resident_quad_kernel(ResidentArgs a) 
                 const float2 cs[4] = {M::cs(th.x), M::cs(th.y), M::cs(th.z), M::cs(th.w)};
                 cache[i * units + u] = Quad::pack(cs);
             }
+            __syncthreads();
         }
-        __syncthreads();
 
         if (t + 1 == next_readout) {
             const int64_t k = next_readout / a.readout_every - 1;
@@ -725,6 +752,19 @@ cudaError_t plan_resident(const oim_problem_s& p, int32_t R_pad, int32_t prec, i
     }
     plan->threads = threads;
     plan->smem = smem;
+    // the quad kernel's second (cos, sin) cache, where it fits beside everything else
+    plan->double_buffer = false;
+    if (unit == 4) {
+        size_t smem_db = 0;
+        for (int g = 0; g < G; ++g) {
+            const int k = std::min(kg[g], R_pad);
+            smem_db = std::max(smem_db, 2 * align16(cb * (size_t)p.graphs[g].n * k) + (use_csr ? csr_bytes[g] : 0));
+        }
+        if (smem_db <= kSmemBudget) {
+            plan->double_buffer = true;
+            plan->smem = smem_db;
+        }
+    }
     return cudaSuccess;
 }
 
@@ -741,6 +781,7 @@ cudaError_t launch_resident_impl(const oim_run_s& r, const int4* d_items, cudaSt
     a.row_stride = r.readouts_cap;
     a.readout_every = r.readout_every;
     a.T = r.steps;
+    a.double_buffer = r.plan.double_buffer ? 1 : 0;
     a.integer_weights = r.p->integer_weights ? 1 : 0;
     const ResidentPlan& pl = r.plan;
     const int blocks = (int)pl.items.size();
