@@ -26,6 +26,8 @@ int cuda_fail(cudaError_t e, const char* what) {
 
 // implemented in the kernel translation units
 cudaError_t launch_score(const oim_run_s& r, const float* theta, int64_t k, cudaStream_t s);
+cudaError_t launch_spins(const oim_run_s& r, const float* theta, cudaStream_t s);
+cudaError_t launch_score_pass(const oim_run_s& r, int64_t k, const int32_t* d_t0, int32_t t_add, cudaStream_t s);
 cudaError_t launch_score_at(const oim_run_s& r, const float* theta, int64_t k, const int32_t* d_t0,
                             int32_t t_add, cudaStream_t s);
 cudaError_t launch_finalize(const oim_run_s& r, int64_t k, double* score, cudaStream_t s);
@@ -324,6 +326,11 @@ void free_run_buffers(oim_run_s* r) {
     if (r->ev_join) cudaEventDestroy(r->ev_join);
     r->aux = nullptr;
     r->ev_fork = r->ev_join = nullptr;
+    if (r->aux_score) cudaStreamDestroy(r->aux_score);
+    if (r->ev_spins) cudaEventDestroy(r->ev_spins);
+    if (r->ev_scored) cudaEventDestroy(r->ev_scored);
+    r->aux_score = nullptr;
+    r->ev_spins = r->ev_scored = nullptr;
     gemm_free(*r);
     if (r->chunk_exec) cudaGraphExecDestroy(r->chunk_exec);
     r->chunk_exec = nullptr;
@@ -547,6 +554,11 @@ int allocate_run(oim_run_s* r) {
             OIM_CUDA(cudaEventCreateWithFlags(&r->ev_join, cudaEventDisableTiming), "create join event");
         }
     }
+    if (r->form == OIM_FORM_STREAM && r->readout_every > 0) {
+        OIM_CUDA(cudaStreamCreateWithFlags(&r->aux_score, cudaStreamNonBlocking), "create score stream");
+        OIM_CUDA(cudaEventCreateWithFlags(&r->ev_spins, cudaEventDisableTiming), "create spins event");
+        OIM_CUDA(cudaEventCreateWithFlags(&r->ev_scored, cudaEventDisableTiming), "create score event");
+    }
     // graphs scored on the tensor cores leave the CSR score pass
     r->score_ranges.clear();
     r->score_split = false;
@@ -672,6 +684,7 @@ int enqueue_persistent(oim_run_s* r) {
 // from q and joined back before the readout.
 cudaError_t enqueue_steps(const oim_run_s& r, int64_t t0, int64_t t1, const int32_t* d_t0, cudaStream_t q) {
     cudaError_t e = cudaSuccess;
+    bool scoring = false;   // a readout's scoring is running on the score stream
     const bool fork = r.aux != nullptr;
     for (int64_t a = t0; a < t1 && e == cudaSuccess;) {
         const int64_t re = r.readout_every;
@@ -690,11 +703,25 @@ cudaError_t enqueue_steps(const oim_run_s& r, int64_t t0, int64_t t1, const int3
         }
         if (e == cudaSuccess && re > 0 && b % re == 0) {
             float* th = readout_theta(r, b - 1);
-            e = common_parts(r, q, true);
-            if (e == cudaSuccess) e = score_parts(r, th, b / re - 1, d_t0, b, q);
+            if (r.aux_score) {
+                // the spins on the run's stream (once the previous readout's scoring has
+                // read its spins), their scoring on the second stream beside the next steps
+                if (scoring) e = cudaStreamWaitEvent(q, r.ev_scored, 0);
+                if (e == cudaSuccess) e = launch_spins(r, th, q);
+                if (e == cudaSuccess) e = cudaEventRecord(r.ev_spins, q);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(r.aux_score, r.ev_spins, 0);
+                if (e == cudaSuccess) e = launch_score_pass(r, b / re - 1, d_t0, (int32_t)b, r.aux_score);
+                if (e == cudaSuccess) e = cudaEventRecord(r.ev_scored, r.aux_score);
+                scoring = true;
+            } else {
+                e = common_parts(r, q, true);
+                if (e == cudaSuccess) e = score_parts(r, th, b / re - 1, d_t0, b, q);
+            }
         }
         a = b;
     }
+    // every scoring forked above is joined back before the steps' caller goes on
+    if (e == cudaSuccess && scoring) e = cudaStreamWaitEvent(q, r.ev_scored, 0);
     return e;
 }
 

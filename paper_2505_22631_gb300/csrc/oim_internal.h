@@ -190,6 +190,10 @@ struct oim_run_s {
     // from the run's stream after each readout and joined before the next one
     cudaStream_t aux = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // stream form: the scoring half of each readout runs on a second stream beside the
+    // next steps (it reads only the spins, which the steps do not touch)
+    cudaStream_t aux_score = nullptr;
+    cudaEvent_t ev_spins = nullptr, ev_scored = nullptr;
     int4* d_items = nullptr;                  // plan.items on the device
     // stream-form CUDA graph of a whole run, reused while its shape is unchanged
     cudaGraphExec_t chunk_exec = nullptr;

@@ -230,11 +230,16 @@ cudaError_t launch_score(const oim_run_s& r, const float* theta, int64_t k, cuda
     return launch_score_at(r, theta, k, nullptr, 0, s);
 }
 
-// With d_t0 the readout slot is (*d_t0 + t_add) / readout_every - 1, read on the device.
-cudaError_t launch_score_at(const oim_run_s& r, const float* theta, int64_t k, const int32_t* d_t0,
-                            int32_t t_add, cudaStream_t s) {
+// The spins of every node-replica into d_spins (the first half of a score pass).
+cudaError_t launch_spins(const oim_run_s& r, const float* theta, cudaStream_t s) {
     const int64_t quads_total = (int64_t)r.p->nodes * (r.R_pad / 4);
     spin_kernel<<<(unsigned)((quads_total + 255) / 256), 256, 0, s>>>(theta, quads_total, r.p->q, r.d_spins);
+    return cudaGetLastError();
+}
+
+// The agreeing weights of every replica from d_spins into readout slot k (the second
+// half); with d_t0 the slot is (*d_t0 + t_add) / readout_every - 1, read on the device.
+cudaError_t launch_score_pass(const oim_run_s& r, int64_t k, const int32_t* d_t0, int32_t t_add, cudaStream_t s) {
     const int quads = r.R_pad / 4;
     const int npt = nodes_per_thread(r);
     const int chunk = kScoreLanes * npt;
@@ -256,6 +261,12 @@ cudaError_t launch_score_at(const oim_run_s& r, const float* theta, int64_t k, c
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+cudaError_t launch_score_at(const oim_run_s& r, const float* theta, int64_t k, const int32_t* d_t0,
+                            int32_t t_add, cudaStream_t s) {
+    cudaError_t e = launch_spins(r, theta, s);
+    return e == cudaSuccess ? launch_score_pass(r, k, d_t0, t_add, s) : e;
 }
 
 cudaError_t launch_finalize(const oim_run_s& r, int64_t k, double* score, cudaStream_t s) {
