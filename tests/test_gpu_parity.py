@@ -455,3 +455,31 @@ def test_rerun_with_fewer_steps_runs_only_those(orc, c1, form, precision, R):
     z = np.zeros(0, np.float32)
     run.rerun(z, z, z, c1.dt, 0, 77)
     assert np.array_equal(run.phases()[0], orc.init_phases(g.n, R, 77).astype(np.float32))
+
+
+def test_overlapped_scoring_matches_inline_scoring(orc):
+    # the stream form scores each readout on a second stream beside the next steps (in
+    # the whole-run graph of a re-run; a first execution's chunks join it at each chunk's
+    # end); the mixed form with every member in the stream form runs the same step
+    # kernels and scores inline, so phases, traces and scores agree bit for bit, for the
+    # first execution and for the captured re-runs
+    g0 = erdos_renyi(2000, 0.01, 21, "+1")
+    g1 = torus(40, 50, 22, "pm1")
+    T, R = 200, 256
+    K = [constant(T, 4.0 / g.mean_degree) for g in (g0, g1)]
+    Ks, Kn = linear_ramp(T, 0, 1.5), constant(T, 0.1)
+    a = gpu_run([g0, g1], 2, K, Ks, Kn, 0.01, T, R, 3, form="stream", precision="fp16", readout_every=25)
+    b = gpu_run([g0, g1], 2, K, Ks, Kn, 0.01, T, R, 3, form="mixed", precision="fp16", readout_every=25,
+                graph_forms=["stream", "stream"])
+    for seed in (None, 4, 5):
+        if seed is not None:
+            a.rerun(K, Ks, Kn, 0.01, T, seed)
+            b.rerun(K, Ks, Kn, 0.01, T, seed)
+        pa, pb = a.phases(), b.phases()
+        oa, ob = a.readout(), b.readout()
+        for gi in range(2):
+            assert np.array_equal(pa[gi], pb[gi])
+        assert np.array_equal(oa["trace"], ob["trace"])
+        assert np.array_equal(oa["score"], ob["score"])
+    for gi, g in enumerate((g0, g1)):
+        assert np.array_equal(oa["score"][gi], orc.scores(g, 2, orc.readout_f32(2, pa[gi])))
