@@ -486,8 +486,16 @@ def main():
     forms_arr = None if graph_forms is None else np.ascontiguousarray(graph_forms, dtype=np.int32)
 
     def e2e_step(seed):
-        hs = [C.oim_create_problem(n, w.q, c.shape[0], rp, c, ww, 2) for n, rp, c, ww in host_graphs]
-        hb = C.oim_create_batch(hs) if len(hs) > 1 else hs[0]
+        # one graph: oim_create_problem; a batch: oim_create_batch_csr (the graphs checked
+        # and laid out on host threads, then joined and uploaded, in one call)
+        if len(host_graphs) > 1:
+            hb = C.oim_create_batch_csr([n for n, _, _, _ in host_graphs], w.q,
+                                        [c.shape[0] for _, _, c, _ in host_graphs],
+                                        [rp for _, rp, _, _ in host_graphs], [c for _, _, c, _ in host_graphs],
+                                        [ww for _, _, _, ww in host_graphs])
+        else:
+            n, rp, c, ww = host_graphs[0]
+            hb = C.oim_create_problem(n, w.q, c.shape[0], rp, c, ww, 0)
         o = C.oim_default_opts()
         o.form = run.opts.form
         o.precision = run.opts.precision
@@ -500,10 +508,7 @@ def main():
         hr = C.oim_run(hb, pin["K"], pin["Ks"], pin["Kn"], w.dt, w.steps, w.replicas, seed, o)
         C.oim_readout(hr, spins_h, score_h, best_h, None, None)
         C.oim_destroy_run(hr)
-        if len(hs) > 1:
-            C.oim_destroy_problem(hb)
-        for h in hs:
-            C.oim_destroy_problem(h)
+        C.oim_destroy_problem(hb)
 
     e2e = None
     if args.e2e_steps > 0:

@@ -155,6 +155,31 @@ int oim_create_problem(int32_t n, int32_t q, int64_t nnz, const int64_t* row_ptr
  */
 int oim_create_batch(int32_t count, const oim_problem_t* problems, oim_problem_t* out);
 
+/*
+ * oim_create_batch_csr -- create a batch of `count` graphs (same q) straight from
+ * their CSR arrays: the same result as oim_create_problem (flags |
+ * OIM_FLAG_DEFER_UPLOAD) for every graph followed by oim_create_batch and the
+ * destruction of the members, with the graphs checked and laid out on up to 16
+ * host threads at once (the batch's problem construction of Sec. III-C, done as
+ * one call).
+ *   count     number of graphs, >= 1
+ *   n, nnz    int32[count], int64[count] (host): nodes and directed entries per graph
+ *   q         number of stable phases, as in oim_create_problem
+ *   row_ptr, col_idx   arrays of `count` pointers (host), each array host or
+ *             device, each as in oim_create_problem
+ *   weights   NULL (every weight +1), or `count` pointers, each NULL (that graph
+ *             all +1) or float[nnz[g]] as in oim_create_problem
+ *   flags     OIM_FLAG_SKIP_SYMMETRY_CHECK applies to every graph;
+ *             OIM_FLAG_DEFER_UPLOAD keeps the batch on the host until its first run
+ *   out       receives the batch handle; nothing of the members outlives the call
+ * Errors: OIM_EINVAL (count < 1, NULL arrays, or any graph failing
+ * oim_create_problem's checks: the message names the lowest-numbered such graph),
+ * OIM_ENOMEM, OIM_ECUDA.
+ */
+int oim_create_batch_csr(int32_t count, const int32_t* n, int32_t q, const int64_t* nnz,
+                         const int64_t* const* row_ptr, const int32_t* const* col_idx,
+                         const float* const* weights, uint32_t flags, oim_problem_t* out);
+
 /* Number of graphs, total nodes and total directed entries of a problem. */
 int oim_problem_info(oim_problem_t p, int32_t* graphs, int64_t* nodes, int64_t* nnz, int32_t* q);
 

@@ -10,14 +10,14 @@ import numpy as np
 
 from . import capi
 from .capi import (FORMS, PRECISIONS, OimError, oim_schedule_triangular, oim_create_batch,
-                   oim_create_problem,
+                   oim_create_batch_csr, oim_create_problem,
                    oim_debug_derivative, oim_default_opts, oim_destroy_problem, oim_destroy_run,
                    oim_get_phases, oim_last_error, oim_problem_info, oim_readout, oim_rerun,
                    oim_run, oim_run_info, oim_run_sync, oim_version)
 
 __all__ = [
     "Problem", "Run", "simulate", "sweep", "oim_schedule_triangular", "OimError", "FORMS", "PRECISIONS", "oim_create_problem",
-    "oim_create_batch", "oim_problem_info", "oim_destroy_problem", "oim_run", "oim_rerun",
+    "oim_create_batch", "oim_create_batch_csr", "oim_problem_info", "oim_destroy_problem", "oim_run", "oim_rerun",
     "oim_run_sync", "oim_readout", "oim_run_info", "oim_get_phases", "oim_debug_derivative",
     "oim_destroy_run", "oim_default_opts", "oim_version", "oim_last_error",
 ]
@@ -46,6 +46,17 @@ class Problem:
     @classmethod
     def from_graph(cls, g, q: int) -> "Problem":
         return cls.from_csr(g.n, q, g.row_ptr, g.col, g.w)
+
+    @classmethod
+    def from_graphs(cls, graphs, q: int, flags=0) -> "Problem":
+        """A batch of graphs (objects with n, row_ptr, col, w) in one call: the graphs are
+        checked and laid out on host threads (oim_create_batch_csr)."""
+        cast = [(np.ascontiguousarray(g.row_ptr, dtype=np.int64), np.ascontiguousarray(g.col, dtype=np.int32),
+                 None if g.w is None else np.ascontiguousarray(g.w, dtype=np.float32)) for g in graphs]
+        h = oim_create_batch_csr([g.n for g in graphs], q, [c.shape[0] for _, c, _ in cast],
+                                 [rp for rp, _, _ in cast], [c for _, c, _ in cast],
+                                 [w for _, _, w in cast], flags)
+        return cls(h, len(graphs), [int(g.n) for g in graphs], q)
 
     @classmethod
     def batch(cls, problems: list["Problem"]) -> "Problem":

@@ -83,6 +83,7 @@ SIGNATURES = {
     "oim_last_error": (_cp, []),
     "oim_create_problem": (ctypes.c_int, [_i32, _i32, _i64, _vp, _vp, _vp, _u32, _pp]),
     "oim_create_batch": (ctypes.c_int, [_i32, _vp, _pp]),
+    "oim_create_batch_csr": (ctypes.c_int, [_i32, _vp, _i32, _vp, _vp, _vp, _vp, _u32, _pp]),
     "oim_problem_info": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "oim_destroy_problem": (None, [_vp]),
     "oim_run": (ctypes.c_int, [_vp, _vp, _vp, _vp, _f32, _i64, _i32, _u64,
@@ -186,6 +187,27 @@ def oim_create_batch(problems):
     h = ctypes.c_void_p()
     _check(load().oim_create_batch(len(problems), ctypes.cast(arr, ctypes.c_void_p),
                                    ctypes.byref(h)))
+    return h.value
+
+
+def oim_create_batch_csr(n, q, nnz, row_ptrs, col_idxs, weights=None, flags=0):
+    """A batch straight from per-graph CSR arrays (numpy or torch, host or device):
+    n, nnz per graph; weights None or a list with None for all-+1 graphs."""
+    count = len(n)
+    if not (len(nnz) == len(row_ptrs) == len(col_idxs) == count):
+        raise ValueError("per-graph lists differ in length")
+    if weights is not None and len(weights) != count:
+        raise ValueError("weights must have one entry per graph")
+    n_arr = np.ascontiguousarray(n, dtype=np.int32)
+    nnz_arr = np.ascontiguousarray(nnz, dtype=np.int64)
+    rp = (ctypes.c_void_p * count)(*[ptr(x, np.int64) for x in row_ptrs])
+    ci = (ctypes.c_void_p * count)(*[ptr(x, np.int32) for x in col_idxs])
+    wp = None if weights is None else (ctypes.c_void_p * count)(*[ptr(x, np.float32) for x in weights])
+    h = ctypes.c_void_p()
+    _check(load().oim_create_batch_csr(count, n_arr.ctypes.data, int(q), nnz_arr.ctypes.data,
+                                       ctypes.cast(rp, ctypes.c_void_p), ctypes.cast(ci, ctypes.c_void_p),
+                                       None if wp is None else ctypes.cast(wp, ctypes.c_void_p), int(flags),
+                                       ctypes.byref(h)))
     return h.value
 
 

@@ -2,10 +2,12 @@
 // validation, device allocation, choice of the integration form and the launch
 // sequence of a run.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "oim_internal.h"
@@ -108,6 +110,43 @@ cudaError_t fetch(std::vector<T>& out, const T* src, size_t count) {
     return cudaMemcpy(out.data(), src, count * sizeof(T), cudaMemcpyDeviceToHost);
 }
 
+// A read-only view of a caller's array: the array itself when it is host memory, else
+// a host copy of it in `store`.
+template <typename T>
+cudaError_t view(const T*& out, std::vector<T>& store, const T* src, size_t count) {
+    out = src;
+    if (count == 0 || !is_device_ptr(src)) return cudaSuccess;
+    const cudaError_t e = fetch(store, src, count);
+    out = store.data();
+    return e;
+}
+
+// fn(k) for every k in [0, count), on up to kHostThreads host threads (the calling
+// thread among them) taking items in order from a shared counter; on the calling thread
+// alone when the work (entries to touch) is small or no thread can be started.  fn must
+// not throw.
+constexpr int kHostThreads = 16;
+constexpr int64_t kParallelWork = 1 << 20;
+
+template <typename F>
+void parallel_for(int64_t count, int64_t work, F&& fn) {
+    const unsigned hw = std::thread::hardware_concurrency();
+    int64_t threads = std::min<int64_t>(count, std::min<int64_t>(kHostThreads, hw ? (int64_t)hw : 1));
+    if (work < kParallelWork) threads = 1;
+    std::atomic<int64_t> next{0};
+    auto worker = [&]() {
+        for (int64_t k = next.fetch_add(1); k < count; k = next.fetch_add(1)) fn(k);
+    };
+    std::vector<std::thread> pool;
+    try {
+        for (int64_t t = 1; t < threads; ++t) pool.emplace_back(worker);
+    } catch (...) {
+        // fewer threads than asked (the items are shared out all the same)
+    }
+    worker();
+    for (auto& th : pool) th.join();
+}
+
 void free_problem(oim_problem_s* p);
 
 // The stream form's slot descriptors for the nodes of the graphs with take[g] set,
@@ -176,7 +215,8 @@ cudaError_t upload_stream_slots(const StreamSlots& sl, int4* srow, uint4* shead,
 int upload_problem(oim_problem_s* p) {
     OIM_CUDA(dev_alloc(&p->d_rowp, p->h_rowp.size()), "cudaMalloc(row_ptr)");
     OIM_CUDA(dev_alloc(&p->d_col, p->h_col.size()), "cudaMalloc(col)");
-    OIM_CUDA(dev_alloc(&p->d_w, p->h_w.size()), "cudaMalloc(w)");
+    // (+-1 weights: the kernels take the sign from the packed columns and never read w)
+    OIM_CUDA(dev_alloc(&p->d_w, p->unit_weights ? 1 : p->h_w.size()), "cudaMalloc(w)");
     OIM_CUDA(dev_alloc(&p->d_node_graph, (size_t)p->nodes), "cudaMalloc(node_graph)");
     OIM_CUDA(dev_alloc(&p->d_split, (size_t)p->nodes), "cudaMalloc(split)");
     OIM_CUDA(dev_alloc(&p->d_order, (size_t)p->nodes), "cudaMalloc(order)");
@@ -217,7 +257,7 @@ int upload_problem(oim_problem_s* p) {
     if (!p->h_col.empty())
         OIM_CUDA(cudaMemcpy(p->d_col, p->h_col.data(), p->h_col.size() * 4, cudaMemcpyHostToDevice),
                  "upload col");
-    if (!p->h_w.empty())
+    if (!p->h_w.empty() && !p->unit_weights)
         OIM_CUDA(cudaMemcpy(p->d_w, p->h_w.data(), p->h_w.size() * 4, cudaMemcpyHostToDevice),
                  "upload w");
     OIM_CUDA(cudaMemcpy(p->d_node_graph, ng.data(), ng.size() * 4, cudaMemcpyHostToDevice),
@@ -229,19 +269,32 @@ int upload_problem(oim_problem_s* p) {
     OIM_CUDA(cudaMemcpy(p->d_graphs, p->graphs.data(), p->graphs.size() * sizeof(GraphDev),
                         cudaMemcpyHostToDevice),
              "upload graphs");
-    // the upper triangle of every row, in row order, for the score passes
+    // the upper triangle of every row, in row order, for the score passes (counted, then
+    // filled, graph by graph on host threads)
     std::vector<int32_t> urowp((size_t)p->nodes + 1, 0);
-    std::vector<uint32_t> ucol;
-    std::vector<float> uw;
-    ucol.reserve(p->h_col.size() / 2 + 1);
-    for (int64_t i = 0; i < p->nodes; ++i) {
-        for (int32_t e = p->h_rowp[i]; e < p->h_rowp[i + 1]; ++e) {
-            if (p->h_col_plain[e] <= i) continue;
-            ucol.push_back(p->h_col[e]);
-            if (!p->unit_weights) uw.push_back(p->h_w[e]);
+    parallel_for(p->G, p->nnz, [&](int64_t g) {
+        const int64_t i0 = p->graphs[(size_t)g].node_off, i1 = i0 + p->graphs[(size_t)g].n;
+        for (int64_t i = i0; i < i1; ++i) {
+            int32_t c = 0;
+            for (int32_t e = p->h_rowp[i]; e < p->h_rowp[i + 1]; ++e) c += p->h_col_plain[e] > i;
+            urowp[(size_t)i + 1] = c;
         }
-        urowp[(size_t)i + 1] = (int32_t)ucol.size();
-    }
+    });
+    for (int64_t i = 0; i < p->nodes; ++i) urowp[(size_t)i + 1] += urowp[(size_t)i];
+    std::vector<uint32_t> ucol((size_t)urowp[(size_t)p->nodes]);
+    std::vector<float> uw(p->unit_weights ? 0 : ucol.size());
+    parallel_for(p->G, p->nnz, [&](int64_t g) {
+        const int64_t i0 = p->graphs[(size_t)g].node_off, i1 = i0 + p->graphs[(size_t)g].n;
+        for (int64_t i = i0; i < i1; ++i) {
+            int32_t at = urowp[(size_t)i];
+            for (int32_t e = p->h_rowp[i]; e < p->h_rowp[i + 1]; ++e) {
+                if (p->h_col_plain[e] <= i) continue;
+                ucol[(size_t)at] = p->h_col[e];
+                if (!p->unit_weights) uw[(size_t)at] = p->h_w[e];
+                ++at;
+            }
+        }
+    });
     OIM_CUDA(dev_alloc(&p->d_urowp, urowp.size()), "cudaMalloc(upper row_ptr)");
     OIM_CUDA(dev_alloc(&p->d_ucol, std::max<size_t>(ucol.size(), 1)), "cudaMalloc(upper col)");
     OIM_CUDA(dev_alloc(&p->d_uw, std::max<size_t>(uw.size(), 1)), "cudaMalloc(upper w)");
@@ -283,16 +336,6 @@ void free_problem(oim_problem_s* p) {
     dev_free(p->d_ucol);
     dev_free(p->d_uw);
     dev_free(p->d_check);
-}
-
-// Pack columns: global node index, and for +-1 weights the sign in bit 31.
-void pack_columns(oim_problem_s* p) {
-    p->h_col.resize(p->h_col_plain.size());
-    for (size_t e = 0; e < p->h_col_plain.size(); ++e) {
-        uint32_t c = (uint32_t)p->h_col_plain[e];
-        if (p->unit_weights && p->h_w[e] < 0.f) c |= kSignBit;
-        p->h_col[e] = c;
-    }
 }
 
 void free_run_buffers(oim_run_s* r) {
@@ -951,27 +994,42 @@ int oim_create_problem(int32_t n, int32_t q, int64_t nnz, const int64_t* row_ptr
     if (q < 2 || q > 16) return fail(OIM_EINVAL, "q must be in [2, 16]");
     if (nnz < 0 || nnz >= ((int64_t)1 << 31)) return fail(OIM_EINVAL, "nnz out of range");
     if (!row_ptr || (nnz > 0 && !col_idx)) return fail(OIM_EINVAL, "NULL CSR array");
-    std::vector<int64_t> rp;
-    std::vector<int32_t> ci;
-    std::vector<float> w;
-    OIM_CUDA(fetch(rp, row_ptr, (size_t)n + 1), "read row_ptr");
-    OIM_CUDA(fetch(ci, col_idx, (size_t)nnz), "read col_idx");
+    // host arrays are read in place; device arrays are copied to the host first
+    std::vector<int64_t> rp_store;
+    std::vector<int32_t> ci_store;
+    std::vector<float> w_store;
+    const int64_t* rp = nullptr;
+    const int32_t* ci = nullptr;
+    const float* w = nullptr;
+    OIM_CUDA(view(rp, rp_store, row_ptr, (size_t)n + 1), "read row_ptr");
+    OIM_CUDA(view(ci, ci_store, col_idx, (size_t)nnz), "read col_idx");
     if (weights) {
-        OIM_CUDA(fetch(w, weights, (size_t)nnz), "read weights");
+        OIM_CUDA(view(w, w_store, weights, (size_t)nnz), "read weights");
     } else {
-        w.assign((size_t)nnz, 1.0f);
+        w_store.assign((size_t)nnz, 1.0f);
+        w = w_store.data();
     }
     if (rp[0] != 0 || rp[n] != nnz) return fail(OIM_EINVAL, "row_ptr[0] must be 0 and row_ptr[n] = nnz");
+    // one pass: the structure checks, the longest row, the weight of the upper triangle
+    // (summed in row order) and whether every weight is +-1 / an integer
     int32_t max_deg = 0;
+    double wt = 0.0;
+    bool unit = true, integer = true;
     for (int32_t i = 0; i < n; ++i) {
         if (rp[i + 1] < rp[i]) return fail(OIM_EINVAL, "row_ptr must be nondecreasing");
         max_deg = std::max<int32_t>(max_deg, (int32_t)(rp[i + 1] - rp[i]));
+        int32_t prev = -1;
         for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
             const int32_t j = ci[e];
+            const float x = w[e];
             if (j < 0 || j >= n) return fail(OIM_EINVAL, "column index out of range");
             if (j == i) return fail(OIM_EINVAL, "diagonal entry (self coupling) in row " + std::to_string(i));
-            if (e > rp[i] && ci[e - 1] >= j) return fail(OIM_EINVAL, "columns must increase within a row");
-            if (!std::isfinite(w[e])) return fail(OIM_EINVAL, "non-finite weight");
+            if (j <= prev) return fail(OIM_EINVAL, "columns must increase within a row");
+            if (!std::isfinite(x)) return fail(OIM_EINVAL, "non-finite weight");
+            prev = j;
+            if (j > i) wt += (double)x;
+            unit &= std::fabs(x) == 1.0f;
+            integer &= x == std::floor(x);
         }
     }
     if (!(flags & OIM_FLAG_SKIP_SYMMETRY_CHECK)) {
@@ -979,7 +1037,7 @@ int oim_create_problem(int32_t n, int32_t q, int64_t nnz, const int64_t* row_ptr
         // mirror the visited (i, j) come in increasing i, that is in row j's column
         // order: one cursor per row walks them, and every cursor must end at its row's
         // end (each entry matched exactly once, with the same weight).
-        std::vector<int64_t> cur(rp.begin(), rp.end() - 1);
+        std::vector<int64_t> cur(rp, rp + n);
         for (int32_t i = 0; i < n; ++i)
             for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
                 const int32_t j = ci[e];
@@ -1007,43 +1065,48 @@ int oim_create_problem(int32_t n, int32_t q, int64_t nnz, const int64_t* row_ptr
     gd.node_off = 0;
     gd.edge_off = 0;
     gd.max_deg = max_deg;
-    double wt = 0.0;
-    for (int32_t i = 0; i < n; ++i)
-        for (int64_t e = rp[i]; e < rp[i + 1]; ++e)
-            if (ci[e] > i) wt += (double)w[e];
     gd.wtot = wt;
     p->graphs.push_back(gd);
     p->h_rowp.resize((size_t)n + 1);
     for (int32_t i = 0; i <= n; ++i) p->h_rowp[i] = (int32_t)rp[i];
-    for (float x : w) {
-        if (std::fabs(x) != 1.0f) p->unit_weights = false;
-        if (x != std::floor(x)) p->integer_weights = false;
-    }
+    p->unit_weights = unit;
+    p->integer_weights = integer;
     // With +-1 weights each row is stored positive entries first (each part in
-    // ascending column order), so the coupling gather is two sign-free loops.
+    // ascending column order), so the coupling gather is two sign-free loops; h_col
+    // carries the sign in its top bit.  (Each entry's place is computed, not branched
+    // on: the signs of a +-1 graph are random.)
     p->h_col_plain.resize((size_t)nnz);
+    p->h_col.resize((size_t)nnz);
     p->h_w.resize((size_t)nnz);
     p->h_split.resize((size_t)n);
     for (int32_t i = 0; i < n; ++i) {
-        int64_t at = rp[i];
-        for (int pass = 0; pass < 2; ++pass) {
-            if (pass == 1) p->h_split[i] = (int32_t)at;
-            for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
-                const bool neg = p->unit_weights && w[e] < 0.f;
-                if (neg != (pass == 1)) continue;
-                p->h_col_plain[at] = ci[e];
-                p->h_w[at] = w[e];
-                ++at;
-            }
+        const int64_t b = rp[i], en = rp[i + 1];
+        if (!unit) {
+            std::copy(ci + b, ci + en, p->h_col_plain.begin() + b);
+            std::copy(w + b, w + en, p->h_w.begin() + b);
+            for (int64_t e = b; e < en; ++e) p->h_col[e] = (uint32_t)ci[e];
+            p->h_split[i] = (int32_t)en;
+            continue;
         }
-        if (!p->unit_weights) p->h_split[i] = (int32_t)rp[i + 1];
+        int64_t nneg = 0;
+        for (int64_t e = b; e < en; ++e) nneg += w[e] < 0.f;
+        int64_t pos = b, neg = en - nneg;
+        p->h_split[i] = (int32_t)neg;
+        for (int64_t e = b; e < en; ++e) {
+            const bool ng = w[e] < 0.f;
+            const int64_t at = ng ? neg : pos;
+            p->h_col_plain[at] = ci[e];
+            p->h_col[at] = (uint32_t)ci[e] | (ng ? kSignBit : 0u);
+            p->h_w[at] = w[e];
+            neg += ng;
+            pos += !ng;
+        }
     }
     p->h_order.resize((size_t)n);
     for (int32_t i = 0; i < n; ++i) p->h_order[i] = i;
     std::stable_sort(p->h_order.begin(), p->h_order.end(), [&](int32_t a, int32_t b) {
         return rp[a + 1] - rp[a] > rp[b + 1] - rp[b];
     });
-    pack_columns(p);
     if (!(flags & OIM_FLAG_DEFER_UPLOAD)) {
         int rc = upload_problem(p);
         if (rc != OIM_OK) {
@@ -1056,8 +1119,11 @@ int oim_create_problem(int32_t n, int32_t q, int64_t nnz, const int64_t* row_ptr
     return OIM_OK;
 }
 
-int oim_create_batch(int32_t count, const oim_problem_t* problems, oim_problem_t* out) {
-    g_last_error.clear();
+namespace {
+
+// oim_create_batch, with the upload left to the first run when `defer` is set.  The
+// members' rows are copied into the batch graph by graph on host threads.
+int create_batch(int32_t count, const oim_problem_t* problems, bool defer, oim_problem_t* out) {
     if (!out) return fail(OIM_EINVAL, "out is NULL");
     *out = nullptr;
     if (count < 1 || !problems) return fail(OIM_EINVAL, "count must be >= 1");
@@ -1079,39 +1145,102 @@ int oim_create_batch(int32_t count, const oim_problem_t* problems, oim_problem_t
     p->G = count;
     p->nodes = nodes;
     p->nnz = nnz;
-    p->h_rowp.reserve((size_t)nodes + 1);
-    p->h_rowp.push_back(0);
+    for (int32_t k = 0; k < count; ++k) {
+        p->unit_weights = p->unit_weights && problems[k]->unit_weights;
+        p->integer_weights = p->integer_weights && problems[k]->integer_weights;
+    }
+    p->h_rowp.resize((size_t)nodes + 1);
+    p->h_split.resize((size_t)nodes);
+    p->h_order.resize((size_t)nodes);
+    p->h_col_plain.resize((size_t)nnz);
+    p->h_col.resize((size_t)nnz);
+    p->h_w.resize((size_t)nnz);
+    p->h_rowp[0] = 0;
+    std::vector<int64_t> noffs((size_t)count), eoffs((size_t)count);
     int64_t noff = 0, eoff = 0;
     for (int32_t k = 0; k < count; ++k) {
-        const oim_problem_s* s = problems[k];
-        GraphDev gd = s->graphs[0];
+        GraphDev gd = problems[k]->graphs[0];
         gd.node_off = (int32_t)noff;
         gd.edge_off = (int32_t)eoff;
         p->graphs.push_back(gd);
         p->max_n = std::max(p->max_n, gd.n);
-        for (int32_t i = 0; i < gd.n; ++i) {
-            p->h_rowp.push_back((int32_t)(eoff + s->h_rowp[i + 1]));
-            p->h_split.push_back((int32_t)(eoff + s->h_split[i]));
-            p->h_order.push_back(s->h_order[i]);
-        }
-        for (size_t e = 0; e < s->h_col_plain.size(); ++e) {
-            p->h_col_plain.push_back((int32_t)(s->h_col_plain[e] + noff));
-            p->h_w.push_back(s->h_w[e]);
-        }
-        p->unit_weights = p->unit_weights && s->unit_weights;
-        p->integer_weights = p->integer_weights && s->integer_weights;
+        noffs[(size_t)k] = noff;
+        eoffs[(size_t)k] = eoff;
         noff += gd.n;
-        eoff += s->nnz;
+        eoff += problems[k]->nnz;
     }
-    pack_columns(p);
-    int rc = upload_problem(p);
-    if (rc != OIM_OK) {
-        free_problem(p);
-        delete p;
-        return rc;
+    // the member's columns moved by its node offset; the packed words keep their sign
+    // bit only where the whole batch has +-1 weights
+    const uint32_t keep = p->unit_weights ? kSignBit : 0u;
+    parallel_for(count, nnz, [&](int64_t k) {
+        const oim_problem_s* s = problems[k];
+        const int64_t no = noffs[(size_t)k], eo = eoffs[(size_t)k];
+        for (int32_t i = 0; i < s->graphs[0].n; ++i) {
+            p->h_rowp[(size_t)(no + i + 1)] = (int32_t)(eo + s->h_rowp[i + 1]);
+            p->h_split[(size_t)(no + i)] = (int32_t)(eo + s->h_split[i]);
+            p->h_order[(size_t)(no + i)] = s->h_order[i];
+        }
+        for (int64_t e = 0; e < s->nnz; ++e) {
+            const int32_t c = s->h_col_plain[(size_t)e] + (int32_t)no;
+            p->h_col_plain[(size_t)(eo + e)] = c;
+            p->h_col[(size_t)(eo + e)] = (uint32_t)c | (s->h_col[(size_t)e] & keep);
+        }
+        std::copy(s->h_w.begin(), s->h_w.end(), p->h_w.begin() + eo);
+    });
+    if (!defer) {
+        const int rc = upload_problem(p);
+        if (rc != OIM_OK) {
+            free_problem(p);
+            delete p;
+            return rc;
+        }
     }
     *out = p;
     return OIM_OK;
+}
+
+}  // namespace
+
+int oim_create_batch(int32_t count, const oim_problem_t* problems, oim_problem_t* out) {
+    g_last_error.clear();
+    return create_batch(count, problems, false, out);
+}
+
+int oim_create_batch_csr(int32_t count, const int32_t* n, int32_t q, const int64_t* nnz,
+                         const int64_t* const* row_ptr, const int32_t* const* col_idx,
+                         const float* const* weights, uint32_t flags, oim_problem_t* out) {
+    NvtxRange range("oim_create_batch_csr");
+    g_last_error.clear();
+    if (!out) return fail(OIM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (count < 1) return fail(OIM_EINVAL, "count must be >= 1");
+    if (!n || !nnz || !row_ptr || !col_idx) return fail(OIM_EINVAL, "NULL per-graph array");
+    // each graph as oim_create_problem would take it (kept on the host), on host threads;
+    // a worker thread starts on device 0, so it is first moved to the caller's device
+    int dev = 0;
+    const bool have_dev = cudaGetDevice(&dev) == cudaSuccess;
+    std::vector<oim_problem_t> members((size_t)count, nullptr);
+    std::vector<int> rcs((size_t)count, OIM_OK);
+    std::vector<std::string> msgs((size_t)count);
+    int64_t work = 0;
+    for (int32_t k = 0; k < count; ++k) work += std::max<int64_t>(nnz[k], 0) + std::max<int32_t>(n[k], 0);
+    parallel_for(count, work, [&](int64_t k) {
+        if (have_dev) cudaSetDevice(dev);
+        rcs[(size_t)k] = oim_create_problem(n[k], q, nnz[k], row_ptr[k], col_idx[k], weights ? weights[k] : nullptr,
+                                            flags | OIM_FLAG_DEFER_UPLOAD, &members[(size_t)k]);
+        if (rcs[(size_t)k] != OIM_OK) msgs[(size_t)k] = oim_last_error();
+    });
+    int rc = OIM_OK;
+    for (int32_t k = 0; k < count && rc == OIM_OK; ++k)
+        if (rcs[(size_t)k] != OIM_OK) rc = fail(rcs[(size_t)k], "graph " + std::to_string(k) + ": " + msgs[(size_t)k]);
+    if (rc == OIM_OK) rc = create_batch(count, members.data(), (flags & OIM_FLAG_DEFER_UPLOAD) != 0, out);
+    for (oim_problem_t m : members)
+        if (m) {
+            // never uploaded: host memory only
+            free_problem(m);
+            delete m;
+        }
+    return rc;
 }
 
 int oim_problem_info(oim_problem_t p, int32_t* graphs, int64_t* nodes, int64_t* nnz, int32_t* q) {

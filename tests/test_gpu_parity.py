@@ -483,3 +483,39 @@ def test_overlapped_scoring_matches_inline_scoring(orc):
         assert np.array_equal(oa["score"], ob["score"])
     for gi, g in enumerate((g0, g1)):
         assert np.array_equal(oa["score"][gi], orc.scores(g, 2, orc.readout_f32(2, pa[gi])))
+
+
+@pytest.mark.parametrize("form,precision", [("stream", "fp16"), ("stream", "fp32"), ("resident", "fp32")])
+def test_batch_from_csr_arrays_runs_like_members_then_batch(form, precision):
+    # oim_create_batch_csr lays the graphs out on host threads and joins them in one call;
+    # its batch must be the one oim_create_problem per graph plus oim_create_batch build:
+    # the same phases, scores and traces bit for bit (+-1 graphs with their sign runs, a
+    # real-weight batch, a graph given as device arrays)
+    import torch
+    from paper_2505_22631_gb300 import Problem, Run, oim_create_batch_csr
+    from workloads import sherrington_kirkpatrick
+    T, R = 60, 64
+    cases = [[erdos_renyi(300, 0.05, 31, "pm1"), torus(12, 10, 32, "pm1"), erdos_renyi(200, 0.08, 33, "+1")],
+             [sherrington_kirkpatrick(120, 34), erdos_renyi(250, 0.05, 35, "+1")]]
+    for gs in cases:
+        K = [constant(T, 2.0 / g.mean_degree) for g in gs]
+        Ks, Kn = [linear_ramp(T, 0.0, 1.0)] * len(gs), [constant(T, 0.1)] * len(gs)
+        sched = (np.stack(K), np.stack(Ks), np.stack(Kn))
+        kw = dict(form=form, precision=precision, readout_every=20)
+        ref_prob = Problem.batch([Problem.from_graph(g, 2) for g in gs])
+        ref = Run(ref_prob, *sched, 0.01, T, R, 7, **kw)
+        # the first graph's arrays on the device, the others on the host
+        dev = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (gs[0].row_ptr, gs[0].col, gs[0].w)]
+        h = oim_create_batch_csr([g.n for g in gs], 2, [g.nnz for g in gs], [dev[0]] + [g.row_ptr for g in gs[1:]],
+                                 [dev[1]] + [g.col for g in gs[1:]], [dev[2]] + [g.w for g in gs[1:]])
+        prob = Problem(h, len(gs), [g.n for g in gs], 2)
+        run = Run(prob, *sched, 0.01, T, R, 7, **kw)
+        for a, b in zip(ref.phases(), run.phases()):
+            assert np.array_equal(a, b)
+        ra, rb = ref.readout(energy=True), run.readout(energy=True)
+        for key in ("score", "best_replica", "trace", "energy"):
+            assert np.array_equal(ra[key], rb[key]), key
+        same = Problem.from_graphs(gs, 2)
+        again = Run(same, *sched, 0.01, T, R, 7, **kw)
+        for a, b in zip(ref.phases(), again.phases()):
+            assert np.array_equal(a, b)

@@ -151,6 +151,47 @@ def test_symmetry_check_agrees_with_the_dense_definition(capi):
         assert accepted == symmetric, (trial, kind)
 
 
+def test_batch_from_csr_arrays_checks_every_graph(capi):
+    """oim_create_batch_csr (graphs checked on host threads, upload deferred here): the
+    batch has the graphs' sizes, a malformed graph is rejected with the checks of
+    oim_create_problem and its index in the message, and empty or NULL lists are refused."""
+    from workloads import erdos_renyi, torus
+    gs = [erdos_renyi(60 + 10 * k, 0.1, k, "pm1" if k % 2 else "+1") for k in range(6)] + [torus(6, 5, 3, "pm1")]
+    ws = [None if k % 3 == 0 else g.w for k, g in enumerate(gs)]
+    h = capi.oim_create_batch_csr([g.n for g in gs], 2, [g.nnz for g in gs], [g.row_ptr for g in gs],
+                                  [g.col for g in gs], ws, capi.OIM_FLAG_DEFER_UPLOAD)
+    assert capi.oim_problem_info(h) == (len(gs), sum(g.n for g in gs), sum(g.nnz for g in gs), 2)
+    capi.oim_destroy_problem(h)
+    # graph 4 gets a diagonal entry, graph 5 an asymmetric weight: the first is named
+    bad_col = gs[4].col.copy()
+    bad_col[gs[4].row_ptr[3]] = 3
+    bad_w = gs[5].w.copy()
+    bad_w[0] = 3.0
+    cols = [g.col for g in gs]
+    cols[4] = bad_col
+    wts = [g.w for g in gs]
+    wts[5] = bad_w
+    with pytest.raises(capi.OimError) as ei:
+        capi.oim_create_batch_csr([g.n for g in gs], 2, [g.nnz for g in gs], [g.row_ptr for g in gs], cols, wts,
+                                  capi.OIM_FLAG_DEFER_UPLOAD)
+    assert ei.value.code == capi.OIM_EINVAL
+    assert capi.oim_last_error().startswith("graph 4: ")
+    # the symmetry check is the caller's to skip, as in oim_create_problem
+    wts[4] = gs[4].w
+    h = capi.oim_create_batch_csr([g.n for g in gs], 2, [g.nnz for g in gs], [g.row_ptr for g in gs],
+                                  [g.col for g in gs], wts,
+                                  capi.OIM_FLAG_DEFER_UPLOAD | capi.OIM_FLAG_SKIP_SYMMETRY_CHECK)
+    capi.oim_destroy_problem(h)
+    with pytest.raises(capi.OimError) as ei:
+        capi.oim_create_batch_csr([], 2, [], [], [], None)
+    assert ei.value.code == capi.OIM_EINVAL
+    lib = capi.load()
+    out = ctypes.c_void_p()
+    n = np.array([4], np.int32)
+    assert lib.oim_create_batch_csr(1, n.ctypes.data, 2, None, None, None, None, 0, ctypes.byref(out)) == \
+        capi.OIM_EINVAL
+
+
 def test_null_handles_rejected(capi):
     with pytest.raises(capi.OimError) as ei:
         capi.oim_run_sync(None)
