@@ -1226,9 +1226,15 @@ int oim_create_batch_csr(int32_t count, const int32_t* n, int32_t q, const int64
     for (int32_t k = 0; k < count; ++k) work += std::max<int64_t>(nnz[k], 0) + std::max<int32_t>(n[k], 0);
     parallel_for(count, work, [&](int64_t k) {
         if (have_dev) cudaSetDevice(dev);
-        rcs[(size_t)k] = oim_create_problem(n[k], q, nnz[k], row_ptr[k], col_idx[k], weights ? weights[k] : nullptr,
-                                            flags | OIM_FLAG_DEFER_UPLOAD, &members[(size_t)k]);
-        if (rcs[(size_t)k] != OIM_OK) msgs[(size_t)k] = oim_last_error();
+        try {
+            rcs[(size_t)k] = oim_create_problem(n[k], q, nnz[k], row_ptr[k], col_idx[k],
+                                                weights ? weights[k] : nullptr, flags | OIM_FLAG_DEFER_UPLOAD,
+                                                &members[(size_t)k]);
+            if (rcs[(size_t)k] != OIM_OK) msgs[(size_t)k] = oim_last_error();
+        } catch (...) {   // a host allocation that failed on a worker thread
+            rcs[(size_t)k] = OIM_ENOMEM;
+            msgs[(size_t)k] = "host allocation";
+        }
     });
     int rc = OIM_OK;
     for (int32_t k = 0; k < count && rc == OIM_OK; ++k)
