@@ -248,6 +248,8 @@ __device__ __forceinline__ uint32_t f2_to_h2(float2 f) {
     }
 }
 
+constexpr int kOctetThreads = 128;   // threads per block of the per-step 16-bit kernel
+
 // The 16-bit form: thread = node x octet of eight consecutive replicas.  A slot's
 // 32-byte descriptor {node, row start, first -1 entry, row end, graph, local index,
 // first two column indices} arrives in one load, so the first two neighbours' pairs
@@ -267,9 +269,12 @@ __device__ __forceinline__ uint32_t f2_to_h2(float2 f) {
 // -(acc - x1 - x2) = (x1 - acc) + x2, each rounding to nearest exactly as the FMAs by -1
 // would.  The sign is folded into dt K at the end (exact).  Other weights: each pair
 // is converted to FP32 and multiply-added.
-// 48 registers (five blocks of 256 per SM): 40 warps to cover the gather's latency
-// (measured on the two-graph benchmark batch: 64 registers 19.9 us, 48 registers
-// 18.6 us per step; 40 registers spill)
+// 48 registers: 40 warps an SM to cover the gather's latency (measured on the two-graph
+// benchmark batch: 64 registers 19.9 us, 48 registers 18.6 us per step; 40 registers
+// spill), in blocks of 128 threads (ten an SM): a block's slot frees as soon as its four
+// nodes are done, which leaves fewer warp slots idle behind a block's slowest warp than
+// blocks of eight nodes (16.95 against 17.28 us per step on the benchmark batch, 124.4
+// against 127.8 on the 16-graph batch; 64 threads: 17.00 / 123.2)
 // One step of one (slot, octet) work item.  kCoherent: the neighbours' pairs are read
 // through L2 only (ld.global.cg), for the persistent kernel, whose pairs were written
 // by other blocks during the same launch; the per-step kernel reads them through the
@@ -411,7 +416,7 @@ __device__ __forceinline__ T* after_wait(T* p) {
 }
 
 template <typename H2, bool kUnit, int kQ>
-__global__ void __launch_bounds__(256, 5) step_octet_kernel(CSRDev csr, StepParams P, float* theta,
+__global__ void __launch_bounds__(kOctetThreads, 10) step_octet_kernel(CSRDev csr, StepParams P, float* theta,
                                                             const H2* __restrict__ cs_in,
                                                             H2* __restrict__ cs_out, int64_t t_fixed,
                                                             const int32_t* __restrict__ d_t0,
@@ -558,16 +563,17 @@ cudaError_t launch_set_seed(uint64_t* d_seed, uint64_t seed, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// Launch shape of the thread = (node, replica quad) kernels: blocks of 256 threads,
-// x over quads (a warp covers consecutive quads of a node: coalesced rows), y over
-// nodes; the grid runs nodes along x (up to 2^31 - 1 blocks) and quads along y.
+// Launch shape of the thread = (node, replica quad) kernels: blocks of 256 threads (the
+// per-step 16-bit kernel: kOctetThreads), x over quads (a warp covers consecutive quads
+// of a node: coalesced rows), y over nodes; the grid runs nodes along x (up to 2^31 - 1
+// blocks) and quads along y.
 struct QuadGrid {
     dim3 grid, block;
 };
-static QuadGrid quad_grid(int64_t nodes, int quads) {
+static QuadGrid quad_grid(int64_t nodes, int quads, int threads = 256) {
     int qx = 1;
     while (qx < quads && qx < 32) qx <<= 1;
-    const int ny = 256 / qx;
+    const int ny = threads / qx;
     QuadGrid q;
     q.block = dim3((unsigned)qx, (unsigned)ny);
     q.grid = dim3((unsigned)((nodes + ny - 1) / ny), (unsigned)((quads + qx - 1) / qx));
@@ -580,8 +586,8 @@ struct StepGrid {
     dim3 grid, block;
     int quads_fast;
 };
-static StepGrid step_grid(int64_t nodes, int quads) {
-    const QuadGrid q = quad_grid(nodes, quads);
+static StepGrid step_grid(int64_t nodes, int quads, int threads = 256) {
+    const QuadGrid q = quad_grid(nodes, quads, threads);
     StepGrid sg{q.grid, q.block, 0};
     if (q.grid.x <= 65535u) {
         sg.grid = dim3(q.grid.y, q.grid.x);
@@ -706,7 +712,7 @@ template <typename H2>
 static cudaError_t step_octet(const oim_run_s& r, int64_t t, const int32_t* d_t0, cudaStream_t s) {
     const StepParams P = params_of(r);
     const CSRDev csr = step_csr(r);
-    const StepGrid q = step_grid(csr.nodes, r.R_pad / 8);
+    const StepGrid q = step_grid(csr.nodes, r.R_pad / 8, kOctetThreads);
     const int in = (int)(t & 1);
     // phases in place (one buffer), the (cos, sin) pairs double-buffered
     float* theta = r.d_theta[in];
