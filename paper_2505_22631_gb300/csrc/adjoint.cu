@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(256) adj_planes_kernel(int64_t state, const fl
 // D(theta) * scale into lam (the terminal adjoint, scale = -2 pi / R), and the
 // per-graph FP64 sum of E = 1/2 sum_i (c_i A_i + s_i B_i) over the real replicas.
 // Y: the (c, s) planes of theta.
-__global__ void __launch_bounds__(256) adj_terminal_kernel(CSRDev csr, int R, int R_pad, float scale,
+__global__ void __launch_bounds__(128) adj_terminal_kernel(CSRDev csr, int R, int R_pad, float scale,
                                                            const float* __restrict__ Y,
                                                            float* __restrict__ lam,
                                                            double* __restrict__ loss) {
@@ -101,9 +101,9 @@ __global__ void __launch_bounds__(256) adj_terminal_kernel(CSRDev csr, int R, in
 // theta_prev (theta_{t-1}) is given, the planes lambda_t (c, s)_{t-1} for step t - 1.
 //   AB   the forward step's coupling sums at theta_t, float2 [node][R_pad]
 //   Ylam the planes lambda_{t+1} c_t, lambda_{t+1} s_t
-// 64 registers, four blocks per SM (measured: 726 -> 699 ms for the backward pass of the
+// 64 registers, 32 warps per SM (measured: 726 -> 699 ms for the backward pass of the
 // schedule workload against the unbounded 70 registers)
-__global__ void __launch_bounds__(256, 4) adj_step_kernel(CSRDev csr, StepParams P, int64_t t,
+__global__ void __launch_bounds__(128, 8) adj_step_kernel(CSRDev csr, StepParams P, int64_t t,
                                                        const float* __restrict__ theta,
                                                        const float* __restrict__ theta_prev,
                                                        const float2* __restrict__ AB,
@@ -218,15 +218,17 @@ __global__ void __launch_bounds__(256, 4) adj_step_kernel(CSRDev csr, StepParams
 
 StepParams make_params(const oim_run_s& r);
 
-// Blocks of 256 threads: x over replica quads (a warp covers consecutive quads of a
-// node), y over nodes; the grid runs nodes along x and quads along y.
+// Blocks of 128 threads: x over replica quads (a warp covers consecutive quads of a
+// node), y over nodes; the grid runs nodes along x and quads along y.  (Against blocks of
+// 256: the backward pass of the 64-graph schedule workload 237.1 -> 230.3 ms, a block's
+// slot freeing as soon as its fewer nodes are done.)
 struct QuadGridA {
     dim3 grid, block;
 };
 static QuadGridA quad_grid_a(int64_t nodes, int quads) {
     int qx = 1;
     while (qx < quads && qx < 32) qx <<= 1;
-    const int ny = 256 / qx;
+    const int ny = 128 / qx;
     QuadGridA q;
     q.block = dim3((unsigned)qx, (unsigned)ny);
     q.grid = dim3((unsigned)((nodes + ny - 1) / ny), (unsigned)((quads + qx - 1) / qx));
