@@ -515,7 +515,10 @@ def test_batch_from_csr_arrays_runs_like_members_then_batch(form, precision):
         ra, rb = ref.readout(energy=True), run.readout(energy=True)
         for key in ("score", "best_replica", "trace", "energy"):
             assert np.array_equal(ra[key], rb[key]), key
-        same = Problem.from_graphs(gs, 2)
-        again = Run(same, *sched, 0.01, T, R, 7, **kw)
-        for a, b in zip(ref.phases(), again.phases()):
-            assert np.array_equal(a, b)
+        # the Python form, and a batch whose upload waits for its first run
+        from paper_2505_22631_gb300 import capi
+        for flags in (0, capi.OIM_FLAG_DEFER_UPLOAD):
+            same = Problem.from_graphs(gs, 2, flags=flags)
+            again = Run(same, *sched, 0.01, T, R, 7, **kw)
+            for a, b in zip(ref.phases(), again.phases()):
+                assert np.array_equal(a, b)
