@@ -581,20 +581,20 @@ static QuadGrid quad_grid(int64_t nodes, int quads, int threads = 128) {
     return q;
 }
 
-// The step kernels' grid: replica blocks along x (dispatched first) and node blocks
-// along y while the node blocks fit grid.y (65535), else the quad_grid orientation.
+// The step kernels' grid: node blocks along x (dispatched first, heaviest rows first) and
+// replica blocks along y, quads_fast = 0.  The blocks that run at the same time then share
+// a replica range, and with it the neighbours' pair segments in L1 and L2 (a torus row's
+// neighbours are the rows next to it): 17.03 -> 16.77 us per step for the 16-bit kernel
+// and 35.4 -> 34.3 for the FP32 one on the benchmark batch, against replica blocks along
+// x (quads_fast = 1), which put every replica block of the heaviest rows first.  The
+// kernels keep both orientations (quads_fast a launch argument).
 struct StepGrid {
     dim3 grid, block;
     int quads_fast;
 };
 static StepGrid step_grid(int64_t nodes, int quads, int threads = 128) {
     const QuadGrid q = quad_grid(nodes, quads, threads);
-    StepGrid sg{q.grid, q.block, 0};
-    if (q.grid.x <= 65535u) {
-        sg.grid = dim3(q.grid.y, q.grid.x);
-        sg.quads_fast = 1;
-    }
-    return sg;
+    return StepGrid{q.grid, q.block, 0};
 }
 
 static StepParams params_of(const oim_run_s& r) {
