@@ -771,14 +771,21 @@ cudaError_t enqueue_steps(const oim_run_s& r, int64_t t0, int64_t t1, const int3
 // A per-step form as init, steps / L replays of one captured chunk of L steps and its
 // score passes (steps and readout slots read from the device step base, which the
 // chunk's last node moves on by L), and the remaining steps launched directly.  The
-// chunk is captured once per (L, dt, readout period) and kept with the run.
+// chunk is captured once per (L, dt, readout period) and kept with the run.  When it has
+// to be captured, the first L steps are launched directly before the capture, so that
+// the GPU runs them while the host records and instantiates the chunk.
 int enqueue_stream_chunks(oim_run_s* r, int64_t L) {
     cudaStream_t s = r->stream;
     cudaError_t e = init_parts(*r, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(r->d_t0, 0, sizeof(int32_t), s);
     if (e != cudaSuccess) return cuda_fail(e, "stream-form launch");
+    int64_t first = 0;   // chunks already launched directly
     if (!r->step_chunk_exec || r->step_chunk_len != L || r->step_chunk_dt != r->dt ||
         r->step_chunk_every != r->readout_every) {
+        e = enqueue_steps(*r, 0, L, nullptr, s);
+        if (e == cudaSuccess) e = launch_advance_t0(r->d_t0, (int32_t)L, s);
+        if (e != cudaSuccess) return cuda_fail(e, "stream-form launch");
+        first = 1;
         if (r->step_chunk_exec) cudaGraphExecDestroy(r->step_chunk_exec);
         r->step_chunk_exec = nullptr;
         cudaStream_t cap = nullptr;
@@ -804,7 +811,7 @@ int enqueue_stream_chunks(oim_run_s* r, int64_t L) {
         r->step_chunk_every = r->readout_every;
     }
     const int64_t chunks = r->steps / L;
-    for (int64_t c = 0; c < chunks; ++c) OIM_CUDA(cudaGraphLaunch(r->step_chunk_exec, s), "chunk launch");
+    for (int64_t c = first; c < chunks; ++c) OIM_CUDA(cudaGraphLaunch(r->step_chunk_exec, s), "chunk launch");
     if (e == cudaSuccess) e = enqueue_steps(*r, chunks * L, r->steps, nullptr, s);
     if (e == cudaSuccess) e = common_parts(*r, s);
     if (e != cudaSuccess) return cuda_fail(e, "stream-form launch");
