@@ -495,10 +495,13 @@ def test_batch_from_csr_arrays_runs_like_members_then_batch(form, precision):
     from paper_2505_22631_gb300 import Problem, Run, oim_create_batch_csr
     from workloads import sherrington_kirkpatrick
     T, R = 60, 64
+    edgeless = csr_from_edges(5, np.zeros(0, np.int64), np.zeros(0, np.int64), None, "edgeless5")
+    single = csr_from_edges(1, np.zeros(0, np.int64), np.zeros(0, np.int64), None, "single")
     cases = [[erdos_renyi(300, 0.05, 31, "pm1"), torus(12, 10, 32, "pm1"), erdos_renyi(200, 0.08, 33, "+1")],
-             [sherrington_kirkpatrick(120, 34), erdos_renyi(250, 0.05, 35, "+1")]]
+             [sherrington_kirkpatrick(120, 34), erdos_renyi(250, 0.05, 35, "+1")],
+             [erdos_renyi(100, 0.1, 36, "pm1"), edgeless, single]]
     for gs in cases:
-        K = [constant(T, 2.0 / g.mean_degree) for g in gs]
+        K = [constant(T, 2.0 / max(g.mean_degree, 1.0)) for g in gs]
         Ks, Kn = [linear_ramp(T, 0.0, 1.0)] * len(gs), [constant(T, 0.1)] * len(gs)
         sched = (np.stack(K), np.stack(Ks), np.stack(Kn))
         kw = dict(form=form, precision=precision, readout_every=20)

@@ -162,6 +162,12 @@ def test_batch_from_csr_arrays_checks_every_graph(capi):
                                   [g.col for g in gs], ws, capi.OIM_FLAG_DEFER_UPLOAD)
     assert capi.oim_problem_info(h) == (len(gs), sum(g.n for g in gs), sum(g.nnz for g in gs), 2)
     capi.oim_destroy_problem(h)
+    # graphs without edges and a single node are graphs like any other
+    empty_rp, empty_col = np.zeros(6, np.int64), np.zeros(0, np.int32)
+    h = capi.oim_create_batch_csr([5, 1, gs[0].n], 2, [0, 0, gs[0].nnz], [empty_rp, empty_rp[:2], gs[0].row_ptr],
+                                  [empty_col, empty_col, gs[0].col], None, capi.OIM_FLAG_DEFER_UPLOAD)
+    assert capi.oim_problem_info(h) == (3, 6 + gs[0].n, gs[0].nnz, 2)
+    capi.oim_destroy_problem(h)
     # graph 4 gets a diagonal entry, graph 5 an asymmetric weight: the first is named
     bad_col = gs[4].col.copy()
     bad_col[gs[4].row_ptr[3]] = 3
